@@ -1,0 +1,189 @@
+"""CPU oracle for the edge-centric graphlet estimator -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library never calls it, and it
+shares no code with the GPU path.
+
+What it computes (paper: Rossi, Zhou, Ahmed, "Estimation of Graphlet
+Statistics"):
+
+* ``local_counts``  -- Algorithm 2 per sampled edge (triangle set T_e, 2-star
+  sets S_u, S_v via a marker table), Algorithm 3 (4-cliques through e) and
+  Algorithm 4 read as counting pairs (w in S_u, r in S_v) with w ~ r
+  (4-cycles through e).  Plain C in ``oracle.c``.
+* ``sums``          -- exact per-edge numerators N_i (Sec. 3, Eqs. for
+  X_3..X_12 with sigma = M/K) and their sums / sums of squares in 128-bit
+  integers (C), returned as Python ints.
+* ``estimate``      -- the estimators X_i = (M/K) sum N_i / D_i (Sec. 3), the
+  variance V_i and the 95% bounds X -/+ 1.96 sqrt(V) (Sec. 5.3).  Exact
+  rational arithmetic (``fractions.Fraction``) rounded once to fp64.
+  The variance is this project's reading (the paper prints no formula): the
+  design-based variance of the expansion estimator under simple random
+  sampling without replacement, V = M (M-K) Q / (K^2 (K-1) D^2) with
+  Q = K sum N^2 - (sum N)^2.  "parity unpinned" for V against the paper; it is
+  pinned to a direct two-pass sample variance and to the spread across seeds.
+* ``sample``        -- Algorithm 1 with uniform Bernoulli(p) selection of each
+  edge, keyed by a SplitMix64 counter hash (project-defined random source).
+"""
+from __future__ import annotations
+
+import ctypes
+import functools
+import math
+import os
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_oracle.so")
+
+#: graphlet ids carried by the estimator, in output order
+GRAPHLETS = (3, 4, 7, 8, 9, 10, 11, 12)
+#: denominators D_i of X_i = (M/K) * sum N_i / D_i
+DENOM = {3: 3, 4: 2, 7: 6, 8: 1, 9: 2, 10: 4, 11: 6, 12: 1}
+Z95 = 1.96
+
+
+def build(force: bool = False) -> str:
+    src = os.path.join(_HERE, "oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-std=gnu11", "-ffp-contract=off", src,
+                    "-o", _SO + ".tmp"], check=True, capture_output=True)
+    os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+@functools.lru_cache(maxsize=1)
+def _lib() -> ctypes.CDLL:
+    lib = ctypes.CDLL(build())
+    P, I64, U64, I = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
+    lib.oracle_local_counts.argtypes = [I64, P, P, I64, P, I, P, P, P, P, P]
+    lib.oracle_local_counts.restype = I
+    lib.oracle_local_counts_literal_alg4.argtypes = [I64, P, P, I64, P, P, P, P, P, P]
+    lib.oracle_local_counts_literal_alg4.restype = I
+    lib.oracle_numerators.argtypes = [I64, P, P, P, P, P, P, P, P]
+    lib.oracle_sample.argtypes = [I64, P, P, U64, U64, P, I64]
+    lib.oracle_sample.restype = I64
+    lib.oracle_splitmix64.argtypes = [U64]
+    lib.oracle_splitmix64.restype = U64
+    return lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def splitmix64(x: int) -> int:
+    return int(_lib().oracle_splitmix64(x & (2**64 - 1)))
+
+
+def local_counts(row_ptr, col, pairs, four: bool = True, _literal_alg4: bool = False) -> dict:
+    """Per-edge (t, a, b, k, q) for every pair of ``pairs`` (int32 [K, 2]).
+
+    ``_literal_alg4`` runs Algorithm 4 exactly as printed (a planted mistake
+    used only by the tests to show the printed test is wrong)."""
+    row_ptr, col = _c(row_ptr, np.int64), _c(col, np.int32)
+    pairs = _c(pairs, np.int32).reshape(-1, 2)
+    k = len(pairs)
+    out = {name: np.zeros(k, dtype=np.int64) for name in ("t", "a", "b", "k", "q")}
+    ptrs = [out[x].ctypes.data for x in ("t", "a", "b", "k", "q")]
+    if _literal_alg4:
+        rc = _lib().oracle_local_counts_literal_alg4(len(row_ptr) - 1, row_ptr.ctypes.data,
+                                                     col.ctypes.data, k, pairs.ctypes.data, *ptrs)
+    else:
+        rc = _lib().oracle_local_counts(len(row_ptr) - 1, row_ptr.ctypes.data, col.ctypes.data, k,
+                                        pairs.ctypes.data, int(four), *ptrs)
+    if rc != 0:
+        raise ValueError("oracle: a sampled pair is not an edge of the graph")
+    return out
+
+
+def _u128(lo: int, hi: int) -> int:
+    return (int(hi) << 64) | int(lo)
+
+
+def _i128(lo: int, hi: int) -> int:
+    v = _u128(lo, hi)
+    return v - (1 << 128) if v >> 127 else v
+
+
+def numerators(lc: dict, per_edge: bool = False):
+    """Exact sums {i: sum N_i}, {i: sum N_i^2} (Python ints) and optionally
+    the per-edge numerator matrix int64 [K, 8]."""
+    k = len(lc["t"])
+    sums = np.zeros(16, dtype=np.uint64)
+    sq = np.zeros(16, dtype=np.uint64)
+    nmat = np.zeros((k, 8), dtype=np.int64) if per_edge else None
+    _lib().oracle_numerators(k, *(lc[x].ctypes.data for x in ("t", "a", "b", "k", "q")),
+                             nmat.ctypes.data if per_edge else None, sums.ctypes.data,
+                             sq.ctypes.data)
+    s = {g: _i128(sums[2 * i], sums[2 * i + 1]) for i, g in enumerate(GRAPHLETS)}
+    s2 = {g: _u128(sq[2 * i], sq[2 * i + 1]) for i, g in enumerate(GRAPHLETS)}
+    return (s, s2, nmat) if per_edge else (s, s2)
+
+
+def sample(row_ptr, col, fraction: float, seed: int) -> np.ndarray:
+    """Bernoulli(fraction) edge sample as int32 [K, 2] pairs (u < v)."""
+    row_ptr, col = _c(row_ptr, np.int64), _c(col, np.int32)
+    if not (0.0 <= fraction <= 1.0):
+        raise ValueError("fraction must lie in [0, 1]")
+    threshold = int(math.floor(fraction * 2.0**53))
+    m = len(col) // 2
+    out = np.zeros((max(m, 1), 2), dtype=np.int32)
+    kept = _lib().oracle_sample(len(row_ptr) - 1, row_ptr.ctypes.data, col.ctypes.data,
+                                threshold, seed & (2**64 - 1), out.ctypes.data, m)
+    return out[:kept].copy()
+
+
+def estimate(s: dict, s2: dict, m: int, k: int, z: float = Z95) -> dict:
+    """Estimates, variances and bounds per graphlet from exact sums.
+
+    X = (M/K) * S / D                            (Sec. 3, sigma = |E|/|J|)
+    V = M (M-K) (K S2 - S^2) / (K^2 (K-1) D^2)   (SRSWOR variance, K >= 2)
+    lb, ub = X -/+ z sqrt(V)                     (Sec. 5.3, z = 1.96)
+    exact = S / D when K == M (must divide).
+    """
+    res = {}
+    for g in GRAPHLETS:
+        d = DENOM[g]
+        S, S2 = s[g], s2[g]
+        r = {"X": math.nan, "V": math.nan, "lb": math.nan, "ub": math.nan, "exact": None}
+        if k >= 1:
+            r["X"] = float(Fraction(m * S, k * d))
+        if k >= 2:
+            Q = k * S2 - S * S
+            assert Q >= 0
+            r["V"] = float(Fraction(m * (m - k) * Q, k * k * (k - 1) * d * d))
+            half = z * math.sqrt(r["V"])
+            r["lb"] = r["X"] - half
+            r["ub"] = r["X"] + half
+        elif k == m == 1:
+            r["V"] = 0.0
+            r["lb"] = r["ub"] = r["X"]
+        if k == m and k >= 1:
+            if S % d != 0:
+                raise ArithmeticError(f"sum N_{g} = {S} not divisible by {d} at K = M")
+            r["exact"] = S // d
+        res[g] = r
+    return res
+
+
+def exact_counts(row_ptr, col) -> dict:
+    """Exact connected 3- and 4-node graphlet counts (all edges sampled)."""
+    from synth import upper_pairs  # input helper only: lists the edges
+    pairs = upper_pairs(np.asarray(row_ptr), np.asarray(col))
+    lc = local_counts(row_ptr, col, pairs)
+    s, s2 = numerators(lc)
+    est = estimate(s, s2, len(pairs), len(pairs))
+    return {g: est[g]["exact"] for g in GRAPHLETS}
+
+
+def count_estimate(row_ptr, col, pairs, z: float = Z95) -> dict:
+    """Full oracle pipeline on an explicit sampled-edge list."""
+    lc = local_counts(row_ptr, col, pairs)
+    s, s2 = numerators(lc)
+    return {"sums": s, "sq": s2, "K": len(pairs), "M": len(col) // 2,
+            "est": estimate(s, s2, len(col) // 2, len(pairs), z)}

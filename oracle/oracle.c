@@ -1,0 +1,223 @@
+/*
+ * CPU ORACLE -- test infrastructure only.
+ *
+ * A plain, slow, single-threaded restatement of the paper's edge-centric
+ * local counting ("Estimation of Graphlet Statistics", Rossi, Zhou, Ahmed):
+ * Algorithm 2 (per-edge triangle / 2-star split with a marker table Phi),
+ * Algorithm 3 (4-cliques through the edge) and Algorithm 4 (4-cycles through
+ * the edge, read as testing membership of S_v), plus the uniform edge sampler
+ * of Algorithm 1 (Bernoulli per edge, SplitMix64 counter hash) and the exact
+ * integer sums the estimators consume. Only the tests, the smoke check and
+ * the benchmark's CPU-baseline leg may call it; the library never does. It
+ * shares no code with the GPU path.
+ *
+ * Graph: simple undirected, int64 row offsets + int32 sorted adjacency, both
+ * orientations stored (the paper's "ordered" neighbour sets, Sec. 3.1).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+/* ----------------------------------------------------------------------
+ * Per-edge local counts (Algorithm 2 with Algorithms 3 and 4).
+ *
+ * For each sampled edge e = (v, u) the marker table Phi labels vertices:
+ *   L1: neighbours of v other than u (later: S_v)
+ *   L3: triangle-closing vertices T_e = N(u) cap N(v)
+ *   L2: 2-star vertices of u, S_u = N(u) \ {v} \ N(v)
+ * Labels carry an epoch per edge so Phi never needs clearing (the paper's
+ * "unique lambda per neighbourhood" trick). u is the endpoint of smaller
+ * degree (ties: smaller id), as in the complexity discussion of Sec. 3.4;
+ * the counts do not depend on this choice.
+ *
+ * Outputs per edge j (all int64):
+ *   t[j] = |T_e|, a[j] = |S_u|, b[j] = |S_v|,
+ *   k[j] = 4-cliques containing e   = unordered adjacent pairs inside T_e,
+ *   q[j] = induced 4-cycles with e  = pairs (w in S_u, r in S_v), w ~ r.
+ * Returns 0, or -1 if a pair is not an edge of the graph / out of range.
+ * ---------------------------------------------------------------------- */
+static int local_counts(int64_t n, const int64_t* row_ptr, const int32_t* col, int64_t num_pairs,
+                        const int32_t* pairs, int want_four, int literal_alg4, int64_t* t_out,
+                        int64_t* a_out, int64_t* b_out, int64_t* k_out, int64_t* q_out) {
+  int64_t* phi = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int32_t* tri = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  int32_t* star_u = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  if (!phi || !tri || !star_u) return -2;
+  int rc = 0;
+  for (int64_t j = 0; j < num_pairs; ++j) {
+    int64_t x = pairs[2 * j], y = pairs[2 * j + 1];
+    if (x < 0 || y < 0 || x >= n || y >= n || x == y) { rc = -1; break; }
+    int64_t dx = row_ptr[x + 1] - row_ptr[x], dy = row_ptr[y + 1] - row_ptr[y];
+    int64_t u, v;
+    if (dx < dy || (dx == dy && x < y)) { u = x; v = y; } else { u = y; v = x; }
+    const int64_t L1 = 4 * (j + 1) + 1, L2 = 4 * (j + 1) + 2, L3 = 4 * (j + 1) + 3;
+    /* mark N(v) \ {u} with lambda_1 */
+    int adjacent = 0;
+    for (int64_t p = row_ptr[v]; p < row_ptr[v + 1]; ++p) {
+      int64_t w = col[p];
+      if (w == u) { adjacent = 1; continue; }
+      phi[w] = L1;
+    }
+    if (!adjacent) { rc = -1; break; }
+    /* scan N(u) \ {v}: triangle (lambda_3) or 2-star of u (lambda_2) */
+    int64_t nt = 0, na = 0;
+    for (int64_t p = row_ptr[u]; p < row_ptr[u + 1]; ++p) {
+      int64_t w = col[p];
+      if (w == v) continue;
+      if (phi[w] == L1) {
+        tri[nt++] = (int32_t)w;
+        phi[w] = L3;
+      } else {
+        star_u[na++] = (int32_t)w;
+        phi[w] = L2;
+      }
+    }
+    int64_t du = row_ptr[u + 1] - row_ptr[u], dv = row_ptr[v + 1] - row_ptr[v];
+    t_out[j] = nt;
+    a_out[j] = na; /* = du - 1 - nt */
+    b_out[j] = dv - 1 - nt;
+    (void)du;
+    int64_t kk = 0, qq = 0;
+    if (want_four) {
+      /* Algorithm 3: for each w in T, count neighbours still labelled
+       * lambda_3, then clear w's label so each adjacent pair counts once. */
+      for (int64_t i = 0; i < nt; ++i) {
+        int64_t w = tri[i];
+        for (int64_t p = row_ptr[w]; p < row_ptr[w + 1]; ++p)
+          if (phi[col[p]] == L3) ++kk;
+        phi[w] = 0;
+      }
+      /* Algorithm 4 (reading: r must be in S_v, i.e. still lambda_1; the
+       * literal test against lambda_2 is kept only so the tests can show
+       * that it disagrees with brute-force enumeration). */
+      const int64_t want = literal_alg4 ? L2 : L1;
+      for (int64_t i = 0; i < na; ++i) {
+        int64_t w = star_u[i];
+        for (int64_t p = row_ptr[w]; p < row_ptr[w + 1]; ++p)
+          if (phi[col[p]] == want) ++qq;
+      }
+    }
+    k_out[j] = kk;
+    q_out[j] = qq;
+  }
+  free(phi);
+  free(tri);
+  free(star_u);
+  return rc;
+}
+
+int oracle_local_counts(int64_t n, const int64_t* row_ptr, const int32_t* col, int64_t num_pairs,
+                        const int32_t* pairs, int want_four, int64_t* t_out, int64_t* a_out,
+                        int64_t* b_out, int64_t* k_out, int64_t* q_out) {
+  return local_counts(n, row_ptr, col, num_pairs, pairs, want_four, 0, t_out, a_out, b_out, k_out,
+                      q_out);
+}
+
+/* Algorithm 4 exactly as printed (tests Phi(r) = lambda_2): a planted
+ * mistake for the tests, never used to produce expected values. */
+int oracle_local_counts_literal_alg4(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                                     int64_t num_pairs, const int32_t* pairs, int64_t* t_out,
+                                     int64_t* a_out, int64_t* b_out, int64_t* k_out,
+                                     int64_t* q_out) {
+  return local_counts(n, row_ptr, col, num_pairs, pairs, 1, 1, t_out, a_out, b_out, k_out, q_out);
+}
+
+/* ----------------------------------------------------------------------
+ * Per-edge numerators N_i and their exact sums.
+ *
+ * With sigma = M/K the estimators of Sec. 3 (X_3..X_12, weights W) are
+ * linear in per-edge terms: X_i = sigma * sum_e N_i(e) / D_i, where
+ *   N3 = t                                  D3 = 3
+ *   N4 = a + b                              D4 = 2
+ *   N7 = k                                  D7 = 6
+ *   N8 = C(t,2) - k                         D8 = 1
+ *   N9 = t(a+b) - 4 N8                      D9 = 2
+ *   N10 = q                                 D10 = 4
+ *   N11 = 2[C(a,2)+C(b,2)] - t(a+b) + 4 N8  D11 = 6
+ *   N12 = a b - q                           D12 = 1
+ * (X9 = (sigma C9 - 4 X8)/2 and X11 = (sigma C11 - X9)/3 expanded per edge.)
+ * sums[i] receives sum N_i as a signed 128-bit integer (lo, hi words) and
+ * sq[i] receives sum N_i^2 as an unsigned 128-bit integer, i indexing
+ * (3,4,7,8,9,10,11,12) as 0..7.
+ * ---------------------------------------------------------------------- */
+void oracle_numerators(int64_t num, const int64_t* t, const int64_t* a, const int64_t* b,
+                       const int64_t* k, const int64_t* q, int64_t* n_out /* [num][8] or NULL */,
+                       uint64_t* sums /* [8][2] */, uint64_t* sq /* [8][2] */) {
+  i128 s[8];
+  u128 s2[8];
+  for (int i = 0; i < 8; ++i) { s[i] = 0; s2[i] = 0; }
+  for (int64_t j = 0; j < num; ++j) {
+    i128 tt = t[j], aa = a[j], bb = b[j], kk = k[j], qq = q[j];
+    i128 n8 = tt * (tt - 1) / 2 - kk;
+    i128 N[8];
+    N[0] = tt;
+    N[1] = aa + bb;
+    N[2] = kk;
+    N[3] = n8;
+    N[4] = tt * (aa + bb) - 4 * n8;
+    N[5] = qq;
+    N[6] = 2 * (aa * (aa - 1) / 2 + bb * (bb - 1) / 2) - tt * (aa + bb) + 4 * n8;
+    N[7] = aa * bb - qq;
+    for (int i = 0; i < 8; ++i) {
+      s[i] += N[i];
+      i128 m = N[i] < 0 ? -N[i] : N[i];
+      s2[i] += (u128)m * (u128)m;
+      if (n_out) n_out[j * 8 + i] = (int64_t)N[i];
+    }
+  }
+  for (int i = 0; i < 8; ++i) {
+    u128 us = (u128)s[i];
+    sums[2 * i] = (uint64_t)us;
+    sums[2 * i + 1] = (uint64_t)(us >> 64);
+    sq[2 * i] = (uint64_t)s2[i];
+    sq[2 * i + 1] = (uint64_t)(s2[i] >> 64);
+  }
+}
+
+/* ----------------------------------------------------------------------
+ * Uniform edge sampling (Algorithm 1 with a Bernoulli distribution F).
+ *
+ * The paper leaves the random source open; this oracle fixes it:
+ *   sm(x)  = SplitMix64 output for state x (Steele, Lea, Flood 2014):
+ *            z = x + 0x9e3779b97f4a7c15;
+ *            z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9;
+ *            z = (z ^ (z >> 27)) * 0x94d049bb133111eb;
+ *            return z ^ (z >> 31);
+ *   edge i (the i-th pair u < v in row-major CSR order) is kept iff
+ *            (sm(seed ^ sm(i)) >> 11) < threshold,
+ *   threshold = floor(p * 2^53) computed by the caller in double precision.
+ * Kept edges are written as (u, v) pairs in increasing i. Returns the
+ * number kept (all are counted even beyond max_pairs; only max_pairs are
+ * written).
+ * ---------------------------------------------------------------------- */
+uint64_t oracle_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+int64_t oracle_sample(int64_t n, const int64_t* row_ptr, const int32_t* col, uint64_t threshold,
+                      uint64_t seed, int32_t* out_pairs, int64_t max_pairs) {
+  int64_t kept = 0;
+  uint64_t i = 0;
+  for (int64_t u = 0; u < n; ++u) {
+    for (int64_t p = row_ptr[u]; p < row_ptr[u + 1]; ++p) {
+      int64_t v = col[p];
+      if (v <= u) continue;
+      uint64_t h = oracle_splitmix64(seed ^ oracle_splitmix64(i));
+      if ((h >> 11) < threshold) {
+        if (kept < max_pairs) {
+          out_pairs[2 * kept] = (int32_t)u;
+          out_pairs[2 * kept + 1] = (int32_t)v;
+        }
+        ++kept;
+      }
+      ++i;
+    }
+  }
+  return kept;
+}

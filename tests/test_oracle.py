@@ -1,0 +1,286 @@
+"""Pins for the CPU oracle: each check comes from something other than the
+oracle itself (Table 1, brute-force enumeration, closed forms, counting
+identities, a published RNG test vector, statistics)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import brute
+import oracle
+import synth
+
+CONNECTED = (3, 4, 7, 8, 9, 10, 11, 12)
+
+
+def oracle_exact(row_ptr, col):
+    return oracle.exact_counts(row_ptr, col)
+
+
+# ------------------------------------------------------------------ Table 1
+
+def test_table1_properties_of_graphlet_definitions():
+    """The edge lists used to build graphlets reproduce Table 1's columns."""
+    table = brute.load_table1()
+    for gid, (n, edges) in brute.GRAPHLET_EDGES.items():
+        got = brute.properties(n, edges)
+        want = table[gid]
+        assert got["n"] == want["n"], gid
+        assert round(got["rho"], 2) == pytest.approx(want["rho"], abs=0.006), gid
+        assert got["dmax"] == want["dmax"], gid
+        assert got["dbar"] == pytest.approx(want["dbar"], abs=0.006), gid
+        for key in ("tri", "core", "chi", "diam", "comp"):
+            assert got[key] == want[key], (gid, key)
+
+
+@pytest.mark.parametrize("gid", [3, 4, 7, 8, 9, 10, 11, 12])
+def test_each_connected_graphlet_counts_itself_once(gid):
+    n, edges = brute.GRAPHLET_EDGES[gid]
+    rp, col = brute.csr_from_edges(n, edges)
+    got = oracle_exact(rp, col)
+    want = brute.brute_counts(brute.adjacency(n, edges))
+    assert got[gid] == 1
+    for g in CONNECTED:
+        assert got[g] == want[g], g
+    if n == 4:
+        for g in (7, 8, 9, 10, 11, 12):
+            assert got[g] == (1 if g == gid else 0)
+
+
+# ------------------------------------------------------------------ brute force
+
+def _check_against_brute(A):
+    rp, col = brute.csr_from_adjacency(A)
+    if len(col) == 0:
+        return
+    got = oracle_exact(rp, col)
+    want = brute.brute_counts(A)
+    for g in CONNECTED:
+        assert got[g] == want[g], (g, got, want)
+
+
+def test_all_labelled_graphs_on_five_vertices():
+    pairs = list(itertools.combinations(range(5), 2))
+    for mask in range(1 << len(pairs)):
+        A = np.zeros((5, 5), dtype=np.int64)
+        for i, (a, b) in enumerate(pairs):
+            if mask >> i & 1:
+                A[a, b] = A[b, a] = 1
+        _check_against_brute(A)
+
+
+def test_random_labelled_graphs_on_six_vertices():
+    pairs = list(itertools.combinations(range(6), 2))
+    rng = np.random.default_rng(6)
+    for mask in rng.choice(1 << len(pairs), size=400, replace=False):
+        A = np.zeros((6, 6), dtype=np.int64)
+        for i, (a, b) in enumerate(pairs):
+            if int(mask) >> i & 1:
+                A[a, b] = A[b, a] = 1
+        _check_against_brute(A)
+
+
+@pytest.mark.parametrize("n,p,seed", [(8, 0.5, 1), (10, 0.3, 2), (10, 0.7, 3), (12, 0.4, 4),
+                                      (12, 0.6, 5), (12, 0.9, 6), (11, 0.2, 7)])
+def test_random_gnp_against_brute_force(n, p, seed):
+    rng = np.random.default_rng(seed)
+    U = np.triu(rng.random((n, n)) < p, 1)
+    A = (U | U.T).astype(np.int64)
+    _check_against_brute(A)
+
+
+def test_literal_algorithm4_disagrees_with_brute_force():
+    """Algorithm 4 as printed (testing lambda_2) counts the wrong thing; the
+    reading used by the oracle (testing S_v membership) is the one that
+    matches enumeration.  This is the planted mistake for the cycle count."""
+    rng = np.random.default_rng(11)
+    mismatches = 0
+    for trial in range(20):
+        n = 9
+        U = np.triu(rng.random((n, n)) < 0.45, 1)
+        A = (U | U.T).astype(np.int64)
+        rp, col = brute.csr_from_adjacency(A)
+        pairs = synth.upper_pairs(rp, col)
+        if len(pairs) == 0:
+            continue
+        lit = oracle.local_counts(rp, col, pairs, _literal_alg4=True)
+        ok = oracle.local_counts(rp, col, pairs)
+        s_lit, _ = oracle.numerators(lit)
+        s_ok, _ = oracle.numerators(ok)
+        want = brute.brute_counts(A)
+        assert s_ok[10] == 4 * want[10]
+        mismatches += s_lit[10] != 4 * want[10]
+    assert mismatches > 0
+
+
+# ------------------------------------------------------------------ closed forms
+
+@pytest.mark.parametrize("kind,args", [
+    ("complete", (4,)), ("complete", (5,)), ("complete", (7,)), ("complete", (9,)),
+    ("cycle", (3,)), ("cycle", (4,)), ("cycle", (5,)), ("cycle", (9,)), ("cycle", (40,)),
+    ("path", (2,)), ("path", (3,)), ("path", (4,)), ("path", (30,)),
+    ("star", (1,)), ("star", (2,)), ("star", (5,)), ("star", (40,)),
+    ("bipartite", (1, 1)), ("bipartite", (2, 2)), ("bipartite", (3, 4)), ("bipartite", (6, 9)),
+])
+def test_closed_forms(kind, args):
+    n, edges = brute.family_edges(kind, *args)
+    rp, col = brute.csr_from_edges(n, edges)
+    got = oracle_exact(rp, col)
+    want = brute.closed_form(kind, *args)
+    for g in CONNECTED:
+        assert got[g] == want[g], (kind, args, g)
+
+
+# ------------------------------------------------------------------ identities
+
+@pytest.mark.parametrize("maker", [
+    lambda: synth.er(120, 900, seed=5),
+    lambda: synth.chung_lu(400, 3000, 2.1, 150.0, seed=9),
+    lambda: synth.rgg(300, 0.12, seed=3),
+    lambda: synth.rmat(9, 8, seed=4),
+])
+def test_counting_identities(maker):
+    rp, col = maker()
+    c = oracle_exact(rp, col)
+    ids = brute.identities(rp, col)
+    assert ids["wedges"] == c[4] + 3 * c[3]
+    assert ids["claws"] == c[11] + c[9] + 2 * c[8] + 4 * c[7]
+    assert ids["paths3_raw"] - 3 * c[3] == c[12] + 2 * c[9] + 4 * c[10] + 6 * c[8] + 12 * c[7]
+    A = brute.adjacency_from_csr(rp, col)
+    A2 = A @ A
+    assert int(np.trace(A2 @ A)) == 6 * c[3]
+    tr4 = int(np.sum(A2 * A2))  # tr(A^4) = ||A^2||_F^2 for symmetric A
+    assert tr4 - 2 * ids["sum_d2"] + 2 * ids["M"] == 8 * (c[10] + c[8] + 3 * c[7])
+
+
+def test_triangle_sum_over_edges_is_three_per_triangle():
+    rp, col = synth.er(200, 2500, seed=8)
+    pairs = synth.upper_pairs(rp, col)
+    lc = oracle.local_counts(rp, col, pairs, four=False)
+    A = brute.adjacency_from_csr(rp, col)
+    assert int(lc["t"].sum()) == int(np.trace(A @ A @ A)) // 6 * 3
+    d = np.diff(rp)
+    # a + b + 2 t = d_u + d_v - 2 per edge
+    du, dv = d[pairs[:, 0]], d[pairs[:, 1]]
+    assert np.array_equal(lc["a"] + lc["b"] + 2 * lc["t"], du + dv - 2)
+
+
+def test_orientation_and_order_do_not_change_counts():
+    rp, col = synth.er(150, 1200, seed=12)
+    pairs = synth.upper_pairs(rp, col)
+    base = oracle.local_counts(rp, col, pairs)
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(len(pairs))
+    flipped = pairs[perm][:, ::-1].copy()
+    other = oracle.local_counts(rp, col, flipped)
+    for key in ("t", "k", "q"):
+        assert np.array_equal(base[key][perm], other[key])
+    assert np.array_equal((base["a"] + base["b"])[perm], other["a"] + other["b"])
+
+
+# ------------------------------------------------------------------ sampler
+
+def test_splitmix64_published_vector():
+    """SplitMix64 seeded with 1234567: the first five outputs published with
+    the reference generator's test suite."""
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+            4593380528125082431, 16408922859458223821]
+    state = 1234567
+    got = []
+    for _ in range(5):
+        got.append(oracle.splitmix64(state))
+        state = (state + 0x9E3779B97F4A7C15) % 2**64
+    assert got == want
+
+
+def test_sampler_limits_and_nesting():
+    rp, col = synth.er(300, 4000, seed=2)
+    allp = synth.upper_pairs(rp, col)
+    assert np.array_equal(oracle.sample(rp, col, 1.0, 7), allp)
+    assert len(oracle.sample(rp, col, 0.0, 7)) == 0
+    a = oracle.sample(rp, col, 0.1, 99)
+    b = oracle.sample(rp, col, 0.3, 99)
+    sa = {tuple(x) for x in a}
+    sb = {tuple(x) for x in b}
+    assert sa <= sb
+    assert np.array_equal(a, oracle.sample(rp, col, 0.1, 99))
+    assert not np.array_equal(a, oracle.sample(rp, col, 0.1, 100))
+
+
+def test_sampler_rate_is_binomial():
+    rp, col = synth.er(2000, 20000, seed=1)
+    m = len(col) // 2
+    for p in (0.01, 0.1, 0.5):
+        k = len(oracle.sample(rp, col, p, 12345))
+        sd = math.sqrt(m * p * (1 - p))
+        assert abs(k - m * p) < 5 * sd
+
+
+# ------------------------------------------------------------------ estimator
+
+def test_full_sample_gives_exact_counts_and_zero_variance():
+    rp, col = synth.er(100, 700, seed=21)
+    pairs = synth.upper_pairs(rp, col)
+    res = oracle.count_estimate(rp, col, pairs)
+    A = brute.adjacency_from_csr(rp, col)
+    want = brute.brute_counts(A)
+    for g in CONNECTED:
+        e = res["est"][g]
+        assert e["exact"] == want[g]
+        assert e["X"] == float(want[g])
+        assert e["V"] == 0.0
+        assert e["lb"] == e["ub"] == e["X"]
+
+
+def test_variance_matches_two_pass_sample_variance():
+    rp, col = synth.chung_lu(2000, 15000, 2.1, 300.0, seed=4)
+    m = len(col) // 2
+    pairs = oracle.sample(rp, col, 0.05, 3)
+    lc = oracle.local_counts(rp, col, pairs)
+    s, s2, nmat = oracle.numerators(lc, per_edge=True)
+    est = oracle.estimate(s, s2, m, len(pairs))
+    k = len(pairs)
+    for i, g in enumerate(oracle.GRAPHLETS):
+        y = nmat[:, i].astype(np.float64) / oracle.DENOM[g]
+        x_direct = m * y.mean()
+        v_direct = m * m * (1 - k / m) * y.var(ddof=1) / k
+        assert est[g]["X"] == pytest.approx(x_direct, rel=1e-12)
+        assert est[g]["V"] == pytest.approx(v_direct, rel=1e-9, abs=1e-9)
+
+
+def test_unbiased_and_covering_over_seeds():
+    """Mean of X over seeds approaches the exact count (unbiasedness,
+    Sec. 3.3) and the 95% interval covers it about 95% of the time
+    (Sec. 5.3)."""
+    rp, col = synth.er(400, 8000, seed=31)
+    m = len(col) // 2
+    exact = oracle_exact(rp, col)
+    pairs_all = synth.upper_pairs(rp, col)
+    lc_all = oracle.local_counts(rp, col, pairs_all)
+    seeds = range(300)
+    xs = {g: [] for g in CONNECTED}
+    cover = {g: 0 for g in CONNECTED}
+    vs = {g: [] for g in CONNECTED}
+    n_v = len(rp) - 1
+    keys_all = pairs_all[:, 0].astype(np.int64) * n_v + pairs_all[:, 1]
+    for sd in seeds:
+        smp = oracle.sample(rp, col, 0.1, sd)
+        idx = np.searchsorted(keys_all, smp[:, 0].astype(np.int64) * n_v + smp[:, 1])
+        sub = {key: val[idx] for key, val in lc_all.items()}
+        s, s2 = oracle.numerators(sub)
+        est = oracle.estimate(s, s2, m, len(idx))
+        for g in CONNECTED:
+            xs[g].append(est[g]["X"])
+            vs[g].append(est[g]["V"])
+            cover[g] += est[g]["lb"] <= exact[g] <= est[g]["ub"]
+    n = len(seeds)
+    for g in CONNECTED:
+        mean = float(np.mean(xs[g]))
+        se = math.sqrt(float(np.mean(vs[g])) / n)
+        assert abs(mean - exact[g]) <= 4.5 * se + 1e-9, (g, mean, exact[g], se)
+        if exact[g] >= 1000:
+            assert 0.89 * n <= cover[g] <= n, (g, cover[g])
+        emp = float(np.var(xs[g], ddof=1))
+        if exact[g] >= 1000:
+            assert 0.6 < emp / float(np.mean(vs[g])) < 1.6, g
