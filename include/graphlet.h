@@ -1,0 +1,188 @@
+/*
+ * graphlet.h -- C ABI of libgraphlet, a GB300 (sm_103a) implementation of
+ * the edge-centric graphlet estimator of Rossi, Zhou and Ahmed, "Estimation
+ * of Graphlet Statistics".
+ *
+ * The library counts, around each sampled edge e = (u, v) of a simple
+ * undirected graph, the connected 3- and 4-node graphlets that contain e
+ * (Algorithm 2: triangles T_e and 2-stars S_u, S_v; Algorithm 3: 4-cliques;
+ * Algorithm 4: 4-cycles), folds the per-edge counts into exact integer sums
+ * and turns them into the unbiased estimates of Sec. 3 with a variance and
+ * 95% bounds (Sec. 5.3).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA global-memory pointers on the current device;
+ *     host pointers are ordinary CPU memory. Each argument says which.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is enqueued on it; calls that return host results
+ *     synchronise that stream before returning.
+ *   - The caller owns every pointer it passes; the library never frees or
+ *     retains caller memory beyond the call, except the CSR arrays given to
+ *     gs_graph_create, which must stay valid until gs_graph_destroy.
+ *   - Every call returns a gs_status. On failure gs_last_error() returns a
+ *     message for the calling thread; outputs are then unspecified.
+ *   - Graph ids are int32; row offsets int64; edge counts int64.
+ *   - Graphlets are named by the paper's index G_i (Table 1). Connected ones
+ *     handled here: G3 triangle, G4 2-star, G7 4-clique, G8 chordal-cycle,
+ *     G9 tailed-triangle, G10 4-cycle, G11 3-star, G12 4-path. Arrays of 8
+ *     per-graphlet values use the order (3, 4, 7, 8, 9, 10, 11, 12).
+ */
+#ifndef GRAPHLET_H
+#define GRAPHLET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t gs_status;
+enum {
+  GS_OK = 0,
+  GS_EINVAL = 1,       /* bad argument (null pointer, negative size, bad mask, ...) */
+  GS_ENOTSORTED = 2,   /* an adjacency list is not strictly increasing */
+  GS_ESELFLOOP = 3,    /* a vertex lists itself */
+  GS_EDUP = 4,         /* an adjacency list repeats a neighbour */
+  GS_EASYM = 5,        /* u lists v but v does not list u */
+  GS_EEDGE = 6,        /* a sampled pair is out of range or not an edge */
+  GS_EDUPSAMPLE = 7,   /* an explicit sample lists the same edge twice */
+  GS_EOVERFLOW = 8,    /* a value does not fit its output type */
+  GS_ENOMEM = 9,       /* device allocation failed */
+  GS_EBUDGET = 10,     /* request exceeds a configured memory budget */
+  GS_ETIMEOUT = 11,    /* a bounded device-side wait expired */
+  GS_ECUDA = 12,       /* a CUDA runtime call failed (message has details) */
+  GS_ECAPACITY = 13    /* an output buffer is too small (size is reported) */
+};
+
+/* Graphlet mask: bit i set = graphlet G_i requested. */
+#define GS_G3 (1u << 3)
+#define GS_G4 (1u << 4)
+#define GS_G7 (1u << 7)
+#define GS_G8 (1u << 8)
+#define GS_G9 (1u << 9)
+#define GS_G10 (1u << 10)
+#define GS_G11 (1u << 11)
+#define GS_G12 (1u << 12)
+#define GS_THREE_NODE (GS_G3 | GS_G4)
+#define GS_CONNECTED (GS_G3 | GS_G4 | GS_G7 | GS_G8 | GS_G9 | GS_G10 | GS_G11 | GS_G12)
+
+/* gs_graph_create flags */
+#define GS_VALIDATE 1u  /* check sorted / simple / symmetric CSR on the device */
+
+/* Per-graphlet result flags */
+#define GS_F_COMPUTED 1u        /* graphlet was in the mask */
+#define GS_F_EXACT 2u           /* every edge sampled: exact[] is valid, V = 0 */
+#define GS_F_VAR_UNDEFINED 4u   /* fewer than 2 sampled edges: V, lb, ub are NaN */
+#define GS_F_OVERFLOW 8u        /* exact count does not fit uint64 */
+
+/* Exact integer sums over the sampled edges J (Sec. 3, Alg. 2 accumulators).
+ * For each graphlet i the per-edge numerator N_i(e) is the integer with
+ * X_i = (M / K) * sum_e N_i(e) / D_i, D = (3, 2, 6, 1, 2, 4, 6, 1):
+ *   N3 = t, N4 = a + b, N7 = k, N8 = C(t,2) - k, N9 = t(a+b) - 4 N8,
+ *   N10 = q, N11 = 2[C(a,2) + C(b,2)] - t(a+b) + 4 N8, N12 = a b - q,
+ * with t = |T_e|, a = |S_u|, b = |S_v|, k = 4-cliques through e,
+ * q = 4-cycles through e. sum[i] is a signed 128-bit integer stored as
+ * (low word, high word); sumsq[i] = sum N_i^2 as an unsigned 128-bit value. */
+typedef struct {
+  int64_t k;            /* number of sampled edges |J| */
+  int64_t m;            /* number of edges of the graph |E| */
+  uint32_t mask;        /* graphlets computed */
+  uint32_t reserved;
+  uint64_t sum[8][2];
+  uint64_t sumsq[8][2];
+} gs_sums;
+
+/* Estimates per graphlet, in the order (3, 4, 7, 8, 9, 10, 11, 12). */
+typedef struct {
+  double x[8];          /* X_i, Sec. 3 estimators with sigma = M / K */
+  double var[8];        /* estimated Var[X_i] (see gs_estimate) */
+  double lb[8];         /* X_i - z sqrt(var) (Sec. 5.3) */
+  double ub[8];         /* X_i + z sqrt(var) */
+  uint64_t exact[8];    /* sum N_i / D_i when K = M (flag GS_F_EXACT) */
+  uint32_t flags[8];    /* GS_F_* */
+} gs_result;
+
+typedef struct gs_graph gs_graph;
+typedef struct gs_workspace gs_workspace;
+
+/* Thread-local message describing the last failure of this thread. */
+const char* gs_last_error(void);
+
+/* Library version string. */
+const char* gs_version(void);
+
+/* Registers a simple undirected graph given as CSR (Sec. 3.1: ordered
+ * neighbour sets). d_row_ptr: device int64[n+1], d_col: device int32[nnz],
+ * nnz = 2|E|, every list strictly increasing, both orientations present, no
+ * self-loops. The arrays are borrowed (not copied) and must outlive the
+ * handle. With GS_VALIDATE the structure is checked on the device and
+ * GS_ENOTSORTED / GS_ESELFLOOP / GS_EDUP / GS_EASYM / GS_EINVAL returned.
+ * Builds the per-graph index (upper-edge offsets for the sampler, hub
+ * adjacency bitmaps and the hub co-degree table) in library-owned device
+ * memory; hub_budget_bytes bounds that memory (0 = default 1 GiB).
+ * Synchronises `stream`. */
+gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n, int64_t nnz,
+                          uint32_t flags, uint64_t hub_budget_bytes, void* stream,
+                          gs_graph** out);
+
+/* Frees the library-owned per-graph index. The CSR arrays are not freed. */
+gs_status gs_graph_destroy(gs_graph* g);
+
+/* Host outputs: vertex count, undirected edge count, maximum degree, number
+ * of hub vertices with adjacency bitmaps and with co-degree table rows. Any
+ * output pointer may be NULL. */
+gs_status gs_graph_info(const gs_graph* g, int64_t* n, int64_t* m, int64_t* max_degree,
+                        int64_t* bitmap_hubs, int64_t* table_hubs);
+
+/* Library-owned scratch for gs_sample / gs_count. One workspace serves one
+ * stream at a time; it grows on demand (cudaMalloc, after synchronising the
+ * stream it was last used on) and is released by gs_workspace_destroy. */
+gs_status gs_workspace_create(gs_workspace** out);
+gs_status gs_workspace_destroy(gs_workspace* ws);
+/* Host output: bytes currently held by the workspace. */
+gs_status gs_workspace_bytes(const gs_workspace* ws, uint64_t* bytes);
+
+/* Uniform edge sampling (Algorithm 1 with a Bernoulli distribution):
+ * canonical edge i (the i-th pair u < v in row-major CSR order) is kept iff
+ * (sm(seed ^ sm(i)) >> 11) < floor(fraction * 2^53), sm = SplitMix64 output
+ * function. Kept edges are written in increasing i to d_pairs (device
+ * int32[2*max_k], (u, v) with u < v). *k_out (host) receives the number
+ * kept; GS_ECAPACITY if it exceeds max_k (then nothing useful is written).
+ * fraction must lie in [0, 1]. Synchronises `stream`. */
+gs_status gs_sample(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
+                    int32_t* d_pairs, int64_t max_k, int64_t* k_out, void* stream);
+
+/* Local counting over a sampled edge set J (Algorithms 2-4) and exact
+ * folding of the per-edge numerators into *h_sums (host).
+ * d_pairs: device int32[2*k], each pair an edge in either orientation, no
+ * edge twice (GS_EDUPSAMPLE); NULL with k = |E| means J = all edges. k = 0
+ * is an empty sample (d_pairs not read; all sums zero).
+ * mask: graphlets wanted (GS_* bits); 4-clique work runs only if G7, G8,
+ * G9 or G11 is set, 4-cycle work only if G10 or G12 is set.
+ * d_per_edge: optional device int64[3*k]; receives (t, k, q) per pair in
+ * input order (k, q are 0 when their pass did not run).
+ * Synchronises `stream`. */
+gs_status gs_count(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs, int64_t k,
+                   uint32_t mask, int64_t* d_per_edge, gs_sums* h_sums, void* stream);
+
+/* Estimates from exact sums (host only, no GPU work):
+ *   X_i   = (M / K) * sum N_i / D_i                  (Sec. 3, sigma = |E|/|J|)
+ *   var_i = M (M - K) (K sumsq_i - sum_i^2) / (K^2 (K - 1) D_i^2)
+ *           -- the without-replacement design variance of the expansion
+ *           estimator; the paper states bounds from Var[X] (Sec. 5.3) but
+ *           prints no formula for it, this is the library's choice.
+ *   lb_i, ub_i = X_i -/+ z sqrt(var_i), z = 1.96 for 95% (Sec. 5.3).
+ * K = M gives var = 0 and exact counts. */
+gs_status gs_estimate(const gs_sums* s, double z, gs_result* out);
+
+/* Convenience: gs_sample (fraction < 1) or all edges (fraction == 1), then
+ * gs_count and gs_estimate. *k_out (host, may be NULL) receives |J|. */
+gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
+                            uint32_t mask, double z, gs_result* out, int64_t* k_out,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAPHLET_H */

@@ -1,0 +1,146 @@
+// Shared declarations of libgraphlet's CUDA sources (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "graphlet.h"
+
+namespace gs {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const char* fmt, ...);
+gs_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define GS_CUDA(call)                                                       \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) return gs::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define GS_TRY(call)                      \
+  do {                                    \
+    gs_status s_ = (call);                \
+    if (s_ != GS_OK) return s_;           \
+  } while (0)
+
+// Device-side error record: the first failing kernel stores a status code
+// and the index of the offending element.
+struct DevError {
+  int32_t code;
+  int32_t pad;
+  int64_t index;
+};
+
+__device__ __forceinline__ void raise_error(DevError* err, int32_t code, int64_t index) {
+  if (atomicCAS(&err->code, 0, code) == 0) err->index = index;
+}
+
+// ---------------------------------------------------------------- graph
+
+// Device view of a registered graph plus its hub index.
+struct DevGraph {
+  const int64_t* row_ptr;   // [n+1]
+  const int32_t* col;       // [nnz], sorted per row
+  int64_t n;
+  int64_t nnz;
+  // adjacency bitmaps of the highest-degree vertices ("hubs")
+  const int32_t* bm_slot;   // [n] bitmap slot of v, -1 if none (NULL if no bitmaps)
+  const uint32_t* bm_bits;  // [bm_count][bm_words]
+  int64_t bm_words;         // ceil(n / 32)
+  int64_t bm_count;
+  // co-degree table |N(x) cap N(y)| for the highest-degree vertices
+  const int32_t* tb_slot;   // [n] table slot of v, -1 if none (NULL if no table)
+  const uint32_t* tb_codeg; // [tb_count][tb_count]
+  int64_t tb_count;
+};
+
+// Membership of x in the sorted list a[0..len): branch-free halving search.
+// Invariant: if x is present it lies in [base, base + len).
+__device__ __forceinline__ bool sorted_contains(const int32_t* __restrict__ a, int64_t len,
+                                                int32_t x) {
+  if (len <= 0) return false;
+  const int32_t* base = a;
+  while (len > 1) {
+    int64_t half = len >> 1;
+    base = (__ldg(base + half) <= x) ? base + half : base;
+    len -= half;
+  }
+  return __ldg(base) == x;
+}
+
+// Membership of x in N(y): bitmap test for hubs, halving search otherwise.
+__device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64_t base_y,
+                                             int64_t deg_y, int32_t x) {
+  if (g.bm_slot != nullptr) {
+    int32_t s = __ldg(g.bm_slot + y);
+    if (s >= 0) {
+      uint32_t w = __ldg(g.bm_bits + (int64_t)s * g.bm_words + (x >> 5));
+      return (w >> (x & 31)) & 1u;
+    }
+  }
+  return sorted_contains(g.col + base_y, deg_y, x);
+}
+
+// ---------------------------------------------------------------- scan
+
+// Exclusive prefix sum of in[0..count) into out[0..count], out[count] = total.
+// `in` and `out` may alias. tmp must hold scan_tmp_elems(count) int64.
+int64_t scan_tmp_elems(int64_t count);
+gs_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t count, int64_t* tmp,
+                             cudaStream_t stream);
+
+// Grid size for grid-stride kernels: a multiple of the SM count.
+int grid_for(int64_t work_items, int threads_per_block, int blocks_per_sm);
+int sm_count();
+
+}  // namespace gs
+
+// ---------------------------------------------------------------- handles
+
+struct gs_graph {
+  gs::DevGraph dev;
+  int64_t m;            // undirected edges = nnz / 2
+  int64_t max_degree;
+  int64_t* up_ptr;      // [n]   index in col of the first neighbour > v
+  int64_t* edge_off;    // [n+1] canonical (u < v) edge offsets per row
+  int32_t* bm_slot;
+  uint32_t* bm_bits;
+  int32_t* tb_slot;
+  uint32_t* tb_codeg;
+};
+
+struct gs_workspace {
+  void* buf[4];
+  size_t cap[4];
+  cudaStream_t last_stream;
+  int device;
+};
+
+namespace gs {
+// Returns a device buffer of at least `bytes` in slot `slot` of the
+// workspace, growing it (after synchronising the stream it was last used
+// on) when needed. Previously held contents of that slot are lost on growth.
+gs_status ws_reserve(gs_workspace* ws, int slot, size_t bytes, cudaStream_t stream, void** out);
+gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
+                      int32_t* d_pairs, int64_t max_k, int64_t* k_out, int32_t** pairs_out,
+                      cudaStream_t stream);
+}  // namespace gs
+
+// Byte-offset bump allocator inside one workspace slot.
+struct Carve {
+  char* base;
+  size_t used;
+  template <class T>
+  T* take(int64_t count) {
+    size_t bytes = ((size_t)(count > 0 ? count : 1) * sizeof(T) + 255) & ~(size_t)255;
+    T* p = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+  template <class T>
+  static size_t bytes_for(int64_t count) {
+    return ((size_t)(count > 0 ? count : 1) * sizeof(T) + 255) & ~(size_t)255;
+  }
+};

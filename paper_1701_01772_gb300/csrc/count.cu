@@ -1,0 +1,630 @@
+// Edge-centric local counting over a sampled edge set J (Algorithms 2-4)
+// and the exact fold of the per-edge numerators (Sec. 3).
+//
+// For an edge e = (u, v) with d_u <= d_v (ties: smaller id is u), let
+// T = N(u) cap N(v), S_u = N(u) \ {v} \ T, S_v = N(v) \ {u} \ T. The paper's
+// per-edge quantities are computed as
+//   t  = |T|                                    (Algorithm 2)
+//   2k = sum_{w in T}   |N(w) cap T|            (Algorithm 3, ordered pairs)
+//   q  = sum_{w in S_u} (|N(w) cap N(v)| - |N(w) cap T| - 1)   (Algorithm 4)
+// The last line restates "pairs (w in S_u, r in S_v) with w ~ r": for w in
+// S_u the common neighbours of w and v are u, the members of T adjacent to
+// w, and the members of S_v adjacent to w. It lets |N(w) cap N(v)| come from
+// a precomputed co-degree table when both w and v are hubs.
+//
+// GPU structure (all work is flattened so that per-edge cost skew -- power
+// law degrees -- does not serialise on one warp):
+//   prep     one thread per pair: canonical orientation, edge check,
+//            duplicate check, per-edge position count d_u (padded to 32
+//            when 4-node work follows).
+//   tri      positions of N(u) are split evenly over all warps; each lane
+//            tests one x in N(u) for membership in N(v). Ballots give t and,
+//            for 4-node work, one 32-bit word of "x in T" flags per chunk of
+//            32 positions.
+//   compact  T lists written in order (one warp per edge).
+//   cost     per chunk of 32 positions (items w = N(u)[i]): membership-test
+//            count of each item (iterate the shorter list, test in the
+//            longer); constant terms (-1 per S_u item, table co-degrees)
+//            added directly.
+//   quad     chunks are cut into tasks of kTaskProbes tests; tasks are split
+//            evenly over all warps; inside a task lanes take consecutive
+//            tests and find their item by a search over the warp's scanned
+//            costs (load-balanced search).
+//   fold     per edge numerators N_i in 128-bit, block partial sums, one
+//            final fixed-order pass.
+#include <string.h>
+
+#include "common.cuh"
+
+namespace gs {
+
+constexpr int kThreads = 256;
+constexpr int kBlocksPerSm = 4;
+constexpr int64_t kTaskProbes = 1024;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kEmpty = ~0ull;
+
+__device__ __forceinline__ int64_t deg_of(const int64_t* __restrict__ row_ptr, int32_t v,
+                                          int64_t* base) {
+  int64_t s = __ldg(row_ptr + v), e = __ldg(row_ptr + v + 1);
+  *base = s;
+  return e - s;
+}
+
+// Last index e in [0, count) with off[e] <= p (off[0] = 0 <= p).
+__device__ __forceinline__ int64_t last_le(const int64_t* __restrict__ off, int64_t count,
+                                           int64_t p) {
+  int64_t lo = 0, len = count;
+  while (len > 1) {
+    int64_t half = len >> 1;
+    lo = (__ldg(off + lo + half) <= p) ? lo + half : lo;
+    len -= half;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------- prep
+
+__global__ void k_all_pairs(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const int64_t* __restrict__ up_ptr,
+                            const int64_t* __restrict__ edge_off, int64_t n,
+                            int32_t* __restrict__ pairs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    int64_t s = up_ptr[u], e = row_ptr[u + 1], o = edge_off[u];
+    for (int64_t p = s + lane; p < e; p += 32) {
+      int64_t i = o + (p - s);
+      pairs[2 * i] = (int32_t)u;
+      pairs[2 * i + 1] = col[p];
+    }
+  }
+}
+
+__global__ void k_prep(DevGraph g, const int32_t* __restrict__ pairs, int64_t K, int pad,
+                       unsigned long long* __restrict__ dup_table, int64_t dup_mask,
+                       int2* __restrict__ uv, int64_t* __restrict__ len, DevError* err) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x = pairs[2 * e], y = pairs[2 * e + 1];
+    len[e] = 0;
+    uv[e] = make_int2(0, 0);
+    if (x < 0 || y < 0 || x >= g.n || y >= g.n || x == y) {
+      raise_error(err, GS_EEDGE, e);
+      continue;
+    }
+    int64_t bx, by;
+    int64_t dx = deg_of(g.row_ptr, x, &bx), dy = deg_of(g.row_ptr, y, &by);
+    bool x_small = dx < dy || (dx == dy && x < y);
+    int32_t u = x_small ? x : y, v = x_small ? y : x;
+    int64_t du = x_small ? dx : dy, bu = x_small ? bx : by;
+    if (!sorted_contains(g.col + bu, du, v)) {
+      raise_error(err, GS_EEDGE, e);
+      continue;
+    }
+    if (dup_table != nullptr) {
+      uint64_t key = ((uint64_t)(uint32_t)min(x, y) << 32) | (uint32_t)max(x, y);
+      uint64_t h = mix64(key) & (uint64_t)dup_mask;
+      for (int64_t probe = 0; probe <= dup_mask; ++probe) {
+        unsigned long long prev = atomicCAS(dup_table + h, kEmpty, (unsigned long long)key);
+        if (prev == kEmpty) break;
+        if (prev == key) {
+          raise_error(err, GS_EDUPSAMPLE, e);
+          break;
+        }
+        h = (h + 1) & (uint64_t)dup_mask;
+      }
+    }
+    uv[e] = make_int2(u, v);
+    len[e] = pad ? ((du + 31) & ~(int64_t)31) : du;
+  }
+}
+
+// ---------------------------------------------------------------- tri
+// Positions [0, P) of the concatenated (padded) N(u) lists are split into
+// equal contiguous ranges of 32-position groups, one range per warp.
+template <bool kPad>
+__global__ void __launch_bounds__(kThreads) k_tri(DevGraph g, const int2* __restrict__ uv,
+                                                  const int64_t* __restrict__ off, int64_t K,
+                                                  unsigned long long* __restrict__ t,
+                                                  uint32_t* __restrict__ tbits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t P = __ldg(off + K);
+  const int64_t groups = (P + 31) >> 5;
+  const int64_t per = (groups + warps - 1) / warps;
+  const int64_t g0 = warp * per, g1 = min(groups, g0 + per);
+  if (g0 >= g1) return;
+  int64_t e = last_le(off, K, g0 * 32);
+  for (int64_t gi = g0; gi < g1; ++gi) {
+    const int64_t p = gi * 32 + lane;
+    int64_t le = e;
+    while (le + 1 < K && __ldg(off + le + 1) <= p) ++le;
+    bool hit = false;
+    if (p < P) {
+      int2 pr = uv[le];
+      int64_t bu, bv;
+      int64_t du = deg_of(g.row_ptr, pr.x, &bu), dv = deg_of(g.row_ptr, pr.y, &bv);
+      int64_t i = p - __ldg(off + le);
+      if (i < du) {
+        int32_t x = __ldg(g.col + bu + i);
+        hit = x != pr.y && adj_contains(g, pr.y, bv, dv, x);
+      }
+    }
+    const unsigned ball = __ballot_sync(kFull, hit);
+    if (kPad && lane == 0) tbits[gi] = ball;
+    const unsigned grp = __match_any_sync(kFull, (unsigned long long)le);
+    const int cnt = __popc(ball & grp);
+    if (cnt && lane == __ffs(grp) - 1) atomicAdd(t + le, (unsigned long long)cnt);
+    e = __shfl_sync(kFull, le, 31);
+  }
+}
+
+// ---------------------------------------------------------------- compact T
+
+__global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off,
+                            const int64_t* __restrict__ toff, int64_t K,
+                            const uint32_t* __restrict__ tbits, int32_t* __restrict__ T) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < K; e += warps) {
+    int2 pr = uv[e];
+    int64_t bu;
+    int64_t du = deg_of(g.row_ptr, pr.x, &bu);
+    int64_t words = (du + 31) >> 5, w0 = off[e] >> 5, pos = toff[e];
+    for (int64_t w = 0; w < words; ++w) {
+      uint32_t word = __ldg(tbits + w0 + w);
+      if ((word >> lane) & 1u)
+        T[pos + __popc(word & ((1u << lane) - 1u))] = __ldg(g.col + bu + w * 32 + lane);
+      pos += __popc(word);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- items
+// One item per position of a 32-position chunk: w = N(u)[i].
+struct Item {
+  int64_t bw;     // row offset of w
+  int32_t dw;     // degree of w
+  int32_t w;
+  int32_t cx;     // tests for |N(w) cap T|
+  int32_t cy;     // tests for |N(w) cap N(v)|
+  int32_t is_t;   // w in T
+  int32_t valid;  // position holds a neighbour other than v
+  int64_t qconst; // constant q contribution (-1 per S_u item, + table co-degree)
+};
+
+struct EdgeCtx {
+  int64_t e;
+  int32_t u, v;
+  int64_t bu, du, bv, dv;
+  int64_t te, toff;
+};
+
+__device__ __forceinline__ void load_edge(const DevGraph& g, const int2* __restrict__ uv,
+                                          const unsigned long long* __restrict__ t,
+                                          const int64_t* __restrict__ toff, int64_t e,
+                                          EdgeCtx& c) {
+  int2 pr = uv[e];
+  c.e = e;
+  c.u = pr.x;
+  c.v = pr.y;
+  c.du = deg_of(g.row_ptr, pr.x, &c.bu);
+  c.dv = deg_of(g.row_ptr, pr.y, &c.bv);
+  c.te = (int64_t)t[e];
+  c.toff = toff[e];
+}
+
+__device__ __forceinline__ uint32_t table_codeg(const DevGraph& g, int32_t a, int32_t b) {
+  if (g.tb_slot == nullptr) return 0;
+  int32_t sa = __ldg(g.tb_slot + a), sb = __ldg(g.tb_slot + b);
+  if (sa < 0 || sb < 0) return 0;
+  return __ldg(g.tb_codeg + (int64_t)sa * g.tb_count + sb) + 1u;  // +1: "present" marker
+}
+
+__device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c, int64_t i,
+                                          uint32_t tword, int lane, bool need_k, bool need_q,
+                                          Item& it) {
+  it.valid = 0;
+  it.cx = it.cy = 0;
+  it.qconst = 0;
+  it.is_t = (tword >> lane) & 1u;
+  it.w = -1;
+  it.dw = 0;
+  it.bw = 0;
+  if (i < c.du) {
+    it.w = __ldg(g.col + c.bu + i);
+    it.valid = it.w != c.v;
+  }
+  if (!it.valid) return;
+  it.dw = (int32_t)deg_of(g.row_ptr, it.w, &it.bw);
+  const bool want_x = it.is_t ? need_k : need_q;
+  if (want_x) it.cx = (int32_t)min((int64_t)it.dw, c.te);
+  if (!it.is_t && need_q) {
+    uint32_t tc = table_codeg(g, it.w, c.v);
+    if (tc != 0) {
+      it.qconst = (int64_t)(tc - 1u) - 1;
+    } else {
+      it.cy = (int32_t)min((int64_t)it.dw, c.dv);
+      it.qconst = -1;
+    }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// Chunk costs: membership tests per chunk and the number of tasks it needs.
+// Also adds the constant part of q. Same warp partition as k_tri.
+__global__ void __launch_bounds__(kThreads)
+    k_chunk_cost(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
+                 const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
+                 const uint32_t* __restrict__ tbits, int need_k, int need_q,
+                 int64_t* __restrict__ chunk_cost, int64_t* __restrict__ task_cnt,
+                 unsigned long long* __restrict__ q) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t P = __ldg(off + K);
+  const int64_t groups = P >> 5;  // padded: P is a multiple of 32
+  const int64_t per = (groups + warps - 1) / warps;
+  const int64_t g0 = warp * per, g1 = min(groups, g0 + per);
+  if (g0 >= g1) return;
+  int64_t e = last_le(off, K, g0 * 32);
+  EdgeCtx c;
+  load_edge(g, uv, t, toff, e, c);
+  for (int64_t gi = g0; gi < g1; ++gi) {
+    while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
+    if (e != c.e) load_edge(g, uv, t, toff, e, c);
+    Item it;
+    load_item(g, c, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k, need_q, it);
+    int64_t cost = warp_sum<int64_t>((int64_t)it.cx + it.cy);
+    int64_t qc = warp_sum<int64_t>(it.qconst);
+    if (lane == 0) {
+      chunk_cost[gi] = cost;
+      task_cnt[gi] = (cost + kTaskProbes - 1) / kTaskProbes;
+      if (qc != 0) atomicAdd(q + e, (unsigned long long)qc);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- quad
+
+__global__ void __launch_bounds__(kThreads)
+    k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
+           const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
+           const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
+           const int64_t* __restrict__ chunk_cost, const int64_t* __restrict__ task_off,
+           int64_t groups, int need_k, int need_q, unsigned long long* __restrict__ k2,
+           unsigned long long* __restrict__ q) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t NT = __ldg(task_off + groups);
+  const int64_t per = (NT + warps - 1) / warps;
+  const int64_t t0 = warp * per, t1 = min(NT, t0 + per);
+  if (t0 >= t1) return;
+  int64_t gi = last_le(task_off, groups, t0);
+  int64_t e = last_le(off, K, gi * 32);
+  EdgeCtx c;
+  load_edge(g, uv, t, toff, e, c);
+  int64_t cur = -1;
+  Item it;
+  int64_t start = 0, ctotal = 0;
+  unsigned long long acc_k = 0;
+  long long acc_q = 0;
+  for (int64_t task = t0; task < t1; ++task) {
+    while (gi + 1 < groups && __ldg(task_off + gi + 1) <= task) ++gi;
+    if (gi != cur) {
+      // flush the previous chunk's counts to its edge
+      unsigned long long sk = warp_sum<unsigned long long>(acc_k);
+      long long sq = warp_sum<long long>(acc_q);
+      if (lane == 0 && cur >= 0) {
+        if (sk) atomicAdd(k2 + c.e, sk);
+        if (sq) atomicAdd(q + c.e, (unsigned long long)sq);
+      }
+      acc_k = 0;
+      acc_q = 0;
+      while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
+      if (e != c.e) load_edge(g, uv, t, toff, e, c);
+      load_item(g, c, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k, need_q,
+                it);
+      int64_t mine = (int64_t)it.cx + it.cy, incl = mine;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        int64_t y = __shfl_up_sync(kFull, incl, d);
+        if (lane >= d) incl += y;
+      }
+      start = incl - mine;
+      ctotal = __shfl_sync(kFull, incl, 31);
+      cur = gi;
+    }
+    const int64_t sub = task - __ldg(task_off + gi);
+    const int64_t lo = sub * kTaskProbes, hi = min(ctotal, lo + kTaskProbes);
+    for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+      const int64_t rr = r0 + lane;
+      // item j = last lane whose start <= rr
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        int64_t s = __shfl_sync(kFull, start, j + step);
+        if (s <= rr) j += step;
+      }
+      const int64_t sj = __shfl_sync(kFull, start, j);
+      const int64_t bw = __shfl_sync(kFull, it.bw, j);
+      const int32_t dw = __shfl_sync(kFull, it.dw, j);
+      const int32_t w = __shfl_sync(kFull, it.w, j);
+      const int32_t cx = __shfl_sync(kFull, it.cx, j);
+      const int32_t is_t = __shfl_sync(kFull, it.is_t, j);
+      if (rr < hi) {
+        int64_t o = rr - sj;
+        if (o < cx) {  // |N(w) cap T|
+          bool hit;
+          if ((int64_t)dw <= c.te) {
+            hit = sorted_contains(T + c.toff, c.te, __ldg(g.col + bw + o));
+          } else {
+            hit = adj_contains(g, w, bw, dw, __ldg(T + c.toff + o));
+          }
+          if (hit) {
+            if (is_t) ++acc_k;
+            else --acc_q;
+          }
+        } else {  // |N(w) cap N(v)|
+          o -= cx;
+          bool hit;
+          if ((int64_t)dw <= c.dv) {
+            hit = adj_contains(g, c.v, c.bv, c.dv, __ldg(g.col + bw + o));
+          } else {
+            hit = adj_contains(g, w, bw, dw, __ldg(g.col + c.bv + o));
+          }
+          if (hit) ++acc_q;
+        }
+      }
+    }
+  }
+  unsigned long long sk = warp_sum<unsigned long long>(acc_k);
+  long long sq = warp_sum<long long>(acc_q);
+  if (lane == 0 && cur >= 0) {
+    if (sk) atomicAdd(k2 + c.e, sk);
+    if (sq) atomicAdd(q + c.e, (unsigned long long)sq);
+  }
+}
+
+// ---------------------------------------------------------------- fold
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int o) {
+  unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+  lo = __shfl_down_sync(kFull, lo, o);
+  hi = __shfl_down_sync(kFull, hi, o);
+  return ((u128)hi << 64) | lo;
+}
+
+// Per-edge numerators (order 3,4,7,8,9,10,11,12) and 128-bit block sums:
+// part[block][0..7] = sum N_i (two's complement), part[block][8..15] = sum N_i^2.
+__global__ void __launch_bounds__(kThreads)
+    k_fold(DevGraph g, const int2* __restrict__ uv, int64_t K,
+           const unsigned long long* __restrict__ t, const unsigned long long* __restrict__ k2,
+           const unsigned long long* __restrict__ q, int64_t* __restrict__ per_edge,
+           u128* __restrict__ part) {
+  u128 acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int2 pr = uv[e];
+    int64_t bu, bv;
+    const i128 du = deg_of(g.row_ptr, pr.x, &bu), dv = deg_of(g.row_ptr, pr.y, &bv);
+    const i128 tt = (i128)t[e];
+    const i128 kk = k2 != nullptr ? (i128)(k2[e] >> 1) : 0;
+    const i128 qq = q != nullptr ? (i128)(long long)q[e] : 0;
+    const i128 a = du - 1 - tt, b = dv - 1 - tt;
+    const i128 n8 = tt * (tt - 1) / 2 - kk;
+    i128 N[8];
+    N[0] = tt;
+    N[1] = a + b;
+    N[2] = kk;
+    N[3] = n8;
+    N[4] = tt * (a + b) - 4 * n8;
+    N[5] = qq;
+    N[6] = 2 * (a * (a - 1) / 2 + b * (b - 1) / 2) - tt * (a + b) + 4 * n8;
+    N[7] = a * b - qq;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      acc[i] += (u128)N[i];
+      u128 m = (u128)(N[i] < 0 ? -N[i] : N[i]);
+      acc[8 + i] += m * m;
+    }
+    if (per_edge != nullptr) {
+      per_edge[3 * e] = (int64_t)tt;
+      per_edge[3 * e + 1] = (int64_t)kk;
+      per_edge[3 * e + 2] = (int64_t)qq;
+    }
+  }
+  __shared__ u128 red[kThreads / 32][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    u128 v = acc[i];
+    for (int o = 16; o > 0; o >>= 1) v += shfl_down_u128(v, o);
+    if (lane == 0) red[warp][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) {
+    u128 s = 0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w][threadIdx.x];
+    part[(int64_t)blockIdx.x * 16 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_fold_final(const u128* __restrict__ part, int blocks,
+                             unsigned long long* __restrict__ out) {
+  if (threadIdx.x < 16) {
+    u128 s = 0;
+    for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * 16 + threadIdx.x];
+    out[2 * threadIdx.x] = (unsigned long long)s;
+    out[2 * threadIdx.x + 1] = (unsigned long long)(s >> 64);
+  }
+}
+
+}  // namespace gs
+
+// =================================================================== C ABI
+using namespace gs;
+
+static gs_status fetch_error(DevError* d_err, cudaStream_t stream, const char* what) {
+  DevError h;
+  GS_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  if (h.code != 0) {
+    const char* kind = h.code == GS_EDUPSAMPLE ? "edge sampled twice"
+                       : h.code == GS_EEDGE    ? "sampled pair is out of range or not an edge"
+                                               : "invalid input";
+    set_error("%s: %s (pair %lld)", what, kind, (long long)h.index);
+    return h.code;
+  }
+  return GS_OK;
+}
+
+static const uint32_t kKnownMask = GS_CONNECTED;
+
+extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs,
+                              int64_t K, uint32_t mask, int64_t* d_per_edge, gs_sums* h_sums,
+                              void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (gr == nullptr || ws == nullptr || h_sums == nullptr || K < 0 || mask == 0 ||
+      (mask & ~kKnownMask) != 0) {
+    set_error("gs_count: invalid arguments (mask must be a non-empty subset of GS_CONNECTED)");
+    return GS_EINVAL;
+  }
+  memset(h_sums, 0, sizeof(*h_sums));
+  h_sums->k = K;
+  h_sums->m = gr->m;
+  h_sums->mask = mask;
+  if (K == 0) return GS_OK;  // empty sample (d_pairs is not read)
+  if (d_pairs == nullptr && K != gr->m) {
+    set_error("gs_count: with d_pairs = NULL, k must equal the edge count %lld", (long long)gr->m);
+    return GS_EINVAL;
+  }
+  const DevGraph& g = gr->dev;
+  const bool need_k = (mask & (GS_G7 | GS_G8 | GS_G9 | GS_G11)) != 0;
+  const bool need_q = (mask & (GS_G10 | GS_G12)) != 0;
+  const bool four = need_k || need_q;
+  const int sms = sm_count();
+  const int fold_blocks = grid_for(K, kThreads, 2);
+  const bool check_dup = d_pairs != nullptr;
+  int64_t dup_cap = 1;
+  while (dup_cap < 2 * K) dup_cap <<= 1;
+
+  // ---- slot 0: per-edge arrays
+  size_t b0 = Carve::bytes_for<DevError>(1) + Carve::bytes_for<unsigned long long>(32) +
+              (d_pairs == nullptr ? Carve::bytes_for<int32_t>(2 * K) : 0) +
+              Carve::bytes_for<int2>(K) + Carve::bytes_for<int64_t>(K + 1) * 2 +
+              Carve::bytes_for<unsigned long long>(K) * 3 +
+              Carve::bytes_for<int64_t>(scan_tmp_elems(K + 1)) +
+              (check_dup ? Carve::bytes_for<unsigned long long>(dup_cap) : 0) +
+              Carve::bytes_for<u128>((int64_t)fold_blocks * 16);
+  void* base0 = nullptr;
+  GS_TRY(ws_reserve(ws, 0, b0, stream, &base0));
+  Carve c0{(char*)base0, 0};
+  DevError* d_err = c0.take<DevError>(1);
+  unsigned long long* d_sums = c0.take<unsigned long long>(32);
+  int32_t* pairs_all = d_pairs == nullptr ? c0.take<int32_t>(2 * K) : nullptr;
+  int2* uv = c0.take<int2>(K);
+  int64_t* off = c0.take<int64_t>(K + 1);
+  int64_t* toff = c0.take<int64_t>(K + 1);
+  unsigned long long* t = c0.take<unsigned long long>(K);
+  unsigned long long* k2 = c0.take<unsigned long long>(K);
+  unsigned long long* q = c0.take<unsigned long long>(K);
+  int64_t* tmp0 = c0.take<int64_t>(scan_tmp_elems(K + 1));
+  unsigned long long* dup = check_dup ? c0.take<unsigned long long>(dup_cap) : nullptr;
+  u128* part = c0.take<u128>((int64_t)fold_blocks * 16);
+
+  GS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(DevError), stream));
+  GS_CUDA(cudaMemsetAsync(t, 0, sizeof(unsigned long long) * K, stream));
+  if (four) {
+    GS_CUDA(cudaMemsetAsync(k2, 0, sizeof(unsigned long long) * K, stream));
+    GS_CUDA(cudaMemsetAsync(q, 0, sizeof(unsigned long long) * K, stream));
+  }
+  if (check_dup) GS_CUDA(cudaMemsetAsync(dup, 0xff, sizeof(unsigned long long) * dup_cap, stream));
+  const int32_t* pairs = d_pairs;
+  if (pairs == nullptr) {
+    k_all_pairs<<<grid_for(g.n * 32, kThreads, 8), kThreads, 0, stream>>>(
+        g.row_ptr, g.col, gr->up_ptr, gr->edge_off, g.n, pairs_all);
+    pairs = pairs_all;
+  }
+  k_prep<<<grid_for(K, kThreads, 8), kThreads, 0, stream>>>(g, pairs, K, four ? 1 : 0, dup,
+                                                            dup_cap - 1, uv, off, d_err);
+  GS_TRY(exclusive_scan_i64(off, off, K, tmp0, stream));
+  int64_t P = 0;
+  GS_CUDA(cudaMemcpyAsync(&P, off + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+  GS_TRY(fetch_error(d_err, stream, "gs_count"));
+
+  // ---- slot 1: per-position arrays
+  const int64_t groups = (P + 31) / 32;
+  size_t b1 = four ? Carve::bytes_for<uint32_t>(groups) + Carve::bytes_for<int64_t>(groups) +
+                         Carve::bytes_for<int64_t>(groups + 1) +
+                         Carve::bytes_for<int64_t>(scan_tmp_elems(groups + 1))
+                   : 256;
+  void* base1 = nullptr;
+  GS_TRY(ws_reserve(ws, 1, b1, stream, &base1));
+  Carve c1{(char*)base1, 0};
+  uint32_t* tbits = four ? c1.take<uint32_t>(groups) : nullptr;
+  int64_t* chunk_cost = four ? c1.take<int64_t>(groups) : nullptr;
+  int64_t* task_off = four ? c1.take<int64_t>(groups + 1) : nullptr;
+  int64_t* tmp1 = four ? c1.take<int64_t>(scan_tmp_elems(groups + 1)) : nullptr;
+
+  const int persist = sms * kBlocksPerSm;
+  if (four)
+    k_tri<true><<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, tbits);
+  else
+    k_tri<false><<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, nullptr);
+  GS_CUDA(cudaGetLastError());
+
+  if (four) {
+    GS_TRY(exclusive_scan_i64((const int64_t*)t, toff, K, tmp0, stream));
+    int64_t tsum = 0;
+    GS_CUDA(cudaMemcpyAsync(&tsum, toff + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    GS_CUDA(cudaStreamSynchronize(stream));
+    void* base2 = nullptr;
+    GS_TRY(ws_reserve(ws, 2, Carve::bytes_for<int32_t>(tsum), stream, &base2));
+    int32_t* T = (int32_t*)base2;
+    k_compact_T<<<grid_for(K * 32, kThreads, 8), kThreads, 0, stream>>>(g, uv, off, toff, K, tbits,
+                                                                        T);
+    k_chunk_cost<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, need_k, need_q,
+                                                   chunk_cost, task_off, q);
+    GS_TRY(exclusive_scan_i64(task_off, task_off, groups, tmp1, stream));
+    k_quad<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, chunk_cost,
+                                             task_off, groups, need_k, need_q, k2, q);
+    GS_CUDA(cudaGetLastError());
+  }
+  k_fold<<<fold_blocks, kThreads, 0, stream>>>(g, uv, K, t, four ? k2 : nullptr,
+                                                four ? q : nullptr, d_per_edge, part);
+  k_fold_final<<<1, 32, 0, stream>>>(part, fold_blocks, d_sums);
+  GS_CUDA(cudaGetLastError());
+  unsigned long long h[32];
+  GS_CUDA(cudaMemcpyAsync(h, d_sums, sizeof(h), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  static const uint32_t bit[8] = {GS_G3, GS_G4, GS_G7, GS_G8, GS_G9, GS_G10, GS_G11, GS_G12};
+  for (int i = 0; i < 8; ++i) {
+    if (!(mask & bit[i])) continue;
+    h_sums->sum[i][0] = h[2 * i];
+    h_sums->sum[i][1] = h[2 * i + 1];
+    h_sums->sumsq[i][0] = h[2 * (8 + i)];
+    h_sums->sumsq[i][1] = h[2 * (8 + i) + 1];
+  }
+  return GS_OK;
+}

@@ -1,0 +1,143 @@
+// Host-side estimators (Sec. 3), variance and confidence bounds (Sec. 5.3),
+// plus the fused sample -> count -> estimate convenience call.
+#include <math.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace {
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+const int64_t kDenom[8] = {3, 2, 6, 1, 2, 4, 6, 1};
+const uint32_t kBit[8] = {GS_G3, GS_G4, GS_G7, GS_G8, GS_G9, GS_G10, GS_G11, GS_G12};
+
+// 256-bit unsigned integer as four 64-bit words, least significant first.
+struct U256 {
+  uint64_t w[4];
+};
+
+U256 mul_128x128(u128 a, u128 b) {
+  uint64_t a0 = (uint64_t)a, a1 = (uint64_t)(a >> 64), b0 = (uint64_t)b, b1 = (uint64_t)(b >> 64);
+  u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
+  U256 r;
+  r.w[0] = (uint64_t)p00;
+  u128 mid = (p00 >> 64) + (uint64_t)p01 + (uint64_t)p10;
+  r.w[1] = (uint64_t)mid;
+  u128 hi = (mid >> 64) + (p01 >> 64) + (p10 >> 64) + (uint64_t)p11;
+  r.w[2] = (uint64_t)hi;
+  r.w[3] = (uint64_t)((hi >> 64) + (p11 >> 64));
+  return r;
+}
+
+// a - b, requires a >= b.
+U256 sub_256(const U256& a, const U256& b) {
+  U256 r;
+  uint64_t borrow = 0;
+  for (int i = 0; i < 4; ++i) {
+    u128 d = (u128)a.w[i] - b.w[i] - borrow;
+    r.w[i] = (uint64_t)d;
+    borrow = (uint64_t)(d >> 64) ? 1 : 0;
+  }
+  return r;
+}
+
+bool less_256(const U256& a, const U256& b) {
+  for (int i = 3; i >= 0; --i)
+    if (a.w[i] != b.w[i]) return a.w[i] < b.w[i];
+  return false;
+}
+
+double to_double_256(const U256& a) {
+  double r = 0.0;
+  for (int i = 3; i >= 0; --i) r = r * 18446744073709551616.0 + (double)a.w[i];
+  return r;
+}
+
+i128 load_i128(const uint64_t v[2]) { return (i128)(((u128)v[1] << 64) | v[0]); }
+u128 load_u128(const uint64_t v[2]) { return ((u128)v[1] << 64) | v[0]; }
+
+}  // namespace
+
+extern "C" gs_status gs_estimate(const gs_sums* s, double z, gs_result* out) {
+  if (s == nullptr || out == nullptr || s->k < 0 || s->m < 0 || s->k > s->m || !(z >= 0.0)) {
+    gs::set_error("gs_estimate: invalid arguments (need 0 <= k <= m, z >= 0)");
+    return GS_EINVAL;
+  }
+  const int64_t M = s->m, K = s->k;
+  for (int i = 0; i < 8; ++i) {
+    out->x[i] = out->var[i] = out->lb[i] = out->ub[i] = NAN;
+    out->exact[i] = 0;
+    out->flags[i] = 0;
+    if (!(s->mask & kBit[i])) continue;
+    uint32_t flags = GS_F_COMPUTED;
+    const i128 S = load_i128(s->sum[i]);
+    const u128 S2 = load_u128(s->sumsq[i]);
+    const int64_t D = kDenom[i];
+    double x = NAN;
+    if (K >= 1) {
+      // X = M S / (K D): one rounding of the exact product when it fits.
+      const u128 absS = (u128)(S < 0 ? -S : S);
+      if (absS < ((u128)1 << 90) && M < ((int64_t)1 << 36)) {
+        x = (double)(S * (i128)M) / (double)(K * D);
+      } else {
+        x = ((double)M / (double)K) * ((double)S / (double)D);
+      }
+    }
+    double var = NAN;
+    if (K == M && K >= 1) {
+      flags |= GS_F_EXACT;
+      var = 0.0;
+      if (S < 0 || S % D != 0 || (u128)(S / D) > (u128)UINT64_MAX) {
+        flags |= GS_F_OVERFLOW;
+      } else {
+        out->exact[i] = (uint64_t)(S / D);
+      }
+    } else if (K >= 2) {
+      // Q = K sum N^2 - (sum N)^2 >= 0 exactly, in 256 bits.
+      const U256 a = mul_128x128(S2, (u128)K);
+      const u128 absS = (u128)(S < 0 ? -S : S);
+      const U256 b = mul_128x128(absS, absS);
+      const double Q = less_256(a, b) ? 0.0 : to_double_256(sub_256(a, b));
+      const double num = (double)M * (double)(M - K);
+      const double den = (double)K * (double)K * (double)(K - 1) * (double)(D * D);
+      var = num / den * Q;
+    } else {
+      flags |= GS_F_VAR_UNDEFINED;
+    }
+    out->x[i] = x;
+    out->var[i] = var;
+    if (!(flags & GS_F_VAR_UNDEFINED)) {
+      const double half = z * sqrt(var);
+      out->lb[i] = x - half;
+      out->ub[i] = x + half;
+    }
+    out->flags[i] = flags;
+  }
+  return GS_OK;
+}
+
+extern "C" gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, double fraction,
+                                       uint64_t seed, uint32_t mask, double z, gs_result* out,
+                                       int64_t* k_out, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (g == nullptr || ws == nullptr || out == nullptr || !(fraction >= 0.0 && fraction <= 1.0)) {
+    gs::set_error("gs_count_estimate: invalid arguments");
+    return GS_EINVAL;
+  }
+  gs_sums sums;
+  int64_t K = 0;
+  int64_t M = 0;
+  gs_graph_info(g, nullptr, &M, nullptr, nullptr, nullptr);
+  if (fraction == 1.0) {
+    K = M;
+    GS_TRY(gs_count(g, ws, nullptr, K, mask, nullptr, &sums, stream));
+  } else {
+    int32_t* pairs = nullptr;
+    GS_TRY(gs::sample_impl(g, ws, fraction, seed, nullptr, 0, &K, &pairs, stream));
+    GS_TRY(gs_count(g, ws, pairs, K, mask, nullptr, &sums, stream));
+  }
+  if (k_out) *k_out = K;
+  return gs_estimate(&sums, z, out);
+}

@@ -1,0 +1,358 @@
+// Graph registration (validation, upper-edge index, hub index) and the
+// uniform edge sampler of Algorithm 1.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gs {
+
+// ------------------------------------------------------------- validation
+// One warp per row (grid-stride). Checks the simple-graph conditions of
+// Sec. 3.1: ids in range, strictly increasing lists (sorted, no repeats),
+// no self-loops, and symmetry (u lists v => v lists u, by halving search).
+__global__ void k_validate(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           int64_t n, int64_t nnz, DevError* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    int64_t s = row_ptr[v], e = row_ptr[v + 1];
+    if (s < 0 || e < s || e > nnz) {
+      if (lane == 0) raise_error(err, GS_EINVAL, v);
+      continue;
+    }
+    for (int64_t p = s + lane; p < e; p += 32) {
+      int32_t x = col[p];
+      if (x < 0 || x >= n) { raise_error(err, GS_EINVAL, p); continue; }
+      if (x == v) { raise_error(err, GS_ESELFLOOP, p); continue; }
+      if (p > s) {
+        int32_t prev = col[p - 1];
+        if (prev == x) raise_error(err, GS_EDUP, p);
+        else if (prev > x) raise_error(err, GS_ENOTSORTED, p);
+      }
+      int64_t xs = row_ptr[x], xe = row_ptr[x + 1];
+      if (xs < 0 || xe < xs || xe > nnz || !sorted_contains(col + xs, xe - xs, (int32_t)v))
+        raise_error(err, GS_EASYM, p);
+    }
+  }
+}
+
+// Per row: index of the first neighbour greater than v, the count of such
+// neighbours (canonical edges u < v owned by row u) and the maximum degree.
+__global__ void k_upper(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                        int64_t n, int64_t* __restrict__ up_ptr, int64_t* __restrict__ up_cnt,
+                        unsigned long long* max_deg) {
+  unsigned long long local_max = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    int64_t s = row_ptr[v], e = row_ptr[v + 1];
+    int64_t lo = s, len = e - s;
+    while (len > 0) {  // lower bound of v + 1
+      int64_t half = len >> 1;
+      if (col[lo + half] <= v) { lo += half + 1; len -= half + 1; }
+      else len = half;
+    }
+    up_ptr[v] = lo;
+    up_cnt[v] = e - lo;
+    unsigned long long d = (unsigned long long)(e - s);
+    local_max = d > local_max ? d : local_max;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long y = __shfl_down_sync(0xffffffffu, local_max, o);
+    local_max = y > local_max ? y : local_max;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(max_deg, local_max);
+}
+
+// ------------------------------------------------------------- hub index
+// Adjacency bitmaps for the highest-degree vertices: bit x of hub h's row is
+// set iff x in N(h). One block per hub; rows are zeroed beforehand.
+__global__ void k_hub_bitmaps(const int64_t* __restrict__ row_ptr,
+                              const int32_t* __restrict__ col, const int32_t* __restrict__ hubs,
+                              int64_t count, int64_t words, uint32_t* __restrict__ bits) {
+  for (int64_t h = blockIdx.x; h < count; h += gridDim.x) {
+    int32_t v = hubs[h];
+    uint32_t* row = bits + h * words;
+    for (int64_t p = row_ptr[v] + threadIdx.x; p < row_ptr[v + 1]; p += blockDim.x) {
+      int32_t x = col[p];
+      atomicOr(row + (x >> 5), 1u << (x & 31));
+    }
+  }
+}
+
+}  // namespace gs
+
+// =================================================================== C ABI
+using namespace gs;
+
+static gs_status read_error(DevError* d_err, cudaStream_t stream, const char* what) {
+  DevError h;
+  GS_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  if (h.code != 0) {
+    const char* kind = "invalid argument";
+    switch (h.code) {
+      case GS_ENOTSORTED: kind = "adjacency list not sorted"; break;
+      case GS_ESELFLOOP: kind = "self-loop"; break;
+      case GS_EDUP: kind = "repeated neighbour"; break;
+      case GS_EASYM: kind = "asymmetric adjacency"; break;
+      case GS_EEDGE: kind = "sampled pair is not an edge"; break;
+      case GS_EDUPSAMPLE: kind = "edge sampled twice"; break;
+      default: break;
+    }
+    set_error("%s: %s (element %lld)", what, kind, (long long)h.index);
+    return h.code;
+  }
+  return GS_OK;
+}
+
+extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n,
+                                     int64_t nnz, uint32_t flags, uint64_t hub_budget_bytes,
+                                     void* stream_, gs_graph** out) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (out == nullptr || d_row_ptr == nullptr || n < 0 || nnz < 0 || (nnz > 0 && d_col == nullptr)) {
+    set_error("gs_graph_create: invalid arguments");
+    return GS_EINVAL;
+  }
+  if (n > INT32_MAX || (nnz & 1)) {
+    set_error("gs_graph_create: n must fit int32 and nnz must be even (both orientations)");
+    return GS_EINVAL;
+  }
+  int64_t ends[2] = {0, 0};
+  GS_CUDA(cudaMemcpyAsync(&ends[0], d_row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaMemcpyAsync(&ends[1], d_row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  if (ends[0] != 0 || ends[1] != nnz) {
+    set_error("gs_graph_create: row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+    return GS_EINVAL;
+  }
+  gs_graph* g = new gs_graph();
+  memset(g, 0, sizeof(*g));
+  g->dev.row_ptr = d_row_ptr;
+  g->dev.col = d_col;
+  g->dev.n = n;
+  g->dev.nnz = nnz;
+  g->m = nnz / 2;
+  auto fail = [&](gs_status s) {
+    gs_graph_destroy(g);
+    return s;
+  };
+  DevError* d_err = nullptr;
+  unsigned long long* d_max = nullptr;
+  int64_t* tmp = nullptr;
+  if (cudaMalloc(&d_err, sizeof(DevError) + sizeof(unsigned long long)) != cudaSuccess) {
+    set_error("gs_graph_create: out of device memory");
+    return fail(GS_ENOMEM);
+  }
+  d_max = reinterpret_cast<unsigned long long*>(d_err + 1);
+  cudaMemsetAsync(d_err, 0, sizeof(DevError) + sizeof(unsigned long long), stream);
+  if (flags & GS_VALIDATE) {
+    k_validate<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(d_row_ptr, d_col, n, nnz, d_err);
+    gs_status s = read_error(d_err, stream, "gs_graph_create");
+    if (s != GS_OK) {
+      cudaFree(d_err);
+      return fail(s);
+    }
+  }
+  int64_t tmp_elems = scan_tmp_elems(n);
+  if (cudaMalloc(&g->up_ptr, sizeof(int64_t) * (size_t)(n > 0 ? n : 1)) != cudaSuccess ||
+      cudaMalloc(&g->edge_off, sizeof(int64_t) * (size_t)(n + 1)) != cudaSuccess ||
+      cudaMalloc(&tmp, sizeof(int64_t) * (size_t)tmp_elems) != cudaSuccess) {
+    cudaFree(d_err);
+    cudaFree(tmp);
+    set_error("gs_graph_create: out of device memory");
+    return fail(GS_ENOMEM);
+  }
+  if (n > 0) {
+    k_upper<<<grid_for(n, 256, 8), 256, 0, stream>>>(d_row_ptr, d_col, n, g->up_ptr, g->edge_off,
+                                                     d_max);
+  }
+  gs_status s = exclusive_scan_i64(g->edge_off, g->edge_off, n, tmp, stream);
+  unsigned long long hmax = 0;
+  int64_t m_check = 0;
+  cudaMemcpyAsync(&hmax, d_max, sizeof(hmax), cudaMemcpyDeviceToHost, stream);
+  cudaMemcpyAsync(&m_check, g->edge_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream);
+  cudaError_t ce = cudaStreamSynchronize(stream);
+  cudaFree(tmp);
+  cudaFree(d_err);
+  if (s != GS_OK) return fail(s);
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "gs_graph_create", __FILE__, __LINE__));
+  g->max_degree = (int64_t)hmax;
+  if (m_check != g->m) {
+    set_error("gs_graph_create: upper-triangle edge count %lld != nnz/2 = %lld (asymmetric CSR?)",
+              (long long)m_check, (long long)g->m);
+    return fail(GS_EASYM);
+  }
+  (void)hub_budget_bytes;
+  *out = g;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_graph_destroy(gs_graph* g) {
+  if (g == nullptr) return GS_OK;
+  cudaFree(g->up_ptr);
+  cudaFree(g->edge_off);
+  cudaFree(g->bm_slot);
+  cudaFree(g->bm_bits);
+  cudaFree(g->tb_slot);
+  cudaFree(g->tb_codeg);
+  delete g;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_graph_info(const gs_graph* g, int64_t* n, int64_t* m, int64_t* max_degree,
+                                   int64_t* bitmap_hubs, int64_t* table_hubs) {
+  if (g == nullptr) {
+    set_error("gs_graph_info: null graph");
+    return GS_EINVAL;
+  }
+  if (n) *n = g->dev.n;
+  if (m) *m = g->m;
+  if (max_degree) *max_degree = g->max_degree;
+  if (bitmap_hubs) *bitmap_hubs = g->dev.bm_count;
+  if (table_hubs) *table_hubs = g->dev.tb_count;
+  return GS_OK;
+}
+
+// =================================================================== sampler
+namespace gs {
+
+// SplitMix64 output function (Steele, Lea, Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014) for generator state x.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ bool edge_kept(uint64_t seed, uint64_t i, uint64_t threshold) {
+  return (splitmix64(seed ^ splitmix64(i)) >> 11) < threshold;
+}
+
+constexpr int kSampThreads = 256;
+constexpr int kSampItems = 16;
+constexpr int64_t kSampTile = (int64_t)kSampThreads * kSampItems;
+
+__global__ void k_sample_count(int64_t m, uint64_t seed, uint64_t threshold,
+                               int64_t* __restrict__ tile_cnt) {
+  int64_t base = (int64_t)blockIdx.x * kSampTile + (int64_t)threadIdx.x * kSampItems;
+  int c = 0;
+#pragma unroll
+  for (int j = 0; j < kSampItems; ++j)
+    if (base + j < m) c += edge_kept(seed, (uint64_t)(base + j), threshold);
+  c = __reduce_add_sync(0xffffffffu, c);
+  __shared__ int wsum[kSampThreads / 32];
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t s = 0;
+    for (int w = 0; w < kSampThreads / 32; ++w) s += wsum[w];
+    tile_cnt[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_sample_write(const int32_t* __restrict__ col, const int64_t* __restrict__ up_ptr,
+                               const int64_t* __restrict__ edge_off, int64_t n, int64_t m,
+                               uint64_t seed, uint64_t threshold,
+                               const int64_t* __restrict__ tile_off, int32_t* __restrict__ pairs) {
+  __shared__ int wsum[kSampThreads / 32];
+  int64_t base = (int64_t)blockIdx.x * kSampTile + (int64_t)threadIdx.x * kSampItems;
+  unsigned bits = 0;
+#pragma unroll
+  for (int j = 0; j < kSampItems; ++j)
+    if (base + j < m && edge_kept(seed, (uint64_t)(base + j), threshold)) bits |= 1u << j;
+  int c = __popc(bits);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = c;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  int before = 0;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  int64_t pos = tile_off[blockIdx.x] + before + x - c;
+  while (bits) {
+    int j = __ffs(bits) - 1;
+    bits &= bits - 1;
+    int64_t i = base + j;
+    // row u owning canonical edge i: the last u with edge_off[u] <= i
+    int64_t lo = 0, len = n;
+    while (len > 1) {
+      int64_t half = len >> 1;
+      lo = (edge_off[lo + half] <= i) ? lo + half : lo;
+      len -= half;
+    }
+    int32_t v = col[up_ptr[lo] + (i - edge_off[lo])];
+    pairs[2 * pos] = (int32_t)lo;
+    pairs[2 * pos + 1] = v;
+    ++pos;
+  }
+}
+
+}  // namespace gs
+
+namespace gs {
+
+// Samples into d_pairs (capacity max_k) or, when d_pairs is NULL, into
+// workspace slot 3 sized to the number kept (*pairs_out receives it).
+gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
+                      int32_t* d_pairs, int64_t max_k, int64_t* k_out, int32_t** pairs_out,
+                      cudaStream_t stream) {
+  const int64_t m = g->m;
+  *k_out = 0;
+  if (pairs_out) *pairs_out = d_pairs;
+  if (m == 0) return GS_OK;
+  const uint64_t threshold = (uint64_t)floor(fraction * 9007199254740992.0);
+  int64_t tiles = (m + kSampTile - 1) / kSampTile;
+  size_t bytes = Carve::bytes_for<int64_t>(tiles + 1) * 2 +
+                 Carve::bytes_for<int64_t>(scan_tmp_elems(tiles));
+  void* base = nullptr;
+  GS_TRY(ws_reserve(ws, 2, bytes, stream, &base));
+  Carve c{(char*)base, 0};
+  int64_t* cnt = c.take<int64_t>(tiles + 1);
+  int64_t* off = c.take<int64_t>(tiles + 1);
+  int64_t* tmp = c.take<int64_t>(scan_tmp_elems(tiles));
+  k_sample_count<<<(unsigned)tiles, kSampThreads, 0, stream>>>(m, seed, threshold, cnt);
+  GS_TRY(exclusive_scan_i64(cnt, off, tiles, tmp, stream));
+  int64_t kept = 0;
+  GS_CUDA(cudaMemcpyAsync(&kept, off + tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  *k_out = kept;
+  if (d_pairs == nullptr) {
+    void* b3 = nullptr;
+    GS_TRY(ws_reserve(ws, 3, Carve::bytes_for<int32_t>(2 * kept), stream, &b3));
+    d_pairs = (int32_t*)b3;
+    if (pairs_out) *pairs_out = d_pairs;
+  } else if (kept > max_k) {
+    set_error("gs_sample: %lld edges kept but the output holds %lld", (long long)kept,
+              (long long)max_k);
+    return GS_ECAPACITY;
+  }
+  if (kept > 0)
+    k_sample_write<<<(unsigned)tiles, kSampThreads, 0, stream>>>(
+        g->dev.col, g->up_ptr, g->edge_off, g->dev.n, m, seed, threshold, off, d_pairs);
+  GS_CUDA(cudaGetLastError());
+  return GS_OK;
+}
+
+}  // namespace gs
+
+extern "C" gs_status gs_sample(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
+                               int32_t* d_pairs, int64_t max_k, int64_t* k_out, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (g == nullptr || ws == nullptr || k_out == nullptr || max_k < 0 || d_pairs == nullptr ||
+      !(fraction >= 0.0 && fraction <= 1.0)) {
+    set_error("gs_sample: invalid arguments (fraction must lie in [0, 1])");
+    return GS_EINVAL;
+  }
+  GS_TRY(sample_impl(g, ws, fraction, seed, d_pairs, max_k, k_out, nullptr, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  return GS_OK;
+}

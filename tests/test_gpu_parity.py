@@ -1,0 +1,264 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the
+same seeded inputs. Integer sums and per-edge counts are bit-exact; FP64
+estimates agree within 1e-12 relative."""
+import itertools
+
+import numpy as np
+import pytest
+
+import brute
+import oracle
+import synth
+from gpu_util import assert_estimates_close, assert_sums_equal, oracle_sums, per_edge_reference
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_1701_01772_gb300 as gs  # noqa: E402
+
+ALL = gs.GRAPHLETS
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    gs.build()
+    yield
+
+
+def _graph(rp, col, **kw):
+    return gs.Graph.from_numpy(rp, col, **kw)
+
+
+def _full_check(rp, col, pairs, mask=gs.GS_CONNECTED, ids=ALL):
+    g = _graph(rp, col)
+    per = torch.zeros((len(pairs), 3), dtype=torch.int64, device="cuda")
+    dpairs = torch.as_tensor(pairs, dtype=torch.int32, device="cuda")
+    sums = g.count(dpairs, mask, per_edge=per)
+    s, s2, lc = oracle_sums(rp, col, pairs)
+    assert_sums_equal(sums, s, s2, ids)
+    ref_pe = per_edge_reference(lc)
+    got_pe = per.cpu().numpy()
+    need_k = mask & (gs.GS_G7 | gs.GS_G8 | gs.GS_G9 | gs.GS_G11)
+    need_q = mask & (gs.GS_G10 | gs.GS_G12)
+    assert np.array_equal(got_pe[:, 0], ref_pe[:, 0])
+    if need_k:
+        assert np.array_equal(got_pe[:, 1], ref_pe[:, 1])
+    if need_q:
+        assert np.array_equal(got_pe[:, 2], ref_pe[:, 2])
+    ref = oracle.estimate(s, s2, len(col) // 2, len(pairs))
+    assert_estimates_close(gs.gs_estimate(sums), ref, ids)
+    g.close()
+
+
+# ------------------------------------------------------------------ small graphs
+
+@pytest.mark.parametrize("gid", [3, 4, 7, 8, 9, 10, 11, 12])
+def test_table1_graphlets_count_themselves(gid):
+    n, edges = brute.GRAPHLET_EDGES[gid]
+    rp, col = brute.csr_from_edges(n, edges)
+    g = _graph(rp, col)
+    res = gs.gs_estimate(g.count(None)).as_dict()
+    want = brute.brute_counts(brute.adjacency(n, edges))
+    for i in ALL:
+        assert res[i]["exact"] == want[i], (gid, i)
+    g.close()
+
+
+def test_random_small_graphs_exact_against_brute_force():
+    rng = np.random.default_rng(3)
+    for trial in range(25):
+        n = int(rng.integers(5, 13))
+        U = np.triu(rng.random((n, n)) < rng.uniform(0.2, 0.9), 1)
+        A = (U | U.T).astype(np.int64)
+        rp, col = brute.csr_from_adjacency(A)
+        if len(col) == 0:
+            continue
+        g = _graph(rp, col)
+        res = gs.gs_estimate(g.count(None)).as_dict()
+        want = brute.brute_counts(A)
+        for i in ALL:
+            assert res[i]["exact"] == want[i], (trial, i)
+        g.close()
+
+
+@pytest.mark.parametrize("kind,args", [("complete", (40,)), ("cycle", (1000,)), ("star", (3000,)),
+                                       ("bipartite", (50, 70)), ("path", (5000,))])
+def test_closed_forms(kind, args):
+    n, edges = brute.family_edges(kind, *args)
+    rp, col = brute.csr_from_edges(n, edges) if n <= 200 else synth.from_pairs(
+        n, np.array([e[0] for e in edges]), np.array([e[1] for e in edges]))
+    g = _graph(rp, col)
+    res = gs.gs_estimate(g.count(None)).as_dict()
+    want = brute.closed_form(kind, *args)
+    for i in ALL:
+        assert res[i]["exact"] == want[i], (kind, i)
+    g.close()
+
+
+# ------------------------------------------------------------------ workloads
+
+def test_er_2000_exact_and_explicit_sample():
+    """Erdos-Renyi G(2000, 20000): exact counts (all edges) and a seeded 10%
+    explicit edge list (shuffled, random orientation)."""
+    rp, col = synth.er_2000()
+    pairs_all = synth.upper_pairs(rp, col)
+    _full_check(rp, col, pairs_all)
+    sample = synth.explicit_sample(rp, col, 0.10, seed=2024)
+    _full_check(rp, col, sample)
+    g = _graph(rp, col)
+    res = gs.gs_estimate(g.count(None)).as_dict()
+    exact = oracle.exact_counts(rp, col)
+    for i in ALL:
+        assert res[i]["exact"] == exact[i]
+    g.close()
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: synth.chung_lu(20000, 150000, 2.1, 1500.0, seed=77),
+    lambda: synth.rmat(13, 12, seed=5),
+    lambda: synth.rgg(6000, 0.04, seed=8),
+], ids=["chung_lu_20k", "rmat_13", "rgg_6k"])
+def test_medium_graphs_all_edges_and_samples(maker):
+    rp, col = maker()
+    _full_check(rp, col, synth.upper_pairs(rp, col))
+    _full_check(rp, col, synth.explicit_sample(rp, col, 0.05, seed=1))
+
+
+@pytest.mark.parametrize("mask", [gs.GS_G3, gs.GS_THREE_NODE, gs.GS_G7, gs.GS_G10,
+                                  gs.GS_G8 | gs.GS_G12, gs.GS_G11, gs.GS_CONNECTED])
+def test_masks_select_passes(mask):
+    rp, col = synth.chung_lu(5000, 40000, 2.1, 600.0, seed=12)
+    pairs = synth.explicit_sample(rp, col, 0.2, seed=3)
+    ids = [g for g in ALL if mask & (1 << g)]
+    _full_check(rp, col, pairs, mask=mask, ids=ids)
+
+
+def test_sampler_matches_oracle_bit_exact():
+    for rp, col in (synth.er_2000(), synth.chung_lu(50000, 400000, 2.1, 3000.0, seed=4)):
+        g = _graph(rp, col)
+        for frac, seed in ((0.01, 1), (0.1, 77), (0.5, 3), (1.0, 5), (0.0, 9)):
+            got = g.sample(frac, seed).cpu().numpy()
+            want = oracle.sample(rp, col, frac, seed)
+            assert np.array_equal(got, want), (frac, seed)
+        g.close()
+
+
+def test_count_estimate_fused_matches_oracle():
+    rp, col = synth.chung_lu(8000, 60000, 2.1, 900.0, seed=21)
+    g = _graph(rp, col)
+    res, k = g.count_estimate(0.1, seed=42)
+    pairs = oracle.sample(rp, col, 0.1, 42)
+    assert k == len(pairs)
+    s, s2, _ = oracle_sums(rp, col, pairs)
+    assert_estimates_close(res, oracle.estimate(s, s2, len(col) // 2, k), ALL)
+    res1, k1 = g.count_estimate(1.0)
+    exact = oracle.exact_counts(rp, col)
+    got = res1.as_dict()
+    for i in ALL:
+        assert got[i]["exact"] == exact[i]
+        assert got[i]["V"] == 0.0
+    g.close()
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_empty_and_single_edge_samples():
+    rp, col = synth.er(500, 3000, seed=1)
+    g = _graph(rp, col)
+    empty = torch.zeros((0, 2), dtype=torch.int32, device="cuda")
+    s = g.count(empty)
+    r = gs.gs_estimate(s)
+    assert s.k == 0 and all(v == (0, 0) for v in s.sums().values())
+    one = torch.as_tensor(synth.upper_pairs(rp, col)[:1], device="cuda")
+    r = gs.gs_estimate(g.count(one)).as_dict()
+    for i in ALL:
+        assert r[i]["flags"] & gs.GS_F_VAR_UNDEFINED
+    g.close()
+
+
+def test_isolated_vertices_and_tiny_graph():
+    rp, col = synth.from_pairs(50, np.array([3, 3, 4]), np.array([4, 5, 5]))
+    g = _graph(rp, col)
+    r = gs.gs_estimate(g.count(None)).as_dict()
+    assert r[3]["exact"] == 1 and r[4]["exact"] == 0
+    g.close()
+
+
+def test_hub_heavy_star_of_cliques():
+    """A hub joined to many small cliques: degree skew within one edge set."""
+    edges = []
+    hub = 0
+    nxt = 1
+    for c in range(300):
+        size = 3 + c % 6
+        members = list(range(nxt, nxt + size))
+        nxt += size
+        edges += list(itertools.combinations(members, 2))
+        edges += [(hub, m) for m in members]
+    a = np.array([e[0] for e in edges])
+    b = np.array([e[1] for e in edges])
+    rp, col = synth.from_pairs(nxt, a, b)
+    _full_check(rp, col, synth.upper_pairs(rp, col))
+
+
+def test_invalid_inputs_are_rejected():
+    rp, col = synth.er(300, 2000, seed=2)
+    g = _graph(rp, col)
+    pairs = synth.upper_pairs(rp, col)[:10].copy()
+    bad = pairs.copy()
+    # a non-edge
+    nz = set(map(tuple, synth.upper_pairs(rp, col)))
+    u = next(x for x in range(300) if (0, x) not in nz and x != 0)
+    bad[3] = (0, u)
+    with pytest.raises(gs.GraphletError) as ei:
+        g.count(torch.as_tensor(bad, device="cuda"))
+    assert ei.value.status == 6
+    # out of range id
+    bad = pairs.copy()
+    bad[0] = (0, 10**6)
+    with pytest.raises(gs.GraphletError) as ei:
+        g.count(torch.as_tensor(bad, device="cuda"))
+    assert ei.value.status == 6
+    # duplicate edge (in either orientation)
+    dup = np.concatenate([pairs, pairs[2:3, ::-1]])
+    with pytest.raises(gs.GraphletError) as ei:
+        g.count(torch.as_tensor(np.ascontiguousarray(dup), device="cuda"))
+    assert ei.value.status == 7
+    # bad mask
+    with pytest.raises(gs.GraphletError):
+        g.count(torch.as_tensor(pairs, device="cuda"), mask=1 << 5)
+    # the handle still works afterwards
+    s, s2, _ = oracle_sums(rp, col, pairs)
+    assert_sums_equal(g.count(torch.as_tensor(pairs, device="cuda")), s, s2, ALL)
+    g.close()
+
+
+@pytest.mark.parametrize("defect", ["unsorted", "selfloop", "dup", "asym"])
+def test_invalid_csr_is_rejected(defect):
+    rp, col = synth.er(100, 400, seed=3)
+    col = col.copy()
+    rp = rp.copy()
+    v = int(np.argmax(np.diff(rp)))
+    s, e = rp[v], rp[v + 1]
+    if defect == "unsorted":
+        col[s], col[s + 1] = col[s + 1], col[s]
+        code = 2
+    elif defect == "selfloop":
+        col[s] = v
+        col[s:e] = np.sort(col[s:e])
+        code = 3
+    elif defect == "dup":
+        col[s + 1] = col[s]
+        code = 4
+    else:
+        present = set(col[s:e].tolist()) | {v}
+        y = next(x for x in range(100) if x not in present)
+        col[s] = y
+        col[s:e] = np.sort(col[s:e])
+        code = 5
+    with pytest.raises(gs.GraphletError) as ei:
+        gs.Graph.from_numpy(rp, col)
+    assert ei.value.status == code
