@@ -43,6 +43,7 @@ __device__ __forceinline__ void raise_error(DevError* err, int32_t code, int64_t
 struct DevGraph {
   const int64_t* row_ptr;   // [n+1]
   const int32_t* col;       // [nnz], sorted per row
+  const int64_t* up_ptr;    // [n] index in col of the first neighbour > v
   int64_t n;
   int64_t nnz;
   // adjacency bitmaps of the highest-degree vertices ("hubs")
@@ -81,6 +82,21 @@ __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64
     }
   }
   return sorted_contains(g.col + base_y, deg_y, x);
+}
+
+// Membership of x in a set given either as a vertex's adjacency (vtx >= 0,
+// list = N(vtx)) or as a plain sorted list (vtx < 0).
+__device__ __forceinline__ bool set_contains(const DevGraph& g, int32_t vtx,
+                                             const int32_t* __restrict__ list, int64_t len,
+                                             int32_t x) {
+  if (vtx >= 0 && g.bm_slot != nullptr) {
+    int32_t s = __ldg(g.bm_slot + vtx);
+    if (s >= 0) {
+      uint32_t w = __ldg(g.bm_bits + (int64_t)s * g.bm_words + (x >> 5));
+      return (w >> (x & 31)) & 1u;
+    }
+  }
+  return sorted_contains(list, len, x);
 }
 
 // ---------------------------------------------------------------- scan

@@ -3,14 +3,17 @@
 //
 // For an edge e = (u, v) with d_u <= d_v (ties: smaller id is u), let
 // T = N(u) cap N(v), S_u = N(u) \ {v} \ T, S_v = N(v) \ {u} \ T. The paper's
-// per-edge quantities are computed as
-//   t  = |T|                                    (Algorithm 2)
-//   2k = sum_{w in T}   |N(w) cap T|            (Algorithm 3, ordered pairs)
-//   q  = sum_{w in S_u} (|N(w) cap N(v)| - |N(w) cap T| - 1)   (Algorithm 4)
-// The last line restates "pairs (w in S_u, r in S_v) with w ~ r": for w in
-// S_u the common neighbours of w and v are u, the members of T adjacent to
-// w, and the members of S_v adjacent to w. It lets |N(w) cap N(v)| come from
-// a precomputed co-degree table when both w and v are hubs.
+// per-edge quantities are
+//   t = |T|                                          (Algorithm 2)
+//   k = adjacent pairs inside T                      (Algorithm 3)
+//   q = pairs (w in S_u, r in S_v) with w ~ r        (Algorithm 4)
+// For w in S_u the common neighbours of w and v are u, the members of T
+// adjacent to w and the members of S_v adjacent to w, so with
+// c(x, y) = |N(x) cap N(y)|:
+//   q = sum_{w in S_u} (c(w, v) - 1) - sum_{r in T} (c(r, u) - 1) + 2k
+// (sum_{w in S_u} |N(w) cap T| counted from the T side). Co-degrees of hub
+// pairs come from a table built at registration; the rest are computed by
+// membership tests (see the item comment below).
 //
 // GPU structure (all work is flattened so that per-edge cost skew -- power
 // law degrees -- does not serialise on one warp):
@@ -24,8 +27,8 @@
 //   compact  T lists written in order (one warp per edge).
 //   cost     per chunk of 32 positions (items w = N(u)[i]): membership-test
 //            count of each item (iterate the shorter list, test in the
-//            longer); constant terms (-1 per S_u item, table co-degrees)
-//            added directly.
+//            longer); constant terms (the -1s, table co-degrees) added
+//            directly.
 //   quad     chunks are cut into tasks of kTaskProbes tests; tasks are split
 //            evenly over all warps; inside a task lanes take consecutive
 //            tests and find their item by a search over the warp's scanned
@@ -189,16 +192,32 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
 }
 
 // ---------------------------------------------------------------- items
-// One item per position of a 32-position chunk: w = N(u)[i].
+// One item per position of a 32-position chunk: w = N(u)[i], w != v.
+// With T = N(u) cap N(v) and c(x, y) = |N(x) cap N(y)|, the 4-node terms are
+//   k = sum_{w in T} |N(w) cap T, above w|                 (each pair once)
+//   q = sum_{w in S_u} (c(w, v) - 1) - sum_{r in T} (c(r, u) - 1) + 2k
+// The second line is sum_{w in S_u} (|N(w) cap N(v)| - |N(w) cap T| - 1)
+// with sum_{w in S_u} |N(w) cap T| = sum_{r in T} (c(r, u) - 1) - 2k
+// (count the pairs (r in T, w in N(u) \ {v}) with r ~ w from the r side).
+// Each item carries up to two segments of membership tests:
+//   A (w in T):  x over the shorter of N(w) above w / T above w, tested in
+//                the other; a hit is one 4-clique pair: k += 1, q += 2.
+//   B (c(w, o)): o = u for w in T, o = v for w in S_u; x over the shorter
+//                adjacency, tested in the longer; q -= 1 / q += 1 per hit.
+//                Skipped (constant term instead) when the co-degree table
+//                holds c(w, o).
+struct Seg {
+  const int32_t* it;    // iterated list
+  const int32_t* sl;    // searched list
+  int32_t svtx;         // vertex whose adjacency sl is (bitmap-capable), or -1
+  int32_t slen;         // length of sl
+  int32_t cnt;          // number of tests
+};
+
 struct Item {
-  int64_t bw;     // row offset of w
-  int32_t dw;     // degree of w
-  int32_t w;
-  int32_t cx;     // tests for |N(w) cap T|
-  int32_t cy;     // tests for |N(w) cap N(v)|
-  int32_t is_t;   // w in T
-  int32_t valid;  // position holds a neighbour other than v
-  int64_t qconst; // constant q contribution (-1 per S_u item, + table co-degree)
+  Seg a, b;
+  int32_t bsign;        // +1 (w in S_u) or -1 (w in T) per segment-B hit
+  int64_t qconst;       // constant q contribution of this item
 };
 
 struct EdgeCtx {
@@ -222,40 +241,104 @@ __device__ __forceinline__ void load_edge(const DevGraph& g, const int2* __restr
   c.toff = toff[e];
 }
 
+// c(a, b) + 1 from the co-degree table when both are table hubs, 0 when the
+// table cannot answer (the +1 marks a present entry).
 __device__ __forceinline__ uint32_t table_codeg(const DevGraph& g, int32_t a, int32_t b) {
   if (g.tb_slot == nullptr) return 0;
   int32_t sa = __ldg(g.tb_slot + a), sb = __ldg(g.tb_slot + b);
   if (sa < 0 || sb < 0) return 0;
-  return __ldg(g.tb_codeg + (int64_t)sa * g.tb_count + sb) + 1u;  // +1: "present" marker
+  int32_t lo = min(sa, sb), hi = max(sa, sb);
+  return __ldg(g.tb_codeg + (int64_t)lo * g.tb_count + hi) + 1u;
 }
 
-__device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c, int64_t i,
+// Index of x in the sorted list a[0..len) (x is present).
+__device__ __forceinline__ int64_t sorted_index(const int32_t* __restrict__ a, int64_t len,
+                                                int32_t x) {
+  int64_t lo = 0;
+  while (len > 1) {
+    int64_t half = len >> 1;
+    lo = (__ldg(a + lo + half) <= x) ? lo + half : lo;
+    len -= half;
+  }
+  return lo;
+}
+
+// Segment for c(w, o): iterate the shorter adjacency, test in the longer.
+__device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int64_t bw, int64_t dw,
+                                              int32_t o, int64_t bo, int64_t dob, Seg& s) {
+  if (dw <= dob) {
+    s.it = g.col + bw;
+    s.sl = g.col + bo;
+    s.svtx = o;
+    s.slen = (int32_t)dob;
+    s.cnt = (int32_t)dw;
+  } else {
+    s.it = g.col + bo;
+    s.sl = g.col + bw;
+    s.svtx = w;
+    s.slen = (int32_t)dw;
+    s.cnt = (int32_t)dob;
+  }
+}
+
+__device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
+                                          const int32_t* __restrict__ T, int64_t i,
                                           uint32_t tword, int lane, bool need_k, bool need_q,
                                           Item& it) {
-  it.valid = 0;
-  it.cx = it.cy = 0;
+  it.a.cnt = it.b.cnt = 0;
+  it.a.it = it.a.sl = it.b.it = it.b.sl = g.col;
+  it.a.svtx = it.b.svtx = -1;
+  it.a.slen = it.b.slen = 0;
   it.qconst = 0;
-  it.is_t = (tword >> lane) & 1u;
-  it.w = -1;
-  it.dw = 0;
-  it.bw = 0;
-  if (i < c.du) {
-    it.w = __ldg(g.col + c.bu + i);
-    it.valid = it.w != c.v;
-  }
-  if (!it.valid) return;
-  it.dw = (int32_t)deg_of(g.row_ptr, it.w, &it.bw);
-  const bool want_x = it.is_t ? need_k : need_q;
-  if (want_x) it.cx = (int32_t)min((int64_t)it.dw, c.te);
-  if (!it.is_t && need_q) {
-    uint32_t tc = table_codeg(g, it.w, c.v);
+  it.bsign = 0;
+  if (i >= c.du) return;
+  const int32_t w = __ldg(g.col + c.bu + i);
+  if (w == c.v) return;
+  const bool in_t = (tword >> lane) & 1u;
+  int64_t bw;
+  const int64_t dw = deg_of(g.row_ptr, w, &bw);
+  if (in_t) {
+    // segment A: |N(w) above w  cap  T above w|
+    const int64_t iw = sorted_index(T + c.toff, c.te, w);
+    const int64_t tg = c.te - iw - 1;
+    const int64_t upw = __ldg(g.up_ptr + w);
+    const int64_t dup = bw + dw - upw;
+    if (dup <= tg) {
+      it.a.it = g.col + upw;
+      it.a.sl = T + c.toff + iw + 1;
+      it.a.svtx = -1;
+      it.a.slen = (int32_t)tg;
+      it.a.cnt = (int32_t)dup;
+    } else {
+      it.a.it = T + c.toff + iw + 1;
+      it.a.sl = g.col + bw;
+      it.a.svtx = w;
+      it.a.slen = (int32_t)dw;
+      it.a.cnt = (int32_t)tg;
+    }
+    if (need_q) {
+      // segment B: -(c(w, u) - 1)
+      it.bsign = -1;
+      uint32_t tc = table_codeg(g, w, c.u);
+      if (tc != 0) {
+        it.qconst = 1 - (int64_t)(tc - 1u);
+      } else {
+        it.qconst = 1;
+        codeg_segment(g, w, bw, dw, c.u, c.bu, c.du, it.b);
+      }
+    }
+  } else if (need_q) {
+    // segment B: c(w, v) - 1
+    it.bsign = 1;
+    uint32_t tc = table_codeg(g, w, c.v);
     if (tc != 0) {
       it.qconst = (int64_t)(tc - 1u) - 1;
     } else {
-      it.cy = (int32_t)min((int64_t)it.dw, c.dv);
       it.qconst = -1;
+      codeg_segment(g, w, bw, dw, c.v, c.bv, c.dv, it.b);
     }
   }
+  (void)need_k;
 }
 
 template <class T>
@@ -270,8 +353,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 __global__ void __launch_bounds__(kThreads)
     k_chunk_cost(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
                  const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
-                 const uint32_t* __restrict__ tbits, int need_k, int need_q,
-                 int64_t* __restrict__ chunk_cost, int64_t* __restrict__ task_cnt,
+                 const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T, int need_k,
+                 int need_q, int64_t* __restrict__ chunk_cost, int64_t* __restrict__ task_cnt,
                  unsigned long long* __restrict__ q) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -288,8 +371,9 @@ __global__ void __launch_bounds__(kThreads)
     while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
     if (e != c.e) load_edge(g, uv, t, toff, e, c);
     Item it;
-    load_item(g, c, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k, need_q, it);
-    int64_t cost = warp_sum<int64_t>((int64_t)it.cx + it.cy);
+    load_item(g, c, T, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k, need_q,
+              it);
+    int64_t cost = warp_sum<int64_t>((int64_t)it.a.cnt + it.b.cnt);
     int64_t qc = warp_sum<int64_t>(it.qconst);
     if (lane == 0) {
       chunk_cost[gi] = cost;
@@ -301,26 +385,38 @@ __global__ void __launch_bounds__(kThreads)
 
 // ---------------------------------------------------------------- quad
 
+// Item descriptors of the chunk a warp is working on, in shared memory so a
+// lane can read the item its test belongs to.
+struct SharedItem {
+  const int32_t* it[2];
+  const int32_t* sl[2];
+  int32_t svtx[2];
+  int32_t slen[2];
+  int32_t ca;
+  int32_t bsign;
+};
+
 __global__ void __launch_bounds__(kThreads)
     k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
            const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
            const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
-           const int64_t* __restrict__ chunk_cost, const int64_t* __restrict__ task_off,
-           int64_t groups, int need_k, int need_q, unsigned long long* __restrict__ k2,
-           unsigned long long* __restrict__ q) {
+           const int64_t* __restrict__ task_off, int64_t groups, int need_k, int need_q,
+           unsigned long long* __restrict__ k_out, unsigned long long* __restrict__ q) {
+  __shared__ SharedItem items[kThreads / 32][32];
   const int lane = threadIdx.x & 31;
+  SharedItem* my = items[threadIdx.x >> 5];
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t NT = __ldg(task_off + groups);
   const int64_t per = (NT + warps - 1) / warps;
   const int64_t t0 = warp * per, t1 = min(NT, t0 + per);
   if (t0 >= t1) return;
+  const long long qa = need_q ? 2 : 0;  // q weight of a segment-A hit
   int64_t gi = last_le(task_off, groups, t0);
   int64_t e = last_le(off, K, gi * 32);
   EdgeCtx c;
   load_edge(g, uv, t, toff, e, c);
   int64_t cur = -1;
-  Item it;
   int64_t start = 0, ctotal = 0;
   unsigned long long acc_k = 0;
   long long acc_q = 0;
@@ -331,16 +427,30 @@ __global__ void __launch_bounds__(kThreads)
       unsigned long long sk = warp_sum<unsigned long long>(acc_k);
       long long sq = warp_sum<long long>(acc_q);
       if (lane == 0 && cur >= 0) {
-        if (sk) atomicAdd(k2 + c.e, sk);
+        if (sk) atomicAdd(k_out + c.e, sk);
         if (sq) atomicAdd(q + c.e, (unsigned long long)sq);
       }
       acc_k = 0;
       acc_q = 0;
       while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
       if (e != c.e) load_edge(g, uv, t, toff, e, c);
-      load_item(g, c, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k, need_q,
-                it);
-      int64_t mine = (int64_t)it.cx + it.cy, incl = mine;
+      Item it;
+      load_item(g, c, T, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k,
+                need_q, it);
+      __syncwarp();
+      SharedItem& si = my[lane];
+      si.it[0] = it.a.it;
+      si.it[1] = it.b.it;
+      si.sl[0] = it.a.sl;
+      si.sl[1] = it.b.sl;
+      si.svtx[0] = it.a.svtx;
+      si.svtx[1] = it.b.svtx;
+      si.slen[0] = it.a.slen;
+      si.slen[1] = it.b.slen;
+      si.ca = it.a.cnt;
+      si.bsign = it.bsign;
+      __syncwarp();
+      int64_t mine = (int64_t)it.a.cnt + it.b.cnt, incl = mine;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         int64_t y = __shfl_up_sync(kFull, incl, d);
@@ -362,33 +472,19 @@ __global__ void __launch_bounds__(kThreads)
         if (s <= rr) j += step;
       }
       const int64_t sj = __shfl_sync(kFull, start, j);
-      const int64_t bw = __shfl_sync(kFull, it.bw, j);
-      const int32_t dw = __shfl_sync(kFull, it.dw, j);
-      const int32_t w = __shfl_sync(kFull, it.w, j);
-      const int32_t cx = __shfl_sync(kFull, it.cx, j);
-      const int32_t is_t = __shfl_sync(kFull, it.is_t, j);
       if (rr < hi) {
+        const SharedItem& si = my[j];
         int64_t o = rr - sj;
-        if (o < cx) {  // |N(w) cap T|
-          bool hit;
-          if ((int64_t)dw <= c.te) {
-            hit = sorted_contains(T + c.toff, c.te, __ldg(g.col + bw + o));
+        const int seg = o < si.ca ? 0 : 1;
+        if (seg) o -= si.ca;
+        const bool hit = set_contains(g, si.svtx[seg], si.sl[seg], si.slen[seg], __ldg(si.it[seg] + o));
+        if (hit) {
+          if (seg == 0) {
+            ++acc_k;
+            acc_q += qa;
           } else {
-            hit = adj_contains(g, w, bw, dw, __ldg(T + c.toff + o));
+            acc_q += si.bsign;
           }
-          if (hit) {
-            if (is_t) ++acc_k;
-            else --acc_q;
-          }
-        } else {  // |N(w) cap N(v)|
-          o -= cx;
-          bool hit;
-          if ((int64_t)dw <= c.dv) {
-            hit = adj_contains(g, c.v, c.bv, c.dv, __ldg(g.col + bw + o));
-          } else {
-            hit = adj_contains(g, w, bw, dw, __ldg(g.col + c.bv + o));
-          }
-          if (hit) ++acc_q;
         }
       }
     }
@@ -396,7 +492,7 @@ __global__ void __launch_bounds__(kThreads)
   unsigned long long sk = warp_sum<unsigned long long>(acc_k);
   long long sq = warp_sum<long long>(acc_q);
   if (lane == 0 && cur >= 0) {
-    if (sk) atomicAdd(k2 + c.e, sk);
+    if (sk) atomicAdd(k_out + c.e, sk);
     if (sq) atomicAdd(q + c.e, (unsigned long long)sq);
   }
 }
@@ -429,7 +525,7 @@ __global__ void __launch_bounds__(kThreads)
     int64_t bu, bv;
     const i128 du = deg_of(g.row_ptr, pr.x, &bu), dv = deg_of(g.row_ptr, pr.y, &bv);
     const i128 tt = (i128)t[e];
-    const i128 kk = k2 != nullptr ? (i128)(k2[e] >> 1) : 0;
+    const i128 kk = k2 != nullptr ? (i128)k2[e] : 0;
     const i128 qq = q != nullptr ? (i128)(long long)q[e] : 0;
     const i128 a = du - 1 - tt, b = dv - 1 - tt;
     const i128 n8 = tt * (tt - 1) / 2 - kk;
@@ -604,11 +700,11 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
     int32_t* T = (int32_t*)base2;
     k_compact_T<<<grid_for(K * 32, kThreads, 8), kThreads, 0, stream>>>(g, uv, off, toff, K, tbits,
                                                                         T);
-    k_chunk_cost<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, need_k, need_q,
-                                                   chunk_cost, task_off, q);
+    k_chunk_cost<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, need_k,
+                                                   need_q, chunk_cost, task_off, q);
     GS_TRY(exclusive_scan_i64(task_off, task_off, groups, tmp1, stream));
-    k_quad<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, chunk_cost,
-                                             task_off, groups, need_k, need_q, k2, q);
+    k_quad<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, task_off, groups,
+                                             need_k, need_q, k2, q);
     GS_CUDA(cudaGetLastError());
   }
   k_fold<<<fold_blocks, kThreads, 0, stream>>>(g, uv, K, t, four ? k2 : nullptr,

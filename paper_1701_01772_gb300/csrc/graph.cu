@@ -10,6 +10,9 @@
 
 namespace gs {
 
+// Vertices below this degree never get bitmaps or table rows.
+constexpr int64_t kHubMinDegree = 64;
+
 // ------------------------------------------------------------- validation
 // One warp per row (grid-stride). Checks the simple-graph conditions of
 // Sec. 3.1: ids in range, strictly increasing lists (sorted, no repeats),
@@ -68,8 +71,46 @@ __global__ void k_upper(const int64_t* __restrict__ row_ptr, const int32_t* __re
 }
 
 // ------------------------------------------------------------- hub index
-// Adjacency bitmaps for the highest-degree vertices: bit x of hub h's row is
-// set iff x in N(h). One block per hub; rows are zeroed beforehand.
+// "Hubs" are the vertices of highest degree. Two structures are built once
+// per graph and reused by every request:
+//   bitmaps  for the top bm_count vertices, a bit per vertex id marking the
+//            neighbours, so "x in N(h)" is one load instead of a search;
+//   table    for the top tb_count vertices, c(a, b) = |N(a) cap N(b)| for
+//            every pair of table hubs (upper triangle a < b by slot).
+// Slots are assigned in increasing vertex id among vertices whose degree is
+// at least a threshold, so the index is deterministic.
+
+__global__ void k_count_deg_ge(const int64_t* __restrict__ row_ptr, int64_t n, int64_t d,
+                               unsigned long long* cnt) {
+  unsigned c = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    c += (row_ptr[v + 1] - row_ptr[v]) >= d;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, (unsigned long long)c);
+}
+
+__global__ void k_flag_deg_ge(const int64_t* __restrict__ row_ptr, int64_t n, int64_t d,
+                              int64_t* __restrict__ flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    flag[v] = (row_ptr[v + 1] - row_ptr[v]) >= d;
+}
+
+// slot[v] = rank of v among flagged vertices, -1 otherwise; hubs[slot] = v.
+__global__ void k_assign_slots(const int64_t* __restrict__ flag_scan, const int64_t* __restrict__ row_ptr,
+                               int64_t n, int64_t d, int32_t* __restrict__ slot,
+                               int32_t* __restrict__ hubs) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    bool f = (row_ptr[v + 1] - row_ptr[v]) >= d;
+    int64_t s = flag_scan[v];
+    slot[v] = f ? (int32_t)s : -1;
+    if (f) hubs[s] = (int32_t)v;
+  }
+}
+
+// Bitmap rows: bit x of hub h's row is set iff x in N(h). One block per hub.
 __global__ void k_hub_bitmaps(const int64_t* __restrict__ row_ptr,
                               const int32_t* __restrict__ col, const int32_t* __restrict__ hubs,
                               int64_t count, int64_t words, uint32_t* __restrict__ bits) {
@@ -80,6 +121,58 @@ __global__ void k_hub_bitmaps(const int64_t* __restrict__ row_ptr,
       int32_t x = col[p];
       atomicOr(row + (x >> 5), 1u << (x & 31));
     }
+  }
+}
+
+// Number of table hubs among the neighbours of each vertex.
+__global__ void k_hub_nbr_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const int32_t* __restrict__ slot, int64_t n,
+                                int64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    unsigned c = 0;
+    for (int64_t p = row_ptr[x] + lane; p < row_ptr[x + 1]; p += 32) c += __ldg(slot + col[p]) >= 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) cnt[x] = c;
+  }
+}
+
+// Compacted table-hub slots of each vertex's neighbours, in list order
+// (hence increasing slot).
+__global__ void k_hub_nbr_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               const int32_t* __restrict__ slot, int64_t n,
+                               const int64_t* __restrict__ off, int32_t* __restrict__ lists,
+                               int32_t* __restrict__ owner) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    int64_t pos = off[x];
+    for (int64_t p0 = row_ptr[x]; p0 < row_ptr[x + 1]; p0 += 32) {
+      int64_t p = p0 + lane;
+      int32_t s = p < row_ptr[x + 1] ? __ldg(slot + col[p]) : -1;
+      unsigned b = __ballot_sync(0xffffffffu, s >= 0);
+      if (s >= 0) {
+        int64_t at = pos + __popc(b & ((1u << lane) - 1u));
+        lists[at] = s;
+        owner[at] = (int32_t)x;
+      }
+      pos += __popc(b);
+    }
+  }
+}
+
+// One thread per list entry i of vertex x: adds 1 to c(L[i], L[j]) for every
+// later entry j, i.e. x is a common neighbour of that hub pair.
+__global__ void k_codeg_pairs(const int32_t* __restrict__ lists, const int32_t* __restrict__ owner,
+                              const int64_t* __restrict__ off, int64_t total, int64_t count,
+                              uint32_t* __restrict__ table) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t x = owner[i];
+    int64_t end = off[x + 1];
+    uint32_t* row = table + (int64_t)lists[i] * count;
+    for (int64_t j = i + 1; j < end; ++j) atomicAdd(row + __ldg(lists + j), 1u);
   }
 }
 
@@ -105,6 +198,140 @@ static gs_status read_error(DevError* d_err, cudaStream_t stream, const char* wh
     }
     set_error("%s: %s (element %lld)", what, kind, (long long)h.index);
     return h.code;
+  }
+  return GS_OK;
+}
+
+// Smallest degree threshold d >= min_deg with at most `cap` vertices of
+// degree >= d (binary search with a device count per probe).
+static gs_status hub_threshold(const gs_graph* g, int64_t cap, int64_t min_deg,
+                               unsigned long long* d_cnt, cudaStream_t stream, int64_t* d_out,
+                               int64_t* count_out) {
+  auto count_ge = [&](int64_t d, int64_t* c) -> gs_status {
+    GS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream));
+    k_count_deg_ge<<<grid_for(g->dev.n, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.n, d,
+                                                                   d_cnt);
+    unsigned long long h = 0;
+    GS_CUDA(cudaMemcpyAsync(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    GS_CUDA(cudaStreamSynchronize(stream));
+    *c = (int64_t)h;
+    return GS_OK;
+  };
+  int64_t lo = min_deg, hi = g->max_degree + 1;  // count(hi) = 0 <= cap
+  int64_t c = 0;
+  GS_TRY(count_ge(lo, &c));
+  if (c <= cap) {
+    *d_out = lo;
+    *count_out = c;
+    return GS_OK;
+  }
+  while (hi - lo > 1) {  // count(lo) > cap >= count(hi)
+    int64_t mid = lo + (hi - lo) / 2;
+    GS_TRY(count_ge(mid, &c));
+    if (c <= cap) hi = mid; else lo = mid;
+  }
+  GS_TRY(count_ge(hi, &c));
+  *d_out = hi;
+  *count_out = c;
+  return GS_OK;
+}
+
+// Builds bitmaps and the co-degree table within budget bytes (half each).
+static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stream) {
+  const int64_t n = g->dev.n;
+  if (budget == 0) budget = (uint64_t)1 << 31;
+  if (n == 0 || g->max_degree < kHubMinDegree) return GS_OK;
+  const int64_t words = (n + 31) / 32;
+  const int64_t bm_cap = (int64_t)((budget / 2) / ((uint64_t)words * 4));
+  int64_t tb_cap = (int64_t)sqrt((double)(budget / 2) / 4.0);
+  if (tb_cap > 65535) tb_cap = 65535;
+  unsigned long long* d_cnt = nullptr;
+  int64_t* flag = nullptr;
+  int64_t* tmp = nullptr;
+  GS_CUDA(cudaMalloc(&d_cnt, sizeof(unsigned long long)));
+  struct Free {
+    void* p[3];
+    ~Free() { for (void* x : p) cudaFree(x); }
+  } guard{{nullptr, nullptr, nullptr}};
+  guard.p[0] = d_cnt;
+  if (cudaMalloc(&flag, sizeof(int64_t) * (size_t)(n + 1)) != cudaSuccess ||
+      cudaMalloc(&tmp, sizeof(int64_t) * (size_t)scan_tmp_elems(n)) != cudaSuccess) {
+    cudaFree(flag);
+    set_error("hub index: out of device memory");
+    return GS_ENOMEM;
+  }
+  guard.p[1] = flag;
+  guard.p[2] = tmp;
+  auto assign = [&](int64_t d, int32_t** slot, int32_t** hubs, int64_t count) -> gs_status {
+    GS_CUDA(cudaMalloc(slot, sizeof(int32_t) * (size_t)n));
+    GS_CUDA(cudaMalloc(hubs, sizeof(int32_t) * (size_t)(count > 0 ? count : 1)));
+    k_flag_deg_ge<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, n, d, flag);
+    GS_TRY(exclusive_scan_i64(flag, flag, n, tmp, stream));
+    k_assign_slots<<<grid_for(n, 256, 8), 256, 0, stream>>>(flag, g->dev.row_ptr, n, d, *slot,
+                                                            *hubs);
+    GS_CUDA(cudaGetLastError());
+    return GS_OK;
+  };
+  // ---- bitmaps
+  int64_t d_bm = 0, n_bm = 0;
+  if (bm_cap > 0) {
+    GS_TRY(hub_threshold(g, bm_cap, kHubMinDegree, d_cnt, stream, &d_bm, &n_bm));
+    if (n_bm > 0) {
+      int32_t* hubs = nullptr;
+      GS_TRY(assign(d_bm, &g->bm_slot, &hubs, n_bm));
+      cudaError_t e = cudaMalloc(&g->bm_bits, sizeof(uint32_t) * (size_t)(words * n_bm));
+      if (e != cudaSuccess) {
+        cudaFree(hubs);
+        return cuda_fail(e, "hub bitmaps", __FILE__, __LINE__);
+      }
+      GS_CUDA(cudaMemsetAsync(g->bm_bits, 0, sizeof(uint32_t) * (size_t)(words * n_bm), stream));
+      k_hub_bitmaps<<<grid_for(n_bm * 256, 256, 8), 256, 0, stream>>>(
+          g->dev.row_ptr, g->dev.col, hubs, n_bm, words, g->bm_bits);
+      GS_CUDA(cudaStreamSynchronize(stream));
+      cudaFree(hubs);
+      g->dev.bm_slot = g->bm_slot;
+      g->dev.bm_bits = g->bm_bits;
+      g->dev.bm_words = words;
+      g->dev.bm_count = n_bm;
+    }
+  }
+  // ---- co-degree table
+  int64_t d_tb = 0, n_tb = 0;
+  if (tb_cap > 1) {
+    GS_TRY(hub_threshold(g, tb_cap, kHubMinDegree, d_cnt, stream, &d_tb, &n_tb));
+    if (n_tb > 1) {
+      int32_t* hubs = nullptr;
+      GS_TRY(assign(d_tb, &g->tb_slot, &hubs, n_tb));
+      cudaFree(hubs);
+      GS_CUDA(cudaMalloc(&g->tb_codeg, sizeof(uint32_t) * (size_t)(n_tb * n_tb)));
+      GS_CUDA(cudaMemsetAsync(g->tb_codeg, 0, sizeof(uint32_t) * (size_t)(n_tb * n_tb), stream));
+      // per-vertex lists of table-hub neighbours
+      k_hub_nbr_count<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.col,
+                                                                    g->tb_slot, n, flag);
+      GS_TRY(exclusive_scan_i64(flag, flag, n, tmp, stream));
+      int64_t total = 0;
+      GS_CUDA(cudaMemcpyAsync(&total, flag + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+      GS_CUDA(cudaStreamSynchronize(stream));
+      int32_t* lists = nullptr;
+      int32_t* owner = nullptr;
+      GS_CUDA(cudaMalloc(&lists, sizeof(int32_t) * (size_t)(total > 0 ? total : 1)));
+      if (cudaMalloc(&owner, sizeof(int32_t) * (size_t)(total > 0 ? total : 1)) != cudaSuccess) {
+        cudaFree(lists);
+        set_error("hub index: out of device memory");
+        return GS_ENOMEM;
+      }
+      k_hub_nbr_fill<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(
+          g->dev.row_ptr, g->dev.col, g->tb_slot, n, flag, lists, owner);
+      k_codeg_pairs<<<grid_for(total, 256, 8), 256, 0, stream>>>(lists, owner, flag, total, n_tb,
+                                                                 g->tb_codeg);
+      cudaError_t e = cudaStreamSynchronize(stream);
+      cudaFree(lists);
+      cudaFree(owner);
+      if (e != cudaSuccess) return cuda_fail(e, "co-degree table", __FILE__, __LINE__);
+      g->dev.tb_slot = g->tb_slot;
+      g->dev.tb_codeg = g->tb_codeg;
+      g->dev.tb_count = n_tb;
+    }
   }
   return GS_OK;
 }
@@ -166,6 +393,7 @@ extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_
     set_error("gs_graph_create: out of device memory");
     return fail(GS_ENOMEM);
   }
+  g->dev.up_ptr = g->up_ptr;
   if (n > 0) {
     k_upper<<<grid_for(n, 256, 8), 256, 0, stream>>>(d_row_ptr, d_col, n, g->up_ptr, g->edge_off,
                                                      d_max);
@@ -186,7 +414,8 @@ extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_
               (long long)m_check, (long long)g->m);
     return fail(GS_EASYM);
   }
-  (void)hub_budget_bytes;
+  gs_status hs = build_hub_index(g, hub_budget_bytes, stream);
+  if (hs != GS_OK) return fail(hs);
   *out = g;
   return GS_OK;
 }

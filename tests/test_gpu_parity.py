@@ -32,8 +32,11 @@ def _graph(rp, col, **kw):
     return gs.Graph.from_numpy(rp, col, **kw)
 
 
-def _full_check(rp, col, pairs, mask=gs.GS_CONNECTED, ids=ALL):
-    g = _graph(rp, col)
+NO_HUBS = 1  # a 1-byte hub budget disables bitmaps and the co-degree table
+
+
+def _full_check(rp, col, pairs, mask=gs.GS_CONNECTED, ids=ALL, hub_budget=0):
+    g = _graph(rp, col, hub_budget_bytes=hub_budget)
     per = torch.zeros((len(pairs), 3), dtype=torch.int64, device="cuda")
     dpairs = torch.as_tensor(pairs, dtype=torch.int32, device="cuda")
     sums = g.count(dpairs, mask, per_edge=per)
@@ -121,10 +124,23 @@ def test_er_2000_exact_and_explicit_sample():
     lambda: synth.rmat(13, 12, seed=5),
     lambda: synth.rgg(6000, 0.04, seed=8),
 ], ids=["chung_lu_20k", "rmat_13", "rgg_6k"])
-def test_medium_graphs_all_edges_and_samples(maker):
+@pytest.mark.parametrize("hub_budget", [0, NO_HUBS, 3 << 20], ids=["hubs", "no_hubs", "few_hubs"])
+def test_medium_graphs_all_edges_and_samples(maker, hub_budget):
     rp, col = maker()
-    _full_check(rp, col, synth.upper_pairs(rp, col))
-    _full_check(rp, col, synth.explicit_sample(rp, col, 0.05, seed=1))
+    g = _graph(rp, col, hub_budget_bytes=hub_budget)
+    info = g.info
+    g.close()
+    if hub_budget == NO_HUBS:
+        assert info["bitmap_hubs"] == 0 and info["table_hubs"] == 0
+    _full_check(rp, col, synth.upper_pairs(rp, col), hub_budget=hub_budget)
+    _full_check(rp, col, synth.explicit_sample(rp, col, 0.05, seed=1), hub_budget=hub_budget)
+
+
+def test_hub_index_is_used_on_power_law_graphs():
+    rp, col = synth.chung_lu(20000, 150000, 2.1, 1500.0, seed=77)
+    g = _graph(rp, col)
+    assert g.info["bitmap_hubs"] > 0 and g.info["table_hubs"] > 1
+    g.close()
 
 
 @pytest.mark.parametrize("mask", [gs.GS_G3, gs.GS_THREE_NODE, gs.GS_G7, gs.GS_G10,
@@ -202,6 +218,7 @@ def test_hub_heavy_star_of_cliques():
     b = np.array([e[1] for e in edges])
     rp, col = synth.from_pairs(nxt, a, b)
     _full_check(rp, col, synth.upper_pairs(rp, col))
+    _full_check(rp, col, synth.upper_pairs(rp, col), hub_budget=NO_HUBS)
 
 
 def test_invalid_inputs_are_rejected():
