@@ -175,6 +175,36 @@ gs_status gs_count(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs, 
  * K = M gives var = 0 and exact counts. */
 gs_status gs_estimate(const gs_sums* s, double z, gs_result* out);
 
+/* Work statistics and device timings of the last gs_count on a workspace.
+ * model_bytes is the streaming cost model of the method: per sampled edge
+ *   B(e) = 24 + 4 (d_u + d_v)                         (pair, offsets, Alg. 2)
+ *        + [4-clique pass]  sum_{w in T_e} (8 + 4 d_w)            (Alg. 3)
+ *        + [4-cycle pass]   min over the two sides of
+ *                           sum_{w in S_side} (8 + 4 d_w)        (Alg. 4)
+ * i.e. the bytes of every adjacency list Algorithms 2-4 scan. The kernels
+ * read fewer bytes than that (searches, hub bitmaps, co-degree table). */
+typedef struct {
+  int64_t k;              /* sampled edges counted */
+  int64_t tri_tests;      /* membership tests of the triangle pass (sum d_u) */
+  int64_t quad_tests;     /* membership tests of the 4-node pass */
+  int64_t t_sum;          /* sum over J of |T_e| */
+  int64_t tasks;          /* 4-node work units of kTaskProbes tests */
+  uint64_t model_bytes;   /* sum over J of B(e) */
+  uint64_t model_tri_bytes;  /* the 24 + 4 (d_u + d_v) part (triangle pass) */
+  uint64_t model_quad_bytes; /* the 4-clique + 4-cycle part (4-node pass) */
+  int64_t launches;       /* kernels launched by that call */
+  int64_t launches_total; /* kernels launched through this workspace so far */
+  int32_t timed;          /* 1 if the ms_* fields below are valid */
+  float ms_prep, ms_tri, ms_compact, ms_cost, ms_quad, ms_fold; /* device ms per phase */
+} gs_stats;
+
+/* Turns per-phase CUDA-event timing of gs_count on (1) or off (0). Events are
+ * recorded on the call's stream around each phase. */
+gs_status gs_workspace_set_timing(gs_workspace* ws, int enable);
+
+/* Host output: statistics of the last gs_count that used `ws`. */
+gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
+
 /* Convenience: gs_sample (fraction < 1) or all edges (fraction == 1), then
  * gs_count and gs_estimate. *k_out (host, may be NULL) receives |J|. */
 gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,

@@ -73,6 +73,20 @@ class GsResult(ctypes.Structure):
         return out
 
 
+class GsStats(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("tri_tests", ctypes.c_int64),
+                ("quad_tests", ctypes.c_int64), ("t_sum", ctypes.c_int64),
+                ("tasks", ctypes.c_int64), ("model_bytes", ctypes.c_uint64),
+                ("model_tri_bytes", ctypes.c_uint64), ("model_quad_bytes", ctypes.c_uint64),
+                ("launches", ctypes.c_int64), ("launches_total", ctypes.c_int64),
+                ("timed", ctypes.c_int32), ("ms_prep", ctypes.c_float), ("ms_tri", ctypes.c_float),
+                ("ms_compact", ctypes.c_float), ("ms_cost", ctypes.c_float),
+                ("ms_quad", ctypes.c_float), ("ms_fold", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib_handle = None
 
 
@@ -103,6 +117,8 @@ def lib() -> ctypes.CDLL:
         "gs_estimate": ([ctypes.POINTER(GsSums), D, ctypes.POINTER(GsResult)], ctypes.c_int32),
         "gs_count_estimate": ([P, P, D, U64, U32, D, ctypes.POINTER(GsResult), PI64, P],
                               ctypes.c_int32),
+        "gs_workspace_set_timing": ([P, ctypes.c_int], ctypes.c_int32),
+        "gs_count_stats": ([P, ctypes.POINTER(GsStats)], ctypes.c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -179,6 +195,16 @@ def gs_workspace_bytes(handle: int) -> int:
     return v.value
 
 
+def gs_workspace_set_timing(handle: int, enable: bool) -> None:
+    _check(lib().gs_workspace_set_timing(handle, int(enable)))
+
+
+def gs_count_stats(handle: int) -> GsStats:
+    out = GsStats()
+    _check(lib().gs_count_stats(handle, ctypes.byref(out)))
+    return out
+
+
 def gs_sample(graph: int, ws: int, fraction: float, seed: int, out_pairs, stream=None) -> int:
     """Writes the sample into out_pairs (CUDA int32 [max_k, 2]); returns K."""
     import torch
@@ -225,6 +251,12 @@ class Workspace:
 
     def nbytes(self) -> int:
         return gs_workspace_bytes(self.handle)
+
+    def set_timing(self, enable: bool = True) -> None:
+        gs_workspace_set_timing(self.handle, enable)
+
+    def stats(self) -> dict:
+        return gs_count_stats(self.handle).as_dict()
 
     def close(self):
         if self.handle:

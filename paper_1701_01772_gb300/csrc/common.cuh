@@ -117,6 +117,7 @@ int sm_count();
 
 struct gs_graph {
   gs::DevGraph dev;
+  int64_t* nbr_degsum;  // [n] sum of the degrees of v's neighbours (cost model)
   int64_t m;            // undirected edges = nnz / 2
   int64_t max_degree;
   int64_t* up_ptr;      // [n]   index in col of the first neighbour > v
@@ -132,6 +133,10 @@ struct gs_workspace {
   size_t cap[4];
   cudaStream_t last_stream;
   int device;
+  int timing;
+  cudaEvent_t ev[12];   // start/stop pairs for the six gs_count phases
+  gs_stats stats;       // last gs_count
+  int64_t launches_total;
 };
 
 namespace gs {

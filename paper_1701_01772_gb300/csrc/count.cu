@@ -172,9 +172,12 @@ __global__ void __launch_bounds__(kThreads) k_tri(DevGraph g, const int2* __rest
 
 // ---------------------------------------------------------------- compact T
 
+// Writes T_e in order and tdeg[e] = sum of the degrees of T_e's members
+// (the latter only feeds the cost model statistics).
 __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off,
                             const int64_t* __restrict__ toff, int64_t K,
-                            const uint32_t* __restrict__ tbits, int32_t* __restrict__ T) {
+                            const uint32_t* __restrict__ tbits, int32_t* __restrict__ T,
+                            int64_t* __restrict__ tdeg) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < K; e += warps) {
@@ -182,12 +185,18 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
     int64_t bu;
     int64_t du = deg_of(g.row_ptr, pr.x, &bu);
     int64_t words = (du + 31) >> 5, w0 = off[e] >> 5, pos = toff[e];
+    long long dsum = 0;
     for (int64_t w = 0; w < words; ++w) {
       uint32_t word = __ldg(tbits + w0 + w);
-      if ((word >> lane) & 1u)
-        T[pos + __popc(word & ((1u << lane) - 1u))] = __ldg(g.col + bu + w * 32 + lane);
+      if ((word >> lane) & 1u) {
+        int32_t x = __ldg(g.col + bu + w * 32 + lane);
+        T[pos + __popc(word & ((1u << lane) - 1u))] = x;
+        dsum += __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
+      }
       pos += __popc(word);
     }
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+    if (lane == 0) tdeg[e] = dsum;
   }
 }
 
@@ -355,7 +364,8 @@ __global__ void __launch_bounds__(kThreads)
                  const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
                  const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T, int need_k,
                  int need_q, int64_t* __restrict__ chunk_cost, int64_t* __restrict__ task_cnt,
-                 unsigned long long* __restrict__ q) {
+                 unsigned long long* __restrict__ q, unsigned long long* __restrict__ stats) {
+  unsigned long long tests = 0;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -379,8 +389,10 @@ __global__ void __launch_bounds__(kThreads)
       chunk_cost[gi] = cost;
       task_cnt[gi] = (cost + kTaskProbes - 1) / kTaskProbes;
       if (qc != 0) atomicAdd(q + e, (unsigned long long)qc);
+      tests += cost;
     }
   }
+  if (lane == 0 && tests) atomicAdd(stats + 1, (unsigned long long)tests);
 }
 
 // ---------------------------------------------------------------- quad
@@ -514,11 +526,14 @@ __device__ __forceinline__ u128 shfl_down_u128(u128 v, int o) {
 __global__ void __launch_bounds__(kThreads)
     k_fold(DevGraph g, const int2* __restrict__ uv, int64_t K,
            const unsigned long long* __restrict__ t, const unsigned long long* __restrict__ k2,
-           const unsigned long long* __restrict__ q, int64_t* __restrict__ per_edge,
-           u128* __restrict__ part) {
+           const unsigned long long* __restrict__ q, const int64_t* __restrict__ tdeg,
+           const int64_t* __restrict__ nbr_degsum, int need_k, int need_q,
+           int64_t* __restrict__ per_edge, u128* __restrict__ part,
+           unsigned long long* __restrict__ stats) {
   u128 acc[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i] = 0;
+  unsigned long long tri_tests = 0, model = 0, model4 = 0;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K;
        e += (int64_t)gridDim.x * blockDim.x) {
     int2 pr = uv[e];
@@ -544,6 +559,20 @@ __global__ void __launch_bounds__(kThreads)
       u128 m = (u128)(N[i] < 0 ? -N[i] : N[i]);
       acc[8 + i] += m * m;
     }
+    // streaming cost model B(e) of Algorithms 2-4 (statistics only)
+    tri_tests += (unsigned long long)du;
+    model += 24 + 4 * (unsigned long long)(du + dv);
+    if (tdeg != nullptr) {
+      const long long td = tdeg[e];
+      unsigned long long B4 = 0;
+      if (need_k) B4 += 8 * (unsigned long long)tt + 4 * (unsigned long long)td;
+      if (need_q) {
+        long long su = (long long)(8 * a) + 4 * (nbr_degsum[pr.x] - (long long)dv - td);
+        long long sv = (long long)(8 * b) + 4 * (nbr_degsum[pr.y] - (long long)du - td);
+        B4 += (unsigned long long)(su < sv ? su : sv);
+      }
+      model4 += B4;
+    }
     if (per_edge != nullptr) {
       per_edge[3 * e] = (int64_t)tt;
       per_edge[3 * e + 1] = (int64_t)kk;
@@ -557,6 +586,14 @@ __global__ void __launch_bounds__(kThreads)
     u128 v = acc[i];
     for (int o = 16; o > 0; o >>= 1) v += shfl_down_u128(v, o);
     if (lane == 0) red[warp][i] = v;
+  }
+  tri_tests = warp_sum<unsigned long long>(tri_tests);
+  model = warp_sum<unsigned long long>(model);
+  model4 = warp_sum<unsigned long long>(model4);
+  if (lane == 0) {
+    atomicAdd(stats + 0, tri_tests);
+    atomicAdd(stats + 2, model);
+    if (model4) atomicAdd(stats + 3, model4);
   }
   __syncthreads();
   if (threadIdx.x < 16) {
@@ -597,6 +634,20 @@ static gs_status fetch_error(DevError* d_err, cudaStream_t stream, const char* w
 
 static const uint32_t kKnownMask = GS_CONNECTED;
 
+namespace {
+// Start/stop events of the six phases when timing is on.
+struct PhaseTimer {
+  gs_workspace* ws;
+  cudaStream_t stream;
+  void start(int phase) {
+    if (ws->timing) cudaEventRecord(ws->ev[2 * phase], stream);
+  }
+  void stop(int phase) {
+    if (ws->timing) cudaEventRecord(ws->ev[2 * phase + 1], stream);
+  }
+};
+}  // namespace
+
 extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs,
                               int64_t K, uint32_t mask, int64_t* d_per_edge, gs_sums* h_sums,
                               void* stream_) {
@@ -610,6 +661,8 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   h_sums->k = K;
   h_sums->m = gr->m;
   h_sums->mask = mask;
+  memset(&ws->stats, 0, sizeof(ws->stats));
+  ws->stats.k = K;
   if (K == 0) return GS_OK;  // empty sample (d_pairs is not read)
   if (d_pairs == nullptr && K != gr->m) {
     set_error("gs_count: with d_pairs = NULL, k must equal the edge count %lld", (long long)gr->m);
@@ -624,12 +677,15 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   const bool check_dup = d_pairs != nullptr;
   int64_t dup_cap = 1;
   while (dup_cap < 2 * K) dup_cap <<= 1;
+  int64_t launches = 0;
+  PhaseTimer timer{ws, stream};
 
   // ---- slot 0: per-edge arrays
   size_t b0 = Carve::bytes_for<DevError>(1) + Carve::bytes_for<unsigned long long>(32) +
+              Carve::bytes_for<unsigned long long>(8) +
               (d_pairs == nullptr ? Carve::bytes_for<int32_t>(2 * K) : 0) +
               Carve::bytes_for<int2>(K) + Carve::bytes_for<int64_t>(K + 1) * 2 +
-              Carve::bytes_for<unsigned long long>(K) * 3 +
+              Carve::bytes_for<unsigned long long>(K) * 3 + Carve::bytes_for<int64_t>(K) +
               Carve::bytes_for<int64_t>(scan_tmp_elems(K + 1)) +
               (check_dup ? Carve::bytes_for<unsigned long long>(dup_cap) : 0) +
               Carve::bytes_for<u128>((int64_t)fold_blocks * 16);
@@ -638,6 +694,7 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   Carve c0{(char*)base0, 0};
   DevError* d_err = c0.take<DevError>(1);
   unsigned long long* d_sums = c0.take<unsigned long long>(32);
+  unsigned long long* d_stats = c0.take<unsigned long long>(8);
   int32_t* pairs_all = d_pairs == nullptr ? c0.take<int32_t>(2 * K) : nullptr;
   int2* uv = c0.take<int2>(K);
   int64_t* off = c0.take<int64_t>(K + 1);
@@ -645,11 +702,14 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   unsigned long long* t = c0.take<unsigned long long>(K);
   unsigned long long* k2 = c0.take<unsigned long long>(K);
   unsigned long long* q = c0.take<unsigned long long>(K);
+  int64_t* tdeg = c0.take<int64_t>(K);
   int64_t* tmp0 = c0.take<int64_t>(scan_tmp_elems(K + 1));
   unsigned long long* dup = check_dup ? c0.take<unsigned long long>(dup_cap) : nullptr;
   u128* part = c0.take<u128>((int64_t)fold_blocks * 16);
 
+  timer.start(0);
   GS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(DevError), stream));
+  GS_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(unsigned long long) * 8, stream));
   GS_CUDA(cudaMemsetAsync(t, 0, sizeof(unsigned long long) * K, stream));
   if (four) {
     GS_CUDA(cudaMemsetAsync(k2, 0, sizeof(unsigned long long) * K, stream));
@@ -661,13 +721,18 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
     k_all_pairs<<<grid_for(g.n * 32, kThreads, 8), kThreads, 0, stream>>>(
         g.row_ptr, g.col, gr->up_ptr, gr->edge_off, g.n, pairs_all);
     pairs = pairs_all;
+    ++launches;
   }
   k_prep<<<grid_for(K, kThreads, 8), kThreads, 0, stream>>>(g, pairs, K, four ? 1 : 0, dup,
                                                             dup_cap - 1, uv, off, d_err);
   GS_TRY(exclusive_scan_i64(off, off, K, tmp0, stream));
+  launches += 4;
+  timer.stop(0);
   int64_t P = 0;
   GS_CUDA(cudaMemcpyAsync(&P, off + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
-  GS_TRY(fetch_error(d_err, stream, "gs_count"));
+  gs_status es = fetch_error(d_err, stream, "gs_count");
+  ws->launches_total += launches;
+  if (es != GS_OK) return es;
 
   // ---- slot 1: per-position arrays
   const int64_t groups = (P + 31) / 32;
@@ -684,35 +749,65 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   int64_t* tmp1 = four ? c1.take<int64_t>(scan_tmp_elems(groups + 1)) : nullptr;
 
   const int persist = sms * kBlocksPerSm;
+  int64_t before = launches;
+  timer.start(1);
   if (four)
     k_tri<true><<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, tbits);
   else
     k_tri<false><<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, nullptr);
+  ++launches;
+  timer.stop(1);
   GS_CUDA(cudaGetLastError());
 
+  int64_t tsum = 0;
   if (four) {
+    timer.start(2);
     GS_TRY(exclusive_scan_i64((const int64_t*)t, toff, K, tmp0, stream));
-    int64_t tsum = 0;
+    launches += 3;
     GS_CUDA(cudaMemcpyAsync(&tsum, toff + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
     GS_CUDA(cudaStreamSynchronize(stream));
     void* base2 = nullptr;
     GS_TRY(ws_reserve(ws, 2, Carve::bytes_for<int32_t>(tsum), stream, &base2));
     int32_t* T = (int32_t*)base2;
     k_compact_T<<<grid_for(K * 32, kThreads, 8), kThreads, 0, stream>>>(g, uv, off, toff, K, tbits,
-                                                                        T);
+                                                                        T, tdeg);
+    ++launches;
+    timer.stop(2);
+    timer.start(3);
     k_chunk_cost<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, need_k,
-                                                   need_q, chunk_cost, task_off, q);
+                                                   need_q, chunk_cost, task_off, q, d_stats);
     GS_TRY(exclusive_scan_i64(task_off, task_off, groups, tmp1, stream));
+    launches += 4;
+    timer.stop(3);
+    timer.start(4);
     k_quad<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, task_off, groups,
                                              need_k, need_q, k2, q);
+    ++launches;
+    timer.stop(4);
     GS_CUDA(cudaGetLastError());
+  } else {
+    for (int ph = 2; ph <= 4; ++ph) {
+      timer.start(ph);
+      timer.stop(ph);
+    }
   }
-  k_fold<<<fold_blocks, kThreads, 0, stream>>>(g, uv, K, t, four ? k2 : nullptr,
-                                                four ? q : nullptr, d_per_edge, part);
+  timer.start(5);
+  k_fold<<<fold_blocks, kThreads, 0, stream>>>(g, uv, K, t, four ? k2 : nullptr, four ? q : nullptr,
+                                                four ? tdeg : nullptr, gr->nbr_degsum, need_k,
+                                                need_q, d_per_edge, part, d_stats);
   k_fold_final<<<1, 32, 0, stream>>>(part, fold_blocks, d_sums);
+  launches += 2;
+  timer.stop(5);
+  ws->launches_total += launches - before;
   GS_CUDA(cudaGetLastError());
   unsigned long long h[32];
+  unsigned long long hs[8];
+  int64_t ntasks = 0;
   GS_CUDA(cudaMemcpyAsync(h, d_sums, sizeof(h), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaMemcpyAsync(hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, stream));
+  if (four)
+    GS_CUDA(cudaMemcpyAsync(&ntasks, task_off + groups, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            stream));
   GS_CUDA(cudaStreamSynchronize(stream));
   static const uint32_t bit[8] = {GS_G3, GS_G4, GS_G7, GS_G8, GS_G9, GS_G10, GS_G11, GS_G12};
   for (int i = 0; i < 8; ++i) {
@@ -721,6 +816,21 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
     h_sums->sum[i][1] = h[2 * i + 1];
     h_sums->sumsq[i][0] = h[2 * (8 + i)];
     h_sums->sumsq[i][1] = h[2 * (8 + i) + 1];
+  }
+  gs_stats& st = ws->stats;
+  st.k = K;
+  st.tri_tests = (int64_t)hs[0];
+  st.quad_tests = (int64_t)hs[1];
+  st.model_bytes = hs[2] + hs[3];
+  st.model_tri_bytes = hs[2];
+  st.model_quad_bytes = hs[3];
+  st.t_sum = tsum;
+  st.tasks = ntasks;
+  st.launches = launches;
+  st.timed = ws->timing;
+  if (ws->timing) {
+    float* ms[6] = {&st.ms_prep, &st.ms_tri, &st.ms_compact, &st.ms_cost, &st.ms_quad, &st.ms_fold};
+    for (int ph = 0; ph < 6; ++ph) cudaEventElapsedTime(ms[ph], ws->ev[2 * ph], ws->ev[2 * ph + 1]);
   }
   return GS_OK;
 }

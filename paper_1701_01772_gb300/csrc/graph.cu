@@ -70,6 +70,22 @@ __global__ void k_upper(const int64_t* __restrict__ row_ptr, const int32_t* __re
   if ((threadIdx.x & 31) == 0) atomicMax(max_deg, local_max);
 }
 
+// Sum of the degrees of each vertex's neighbours (one warp per vertex).
+__global__ void k_nbr_degsum(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                             int64_t n, int64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    long long s = 0;
+    for (int64_t p = row_ptr[v] + lane; p < row_ptr[v + 1]; p += 32) {
+      int32_t w = col[p];
+      s += row_ptr[w + 1] - row_ptr[w];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[v] = s;
+  }
+}
+
 // ------------------------------------------------------------- hub index
 // "Hubs" are the vertices of highest degree. Two structures are built once
 // per graph and reused by every request:
@@ -386,6 +402,7 @@ extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_
   }
   int64_t tmp_elems = scan_tmp_elems(n);
   if (cudaMalloc(&g->up_ptr, sizeof(int64_t) * (size_t)(n > 0 ? n : 1)) != cudaSuccess ||
+      cudaMalloc(&g->nbr_degsum, sizeof(int64_t) * (size_t)(n > 0 ? n : 1)) != cudaSuccess ||
       cudaMalloc(&g->edge_off, sizeof(int64_t) * (size_t)(n + 1)) != cudaSuccess ||
       cudaMalloc(&tmp, sizeof(int64_t) * (size_t)tmp_elems) != cudaSuccess) {
     cudaFree(d_err);
@@ -395,6 +412,8 @@ extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_
   }
   g->dev.up_ptr = g->up_ptr;
   if (n > 0) {
+    k_nbr_degsum<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(d_row_ptr, d_col, n,
+                                                               g->nbr_degsum);
     k_upper<<<grid_for(n, 256, 8), 256, 0, stream>>>(d_row_ptr, d_col, n, g->up_ptr, g->edge_off,
                                                      d_max);
   }
@@ -423,6 +442,7 @@ extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_
 extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   if (g == nullptr) return GS_OK;
   cudaFree(g->up_ptr);
+  cudaFree(g->nbr_degsum);
   cudaFree(g->edge_off);
   cudaFree(g->bm_slot);
   cudaFree(g->bm_bits);
@@ -550,6 +570,7 @@ gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint
   int64_t* tmp = c.take<int64_t>(scan_tmp_elems(tiles));
   k_sample_count<<<(unsigned)tiles, kSampThreads, 0, stream>>>(m, seed, threshold, cnt);
   GS_TRY(exclusive_scan_i64(cnt, off, tiles, tmp, stream));
+  ws->launches_total += 4;
   int64_t kept = 0;
   GS_CUDA(cudaMemcpyAsync(&kept, off + tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
   GS_CUDA(cudaStreamSynchronize(stream));
@@ -564,9 +585,11 @@ gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint
               (long long)max_k);
     return GS_ECAPACITY;
   }
-  if (kept > 0)
+  if (kept > 0) {
     k_sample_write<<<(unsigned)tiles, kSampThreads, 0, stream>>>(
         g->dev.col, g->up_ptr, g->edge_off, g->dev.n, m, seed, threshold, off, d_pairs);
+    ws->launches_total += 1;
+  }
   GS_CUDA(cudaGetLastError());
   return GS_OK;
 }

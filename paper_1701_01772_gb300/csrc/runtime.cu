@@ -194,7 +194,30 @@ gs_status gs_workspace_destroy(gs_workspace* ws) {
       cudaStreamSynchronize(ws->last_stream);
       cudaFree(ws->buf[i]);
     }
+  if (ws->ev[0] != nullptr)
+    for (int i = 0; i < 12; ++i) cudaEventDestroy(ws->ev[i]);
   delete ws;
+  return GS_OK;
+}
+
+gs_status gs_workspace_set_timing(gs_workspace* ws, int enable) {
+  if (ws == nullptr) {
+    gs::set_error("gs_workspace_set_timing: null workspace");
+    return GS_EINVAL;
+  }
+  if (enable && ws->ev[0] == nullptr)
+    for (int i = 0; i < 12; ++i) GS_CUDA(cudaEventCreate(&ws->ev[i]));
+  ws->timing = enable ? 1 : 0;
+  return GS_OK;
+}
+
+gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out) {
+  if (ws == nullptr || out == nullptr) {
+    gs::set_error("gs_count_stats: null argument");
+    return GS_EINVAL;
+  }
+  *out = ws->stats;
+  out->launches_total = ws->launches_total;
   return GS_OK;
 }
 
