@@ -55,6 +55,10 @@ struct DevGraph {
   const int32_t* tb_slot;   // [n] table slot of v, -1 if none (NULL if no table)
   const uint32_t* tb_codeg; // [tb_count][tb_count]
   int64_t tb_count;
+  // adjacency among table vertices as a bit matrix over table slots
+  // (tb_count^2 bits, small enough to stay in L2)
+  const uint32_t* hm_bits;  // [tb_count][hm_words]
+  int64_t hm_words;         // ceil(tb_count / 32)
 };
 
 // Membership of x in the sorted list a[0..len): branch-free halving search.
@@ -71,9 +75,25 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* __restrict__ a, i
   return __ldg(base) == x;
 }
 
-// Membership of x in N(y): bitmap test for hubs, halving search otherwise.
+// Table slot of v, or -1 (also when there is no table).
+__device__ __forceinline__ int32_t table_slot(const DevGraph& g, int32_t v) {
+  return (g.hm_bits != nullptr && v >= 0) ? __ldg(g.tb_slot + v) : -1;
+}
+
+// Membership of x in N(y): hub-pair bit matrix when both are table hubs,
+// bitmap test for bitmap hubs, halving search otherwise.
 __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64_t base_y,
                                              int64_t deg_y, int32_t x) {
+  if (g.hm_bits != nullptr) {
+    int32_t ys = __ldg(g.tb_slot + y);
+    if (ys >= 0) {
+      int32_t xs = __ldg(g.tb_slot + x);
+      if (xs >= 0) {
+        uint32_t w = __ldg(g.hm_bits + (int64_t)ys * g.hm_words + (xs >> 5));
+        return (w >> (xs & 31)) & 1u;
+      }
+    }
+  }
   if (g.bm_slot != nullptr) {
     int32_t s = __ldg(g.bm_slot + y);
     if (s >= 0) {
@@ -85,10 +105,18 @@ __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64
 }
 
 // Membership of x in a set given either as a vertex's adjacency (vtx >= 0,
-// list = N(vtx)) or as a plain sorted list (vtx < 0).
-__device__ __forceinline__ bool set_contains(const DevGraph& g, int32_t vtx,
+// list = N(vtx)) or as a plain sorted list (vtx < 0). vslot is vtx's table
+// slot (-1 if none): when x also has one, the hub-pair bit matrix answers.
+__device__ __forceinline__ bool set_contains(const DevGraph& g, int32_t vtx, int32_t vslot,
                                              const int32_t* __restrict__ list, int64_t len,
                                              int32_t x) {
+  if (vslot >= 0) {
+    int32_t xs = __ldg(g.tb_slot + x);
+    if (xs >= 0) {
+      uint32_t w = __ldg(g.hm_bits + (int64_t)vslot * g.hm_words + (xs >> 5));
+      return (w >> (xs & 31)) & 1u;
+    }
+  }
   if (vtx >= 0 && g.bm_slot != nullptr) {
     int32_t s = __ldg(g.bm_slot + vtx);
     if (s >= 0) {
@@ -126,6 +154,7 @@ struct gs_graph {
   uint32_t* bm_bits;
   int32_t* tb_slot;
   uint32_t* tb_codeg;
+  uint32_t* hm_bits;
 };
 
 struct gs_workspace {

@@ -43,6 +43,10 @@ namespace gs {
 
 constexpr int kThreads = 256;
 constexpr int kBlocksPerSm = 4;
+#ifndef GS_QUAD_BLOCKS_PER_SM
+#define GS_QUAD_BLOCKS_PER_SM 8
+#endif
+constexpr int kQuadBlocksPerSm = GS_QUAD_BLOCKS_PER_SM;
 constexpr int64_t kTaskProbes = 1024;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kEmpty = ~0ull;
@@ -219,6 +223,7 @@ struct Seg {
   const int32_t* it;    // iterated list
   const int32_t* sl;    // searched list
   int32_t svtx;         // vertex whose adjacency sl is (bitmap-capable), or -1
+  int32_t sslot;        // table slot of svtx, or -1
   int32_t slen;         // length of sl
   int32_t cnt;          // number of tests
 };
@@ -288,6 +293,7 @@ __device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int6
     s.slen = (int32_t)dw;
     s.cnt = (int32_t)dob;
   }
+  s.sslot = table_slot(g, s.svtx);
 }
 
 __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
@@ -297,6 +303,7 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   it.a.cnt = it.b.cnt = 0;
   it.a.it = it.a.sl = it.b.it = it.b.sl = g.col;
   it.a.svtx = it.b.svtx = -1;
+  it.a.sslot = it.b.sslot = -1;
   it.a.slen = it.b.slen = 0;
   it.qconst = 0;
   it.bsign = 0;
@@ -322,6 +329,7 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
       it.a.it = T + c.toff + iw + 1;
       it.a.sl = g.col + bw;
       it.a.svtx = w;
+      it.a.sslot = table_slot(g, w);
       it.a.slen = (int32_t)dw;
       it.a.cnt = (int32_t)tg;
     }
@@ -348,6 +356,15 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
     }
   }
   (void)need_k;
+}
+
+// Out-of-line copy for k_quad: the item set-up runs once per chunk and its
+// temporaries would otherwise raise the register count of the test loop.
+__device__ __noinline__ void load_item_outlined(const DevGraph& g, const EdgeCtx& c,
+                                                const int32_t* __restrict__ T, int64_t i,
+                                                uint32_t tword, int lane, bool need_k,
+                                                bool need_q, Item& it) {
+  load_item(g, c, T, i, tword, lane, need_k, need_q, it);
 }
 
 template <class T>
@@ -403,12 +420,13 @@ struct SharedItem {
   const int32_t* it[2];
   const int32_t* sl[2];
   int32_t svtx[2];
+  int32_t sslot[2];
   int32_t slen[2];
   int32_t ca;
   int32_t bsign;
 };
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
            const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
            const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
@@ -423,46 +441,52 @@ __global__ void __launch_bounds__(kThreads)
   const int64_t per = (NT + warps - 1) / warps;
   const int64_t t0 = warp * per, t1 = min(NT, t0 + per);
   if (t0 >= t1) return;
-  const long long qa = need_q ? 2 : 0;  // q weight of a segment-A hit
   int64_t gi = last_le(task_off, groups, t0);
   int64_t e = last_le(off, K, gi * 32);
-  EdgeCtx c;
-  load_edge(g, uv, t, toff, e, c);
-  int64_t cur = -1;
+  int64_t cur = -1, cur_e = -1;
   int64_t start = 0, ctotal = 0;
-  unsigned long long acc_k = 0;
-  long long acc_q = 0;
+  unsigned acc_k = 0;
+  int acc_q = 0;
   for (int64_t task = t0; task < t1; ++task) {
     while (gi + 1 < groups && __ldg(task_off + gi + 1) <= task) ++gi;
     if (gi != cur) {
       // flush the previous chunk's counts to its edge
-      unsigned long long sk = warp_sum<unsigned long long>(acc_k);
-      long long sq = warp_sum<long long>(acc_q);
+      const unsigned long long sk = warp_sum<unsigned long long>(acc_k);
+      const long long sq = warp_sum<long long>(acc_q);
       if (lane == 0 && cur >= 0) {
-        if (sk) atomicAdd(k_out + c.e, sk);
-        if (sq) atomicAdd(q + c.e, (unsigned long long)sq);
+        if (sk) atomicAdd(k_out + cur_e, sk);
+        if (sq) atomicAdd(q + cur_e, (unsigned long long)sq);
       }
       acc_k = 0;
       acc_q = 0;
       while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
-      if (e != c.e) load_edge(g, uv, t, toff, e, c);
-      Item it;
-      load_item(g, c, T, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k,
-                need_q, it);
-      __syncwarp();
-      SharedItem& si = my[lane];
-      si.it[0] = it.a.it;
-      si.it[1] = it.b.it;
-      si.sl[0] = it.a.sl;
-      si.sl[1] = it.b.sl;
-      si.svtx[0] = it.a.svtx;
-      si.svtx[1] = it.b.svtx;
-      si.slen[0] = it.a.slen;
-      si.slen[1] = it.b.slen;
-      si.ca = it.a.cnt;
-      si.bsign = it.bsign;
-      __syncwarp();
-      int64_t mine = (int64_t)it.a.cnt + it.b.cnt, incl = mine;
+      int64_t mine;
+      {
+        EdgeCtx c;
+        load_edge(g, uv, t, toff, e, c);
+        Item it;
+        load_item_outlined(g, c, T, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane,
+                           need_k, need_q, it);
+        __syncwarp();
+        SharedItem& si = my[lane];
+        si.it[0] = it.a.it;
+        si.it[1] = it.b.it;
+        si.sl[0] = it.a.sl;
+        si.sl[1] = it.b.sl;
+        si.svtx[0] = it.a.svtx;
+        si.svtx[1] = it.b.svtx;
+        si.sslot[0] = it.a.sslot;
+        si.sslot[1] = it.b.sslot;
+        si.slen[0] = it.a.slen;
+        si.slen[1] = it.b.slen;
+        si.ca = it.a.cnt;
+        // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2
+        // when q is wanted); segment B adds +-1 to q
+        si.bsign = it.bsign;
+        mine = (int64_t)it.a.cnt + it.b.cnt;
+        __syncwarp();
+      }
+      int64_t incl = mine;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         int64_t y = __shfl_up_sync(kFull, incl, d);
@@ -471,11 +495,12 @@ __global__ void __launch_bounds__(kThreads)
       start = incl - mine;
       ctotal = __shfl_sync(kFull, incl, 31);
       cur = gi;
+      cur_e = e;
     }
-    const int64_t sub = task - __ldg(task_off + gi);
-    const int64_t lo = sub * kTaskProbes, hi = min(ctotal, lo + kTaskProbes);
-    for (int64_t r0 = lo; r0 < hi; r0 += 32) {
-      const int64_t rr = r0 + lane;
+    const int64_t lo = (task - __ldg(task_off + gi)) * kTaskProbes;
+    const int32_t len = (int32_t)min(ctotal - lo, kTaskProbes);
+    for (int32_t r = lane; r - lane < len; r += 32) {
+      const int64_t rr = lo + r;
       // item j = last lane whose start <= rr
       int j = 0;
 #pragma unroll
@@ -484,16 +509,17 @@ __global__ void __launch_bounds__(kThreads)
         if (s <= rr) j += step;
       }
       const int64_t sj = __shfl_sync(kFull, start, j);
-      if (rr < hi) {
+      if (r < len) {
         const SharedItem& si = my[j];
-        int64_t o = rr - sj;
+        int32_t o = (int32_t)(rr - sj);
         const int seg = o < si.ca ? 0 : 1;
         if (seg) o -= si.ca;
-        const bool hit = set_contains(g, si.svtx[seg], si.sl[seg], si.slen[seg], __ldg(si.it[seg] + o));
+        const bool hit = set_contains(g, si.svtx[seg], si.sslot[seg], si.sl[seg], si.slen[seg],
+                                      __ldg(si.it[seg] + o));
         if (hit) {
           if (seg == 0) {
             ++acc_k;
-            acc_q += qa;
+            acc_q += need_q ? 2 : 0;
           } else {
             acc_q += si.bsign;
           }
@@ -501,11 +527,11 @@ __global__ void __launch_bounds__(kThreads)
       }
     }
   }
-  unsigned long long sk = warp_sum<unsigned long long>(acc_k);
-  long long sq = warp_sum<long long>(acc_q);
+  const unsigned long long sk = warp_sum<unsigned long long>(acc_k);
+  const long long sq = warp_sum<long long>(acc_q);
   if (lane == 0 && cur >= 0) {
-    if (sk) atomicAdd(k_out + c.e, sk);
-    if (sq) atomicAdd(q + c.e, (unsigned long long)sq);
+    if (sk) atomicAdd(k_out + cur_e, sk);
+    if (sq) atomicAdd(q + cur_e, (unsigned long long)sq);
   }
 }
 
@@ -780,7 +806,7 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
     launches += 4;
     timer.stop(3);
     timer.start(4);
-    k_quad<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, task_off, groups,
+    k_quad<<<sms * kQuadBlocksPerSm, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, task_off, groups,
                                              need_k, need_q, k2, q);
     ++launches;
     timer.stop(4);

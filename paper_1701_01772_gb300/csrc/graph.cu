@@ -140,6 +140,21 @@ __global__ void k_hub_bitmaps(const int64_t* __restrict__ row_ptr,
   }
 }
 
+// Hub-pair bit matrix: bit s2 of row s1 set iff table hubs s1 and s2 are
+// adjacent. One block per table hub.
+__global__ void k_hub_matrix(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                             const int32_t* __restrict__ slot, const int32_t* __restrict__ hubs,
+                             int64_t count, int64_t words, uint32_t* __restrict__ bits) {
+  for (int64_t h = blockIdx.x; h < count; h += gridDim.x) {
+    int32_t v = hubs[h];
+    uint32_t* row = bits + h * words;
+    for (int64_t p = row_ptr[v] + threadIdx.x; p < row_ptr[v + 1]; p += blockDim.x) {
+      int32_t s = __ldg(slot + col[p]);
+      if (s >= 0) atomicOr(row + (s >> 5), 1u << (s & 31));
+    }
+  }
+}
+
 // Number of table hubs among the neighbours of each vertex.
 __global__ void k_hub_nbr_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const int32_t* __restrict__ slot, int64_t n,
@@ -318,6 +333,16 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     if (n_tb > 1) {
       int32_t* hubs = nullptr;
       GS_TRY(assign(d_tb, &g->tb_slot, &hubs, n_tb));
+      const int64_t hm_words = (n_tb + 31) / 32;
+      cudaError_t he = cudaMalloc(&g->hm_bits, sizeof(uint32_t) * (size_t)(hm_words * n_tb));
+      if (he != cudaSuccess) {
+        cudaFree(hubs);
+        return cuda_fail(he, "hub matrix", __FILE__, __LINE__);
+      }
+      GS_CUDA(cudaMemsetAsync(g->hm_bits, 0, sizeof(uint32_t) * (size_t)(hm_words * n_tb), stream));
+      k_hub_matrix<<<grid_for(n_tb * 256, 256, 8), 256, 0, stream>>>(
+          g->dev.row_ptr, g->dev.col, g->tb_slot, hubs, n_tb, hm_words, g->hm_bits);
+      GS_CUDA(cudaStreamSynchronize(stream));
       cudaFree(hubs);
       GS_CUDA(cudaMalloc(&g->tb_codeg, sizeof(uint32_t) * (size_t)(n_tb * n_tb)));
       GS_CUDA(cudaMemsetAsync(g->tb_codeg, 0, sizeof(uint32_t) * (size_t)(n_tb * n_tb), stream));
@@ -347,6 +372,8 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       g->dev.tb_slot = g->tb_slot;
       g->dev.tb_codeg = g->tb_codeg;
       g->dev.tb_count = n_tb;
+      g->dev.hm_bits = g->hm_bits;
+      g->dev.hm_words = hm_words;
     }
   }
   return GS_OK;
@@ -448,6 +475,7 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->bm_bits);
   cudaFree(g->tb_slot);
   cudaFree(g->tb_codeg);
+  cudaFree(g->hm_bits);
   delete g;
   return GS_OK;
 }
