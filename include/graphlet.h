@@ -211,6 +211,39 @@ gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, double fraction
                             uint32_t mask, double z, gs_result* out, int64_t* k_out,
                             void* stream);
 
+/* ------------------------------------------------------------------------
+ * Counting without device allocation. (The paper has no counterpart: this
+ * entry point exists for callers of the library, not for the method.)
+ *
+ * gs_count3_static computes the same triangle / 2-star sums as gs_count
+ * with mask GS_G3 and/or GS_G4 (the mask must be a non-empty subset of
+ * GS_THREE_NODE), but never calls cudaMalloc, cudaFree or any allocating
+ * routine. It is meant for callers that cannot allocate device memory at
+ * the time they count: code recording a CUDA graph (allocation is illegal
+ * while a stream is captured), hosts that give the GPU a fixed memory pool
+ * and forbid growth, or latency paths where a device-wide synchronising
+ * cudaMalloc/cudaFree is not acceptable. The graph must still have been
+ * registered with gs_graph_create beforehand.
+ *
+ * Its scratch is one file-scope device array of GS_STATIC_SCRATCH_BYTES
+ * (48 MiB), reserved on every GPU that loads the library until the process
+ * exits. d_pairs: device int32[2*k], k <= GS_STATIC_MAX_PAIRS (2^20), each
+ * pair an edge in either orientation, no edge twice; larger k is rejected
+ * with GS_ECAPACITY (use gs_count). h_sums is host memory. The call
+ * synchronises `stream`.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture begins. All calls share the one array and it keeps the
+ * previous call's contents (the call clears what must start at zero), so
+ * calls whose GPU work overlaps -- on different streams or host threads,
+ * for the same device -- race and give wrong results: serialise them.
+ * ------------------------------------------------------------------------ */
+#define GS_STATIC_MAX_PAIRS (1 << 20)
+#define GS_STATIC_SCRATCH_BYTES (48u << 20)
+gs_status gs_count3_static(const gs_graph* g, const int32_t* d_pairs, int64_t k, uint32_t mask,
+                           gs_sums* h_sums, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

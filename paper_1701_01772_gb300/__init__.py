@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
         "gs_count_estimate": ([P, P, D, U64, U32, D, ctypes.POINTER(GsResult), PI64, P],
                               ctypes.c_int32),
         "gs_workspace_set_timing": ([P, ctypes.c_int], ctypes.c_int32),
+        "gs_count3_static": ([P, P, I64, U32, ctypes.POINTER(GsSums), P], ctypes.c_int32),
         "gs_count_stats": ([P, ctypes.POINTER(GsStats)], ctypes.c_int32),
     }
     for name, (args, res) in sig.items():
@@ -225,6 +226,21 @@ def gs_count(graph: int, ws: int, pairs, k: int, mask: int = GS_CONNECTED, per_e
                           k, mask,
                           None if per_edge is None else _dev(per_edge, torch.int64, "per_edge"),
                           ctypes.byref(out), _stream_ptr(stream)))
+    return out
+
+
+GS_STATIC_MAX_PAIRS = 1 << 20
+
+
+def gs_count3_static(graph: int, pairs, k: int, mask: int = GS_THREE_NODE,
+                     stream=None) -> GsSums:
+    """Triangle / 2-star sums like gs_count, using only the library's fixed
+    static scratch (no device allocation); k <= GS_STATIC_MAX_PAIRS. See
+    include/graphlet.h for who needs it and its concurrency rules."""
+    import torch
+    out = GsSums()
+    _check(lib().gs_count3_static(graph, None if pairs is None else _dev(pairs, torch.int32, "pairs"),
+                                  k, mask, ctypes.byref(out), _stream_ptr(stream)))
     return out
 
 

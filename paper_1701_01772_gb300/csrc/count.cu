@@ -174,6 +174,13 @@ __global__ void __launch_bounds__(kThreads) k_tri(DevGraph g, const int2* __rest
   }
 }
 
+// Host launcher of the unpadded triangle pass for count_static.cu (a
+// kernel template can only be launched from the file that defines it).
+void launch_tri_unpadded(const DevGraph& g, const int2* uv, const int64_t* off, int64_t K,
+                         unsigned long long* t, int blocks, cudaStream_t stream) {
+  k_tri<false><<<blocks, kThreads, 0, stream>>>(g, uv, off, K, t, nullptr);
+}
+
 // ---------------------------------------------------------------- compact T
 
 // Writes T_e in order and tdeg[e] = sum of the degrees of T_e's members
