@@ -286,10 +286,16 @@ def run_gpu(args, rank, world, device):
     peak, peak_kind = load_peaks()
     achieved = (quad_bytes / (quad_ms / 1e3)) / 1e9 if quad_ms > 0 else 0.0
     traffic = load_traffic("k_quad")
+    tests_per_launch = quad_tests / max(quad_launches, 1)
+    traffic_bytes = (traffic["dram_bytes_per_test"] * tests_per_launch) if traffic else None
+    avg_s = quad_ms / max(quad_launches, 1) / 1e3
     roofline = {"kernel": "k_quad (4-node membership tests)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "traffic": round(traffic_bytes) if traffic_bytes else None,
+                "traffic_source": ("ncu dram bytes per membership test on a 0.1% sample x tests "
+                                   "per launch") if traffic else None,
+                "dram_frac": round(traffic_bytes / avg_s / 1e9 / peak, 4) if traffic_bytes else None,
                 "avg_launch_ms": round(quad_ms / max(quad_launches, 1), 3),
                 "model_bytes_per_launch": quad_bytes // max(quad_launches, 1),
                 "tests_per_s": round(quad_tests / (quad_ms / 1e3), 1) if quad_ms > 0 else None}
