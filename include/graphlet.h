@@ -7,8 +7,8 @@
  * undirected graph, the connected 3- and 4-node graphlets that contain e
  * (Algorithm 2: triangles T_e and 2-stars S_u, S_v; Algorithm 3: 4-cliques;
  * Algorithm 4: 4-cycles), folds the per-edge counts into exact integer sums
- * and turns them into the unbiased estimates of Sec. 3 with a variance and
- * 95% bounds (Sec. 5.3).
+ * and turns them into the unbiased estimates of Sec. 2.3 with a variance and
+ * 95% bounds (Sec. 6.2).
  *
  * Conventions for every entry point:
  *   - Device pointers are CUDA global-memory pointers on the current device;
@@ -75,7 +75,7 @@ enum {
 #define GS_F_VAR_UNDEFINED 4u   /* fewer than 2 sampled edges: V, lb, ub are NaN */
 #define GS_F_OVERFLOW 8u        /* exact count does not fit uint64 */
 
-/* Exact integer sums over the sampled edges J (Sec. 3, Alg. 2 accumulators).
+/* Exact integer sums over the sampled edges J (Sec. 2.3, Alg. 2 accumulators).
  * For each graphlet i the per-edge numerator N_i(e) is the integer with
  * X_i = (M / K) * sum_e N_i(e) / D_i, D = (3, 2, 6, 1, 2, 4, 6, 1):
  *   N3 = t, N4 = a + b, N7 = k, N8 = C(t,2) - k, N9 = t(a+b) - 4 N8,
@@ -94,9 +94,9 @@ typedef struct {
 
 /* Estimates per graphlet, in the order (3, 4, 7, 8, 9, 10, 11, 12). */
 typedef struct {
-  double x[8];          /* X_i, Sec. 3 estimators with sigma = M / K */
+  double x[8];          /* X_i, Sec. 2.3 estimators with sigma = M / K */
   double var[8];        /* estimated Var[X_i] (see gs_estimate) */
-  double lb[8];         /* X_i - z sqrt(var) (Sec. 5.3) */
+  double lb[8];         /* X_i - z sqrt(var) (Sec. 6.2) */
   double ub[8];         /* X_i + z sqrt(var) */
   uint64_t exact[8];    /* sum N_i / D_i when K = M (flag GS_F_EXACT) */
   uint32_t flags[8];    /* GS_F_* */
@@ -111,7 +111,7 @@ const char* gs_last_error(void);
 /* Library version string. */
 const char* gs_version(void);
 
-/* Registers a simple undirected graph given as CSR (Sec. 3.1: ordered
+/* Registers a simple undirected graph given as CSR (Sec. 2.1: ordered
  * neighbour sets). d_row_ptr: device int64[n+1], d_col: device int32[nnz],
  * nnz = 2|E|, every list strictly increasing, both orientations present, no
  * self-loops. The arrays are borrowed (not copied) and must outlive the
@@ -166,12 +166,12 @@ gs_status gs_count(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs, 
                    uint32_t mask, int64_t* d_per_edge, gs_sums* h_sums, void* stream);
 
 /* Estimates from exact sums (host only, no GPU work):
- *   X_i   = (M / K) * sum N_i / D_i                  (Sec. 3, sigma = |E|/|J|)
+ *   X_i   = (M / K) * sum N_i / D_i                  (Sec. 2.3, sigma = |E|/|J|)
  *   var_i = M (M - K) (K sumsq_i - sum_i^2) / (K^2 (K - 1) D_i^2)
  *           -- the without-replacement design variance of the expansion
- *           estimator; the paper states bounds from Var[X] (Sec. 5.3) but
+ *           estimator; the paper states bounds from Var[X] (Sec. 6.2) but
  *           prints no formula for it, this is the library's choice.
- *   lb_i, ub_i = X_i -/+ z sqrt(var_i), z = 1.96 for 95% (Sec. 5.3).
+ *   lb_i, ub_i = X_i -/+ z sqrt(var_i), z = 1.96 for 95% (Sec. 6.2).
  * K = M gives var = 0 and exact counts. */
 gs_status gs_estimate(const gs_sums* s, double z, gs_result* out);
 

@@ -11,11 +11,11 @@ Statistics"):
   sets S_u, S_v via a marker table), Algorithm 3 (4-cliques through e) and
   Algorithm 4 read as counting pairs (w in S_u, r in S_v) with w ~ r
   (4-cycles through e).  Plain C in ``oracle.c``.
-* ``sums``          -- exact per-edge numerators N_i (Sec. 3, Eqs. for
+* ``sums``          -- exact per-edge numerators N_i (Sec. 2.3, Eqs. for
   X_3..X_12 with sigma = M/K) and their sums / sums of squares in 128-bit
   integers (C), returned as Python ints.
-* ``estimate``      -- the estimators X_i = (M/K) sum N_i / D_i (Sec. 3), the
-  variance V_i and the 95% bounds X -/+ 1.96 sqrt(V) (Sec. 5.3).  Exact
+* ``estimate``      -- the estimators X_i = (M/K) sum N_i / D_i (Sec. 2.3), the
+  variance V_i and the 95% bounds X -/+ 1.96 sqrt(V) (Sec. 6.2).  Exact
   rational arithmetic (``fractions.Fraction``) rounded once to fp64.
   The variance is this project's reading (the paper prints no formula): the
   design-based variance of the expansion estimator under simple random
@@ -141,9 +141,9 @@ def sample(row_ptr, col, fraction: float, seed: int) -> np.ndarray:
 def estimate(s: dict, s2: dict, m: int, k: int, z: float = Z95) -> dict:
     """Estimates, variances and bounds per graphlet from exact sums.
 
-    X = (M/K) * S / D                            (Sec. 3, sigma = |E|/|J|)
+    X = (M/K) * S / D                            (Sec. 2.3, sigma = |E|/|J|)
     V = M (M-K) (K S2 - S^2) / (K^2 (K-1) D^2)   (SRSWOR variance, K >= 2)
-    lb, ub = X -/+ z sqrt(V)                     (Sec. 5.3, z = 1.96)
+    lb, ub = X -/+ z sqrt(V)                     (Sec. 6.2, z = 1.96)
     exact = S / D when K == M (must divide).
     """
     res = {}

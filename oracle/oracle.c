@@ -12,7 +12,7 @@
  * shares no code with the GPU path.
  *
  * Graph: simple undirected, int64 row offsets + int32 sorted adjacency, both
- * orientations stored (the paper's "ordered" neighbour sets, Sec. 3.1).
+ * orientations stored (the paper's "ordered" neighbour sets, Sec. 2.1).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -30,7 +30,7 @@ typedef unsigned __int128 u128;
  *   L2: 2-star vertices of u, S_u = N(u) \ {v} \ N(v)
  * Labels carry an epoch per edge so Phi never needs clearing (the paper's
  * "unique lambda per neighbourhood" trick). u is the endpoint of smaller
- * degree (ties: smaller id), as in the complexity discussion of Sec. 3.4;
+ * degree (ties: smaller id), as in the complexity discussion of Sec. 2.5;
  * the counts do not depend on this choice.
  *
  * Outputs per edge j (all int64):
@@ -128,7 +128,7 @@ int oracle_local_counts_literal_alg4(int64_t n, const int64_t* row_ptr, const in
 /* ----------------------------------------------------------------------
  * Per-edge numerators N_i and their exact sums.
  *
- * With sigma = M/K the estimators of Sec. 3 (X_3..X_12, weights W) are
+ * With sigma = M/K the estimators of Sec. 2.3 (X_3..X_12, weights W) are
  * linear in per-edge terms: X_i = sigma * sum_e N_i(e) / D_i, where
  *   N3 = t                                  D3 = 3
  *   N4 = a + b                              D4 = 2

@@ -1,5 +1,5 @@
 // Edge-centric local counting over a sampled edge set J (Algorithms 2-4)
-// and the exact fold of the per-edge numerators (Sec. 3).
+// and the exact fold of the per-edge numerators (Sec. 2.3).
 //
 // For an edge e = (u, v) with d_u <= d_v (ties: smaller id is u), let
 // T = N(u) cap N(v), S_u = N(u) \ {v} \ T, S_v = N(v) \ {u} \ T. The paper's

@@ -1,4 +1,4 @@
-// Host-side estimators (Sec. 3), variance and confidence bounds (Sec. 5.3),
+// Host-side estimators (Sec. 2.3), variance and confidence bounds (Sec. 6.2),
 // plus the fused sample -> count -> estimate convenience call.
 #include <math.h>
 #include <string.h>

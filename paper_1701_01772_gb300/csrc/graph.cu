@@ -15,7 +15,7 @@ constexpr int64_t kHubMinDegree = 64;
 
 // ------------------------------------------------------------- validation
 // One warp per row (grid-stride). Checks the simple-graph conditions of
-// Sec. 3.1: ids in range, strictly increasing lists (sorted, no repeats),
+// Sec. 2.1: ids in range, strictly increasing lists (sorted, no repeats),
 // no self-loops, and symmetry (u lists v => v lists u, by halving search).
 __global__ void k_validate(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                            int64_t n, int64_t nnz, DevError* err) {

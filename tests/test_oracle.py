@@ -251,8 +251,8 @@ def test_variance_matches_two_pass_sample_variance():
 
 def test_unbiased_and_covering_over_seeds():
     """Mean of X over seeds approaches the exact count (unbiasedness,
-    Sec. 3.3) and the 95% interval covers it about 95% of the time
-    (Sec. 5.3)."""
+    Sec. 2.4) and the 95% interval covers it about 95% of the time
+    (Sec. 6.2)."""
     rp, col = synth.er(400, 8000, seed=31)
     m = len(col) // 2
     exact = oracle_exact(rp, col)
