@@ -64,11 +64,16 @@ def load_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the 4-node kernel's source with comments and blank space
+    removed, so that a comment edit does not invalidate recorded counters."""
+    import re
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1701_01772_gb300", "csrc", "count.cu"), "rb") as f:
-        h.update(f.read())
-    with open(os.path.join(ROOT, "paper_1701_01772_gb300", "csrc", "common.cuh"), "rb") as f:
-        h.update(f.read())
+    for name in ("count.cu", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_1701_01772_gb300", "csrc", name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 
