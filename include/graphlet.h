@@ -202,6 +202,14 @@ typedef struct {
  * recorded on the call's stream around each phase. */
 gs_status gs_workspace_set_timing(gs_workspace* ws, int enable);
 
+/* Launch choices for gs_count on this workspace (the batched path's
+ * autotuner searches the same knobs): resident CTAs per SM of the triangle
+ * pass (1..8) and of the 4-node pass (1..8), membership tests per 4-node
+ * work unit (32..2^20), and use_hubs = 0 to ignore the hub bitmaps,
+ * co-degree table and hub-pair matrix. Results do not depend on them. */
+gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_per_sm, int quad_blocks_per_sm,
+                                  int64_t task_probes, int use_hubs);
+
 /* Host output: statistics of the last gs_count that used `ws`. */
 gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
 
@@ -210,6 +218,98 @@ gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
 gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
                             uint32_t mask, double z, gs_result* out, int64_t* k_out,
                             void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched exact counts over many small graphs.
+ *
+ * The batch is given as one packed CSR: d_vtx_off (device int64[G+1]) holds
+ * each graph's first vertex, d_row_ptr (device int64[total_n+1]) the row
+ * offsets into d_col over the whole pack, and d_col (device int32[total_nnz])
+ * the sorted adjacency with ids LOCAL to each graph (0..n_g-1). The library
+ * registers the disjoint union of the graphs (edges never cross graphs, so
+ * every per-edge count of Algorithms 2-4 equals its value in its own graph),
+ * sizes all buffers once, optionally times a grid of launch choices
+ * (GS_BATCH_AUTOTUNE) and captures the whole counting sequence into one CUDA
+ * graph. d_vtx_off and d_row_ptr are borrowed until gs_batch_destroy; d_col
+ * is copied. flags: GS_VALIDATE and/or GS_BATCH_AUTOTUNE.
+ * ------------------------------------------------------------------------ */
+#define GS_BATCH_AUTOTUNE 2u
+typedef struct gs_batch gs_batch;
+typedef struct {
+  int64_t num_graphs;
+  int64_t edges;            /* total edges of the batch */
+  int32_t tri_blocks_per_sm, quad_blocks_per_sm;
+  int64_t task_probes;
+  int32_t use_hubs;         /* launch choices in the captured graph */
+  int32_t candidates;       /* autotuner candidates timed (0 = not tuned) */
+  float best_ms, worst_ms;  /* autotuner: fastest and slowest candidate */
+  int64_t graph_kernels;    /* kernel launches inside the captured graph */
+  uint64_t workspace_bytes;
+} gs_batch_stats;
+
+gs_status gs_batch_create(const int64_t* d_vtx_off, const int64_t* d_row_ptr, const int32_t* d_col,
+                          int64_t num_graphs, int64_t total_n, int64_t total_nnz, uint32_t mask,
+                          uint32_t flags, uint64_t hub_budget_bytes, void* stream,
+                          gs_batch** out);
+/* Exact sums for every graph of the batch (K = M of each graph, so
+ * gs_estimate gives exact counts): one CUDA-graph launch, then the
+ * per-graph sums are copied to h_sums (host gs_sums[num_graphs]).
+ * Synchronises `stream`. */
+gs_status gs_batch_count(gs_batch* b, gs_sums* h_sums, void* stream);
+gs_status gs_batch_info(const gs_batch* b, gs_batch_stats* out);
+gs_status gs_batch_destroy(gs_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Serving: estimation requests over resident graphs, batched continuously.
+ *
+ * gs_server_add_graph registers a graph (device CSR as for gs_graph_create,
+ * borrowed until gs_server_start copies it into the server's union graph);
+ * gs_server_start builds the union and its index and starts `lanes` worker
+ * threads, each with its own CUDA stream. A request names a graph, a
+ * graphlet mask, a sample fraction (Algorithm 1, same sampler and seed
+ * semantics as gs_sample on that graph alone), a seed and z. Workers take
+ * queued requests in arrival order into a batch while the batch's estimated
+ * device memory fits hbm_budget_bytes next to the batches other workers
+ * hold, sample them, and count the whole batch in one pass with a separate
+ * exact fold per request; a request's result is identical to running it
+ * alone. gs_server_wait blocks until a ticket's result is ready (or
+ * timeout_s passes: GS_ETIMEOUT, the request stays queued). Latencies are
+ * measured on the host from submit to completion.
+ * ------------------------------------------------------------------------ */
+typedef struct gs_server gs_server;
+typedef struct {
+  int32_t graph;        /* id from gs_server_add_graph */
+  uint32_t mask;        /* GS_* graphlet bits */
+  double fraction;      /* edge-sample fraction in [0, 1] */
+  uint64_t seed;
+  double z;             /* bound width, 1.96 for 95% */
+} gs_request;
+typedef struct {
+  int64_t k;            /* sampled edges */
+  int64_t batch_size;   /* requests counted in the same pass */
+  double queue_s;       /* submit -> batch start */
+  double latency_s;     /* submit -> result ready */
+  int64_t est_bytes;    /* memory estimate used for admission */
+} gs_request_stats;
+typedef struct {
+  int64_t graphs, batches, completed, pending;
+  double mean_batch;
+  uint64_t peak_reserved_bytes, budget_bytes;
+  int32_t peak_in_flight;  /* most batches on the device at once */
+} gs_server_stats;
+
+gs_status gs_server_create(uint64_t hbm_budget_bytes, int32_t max_batch, int32_t lanes,
+                           gs_server** out);
+gs_status gs_server_add_graph(gs_server* s, const int64_t* d_row_ptr, const int32_t* d_col,
+                              int64_t n, int64_t nnz, int32_t* graph_id);
+gs_status gs_server_start(gs_server* s, uint32_t flags, uint64_t hub_budget_bytes, void* stream);
+/* GS_EBUDGET if the request alone exceeds the budget. */
+gs_status gs_server_submit(gs_server* s, const gs_request* r, uint64_t* ticket);
+gs_status gs_server_wait(gs_server* s, uint64_t ticket, double timeout_s, gs_result* out,
+                         gs_request_stats* stats);
+gs_status gs_server_info(gs_server* s, gs_server_stats* out);
+/* Stops the workers after the queued requests finish, frees everything. */
+gs_status gs_server_destroy(gs_server* s);
 
 /* ------------------------------------------------------------------------
  * Counting without device allocation. (The paper has no counterpart: this

@@ -87,6 +87,44 @@ class GsStats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class GsBatchStats(ctypes.Structure):
+    _fields_ = [("num_graphs", ctypes.c_int64), ("edges", ctypes.c_int64),
+                ("tri_blocks_per_sm", ctypes.c_int32), ("quad_blocks_per_sm", ctypes.c_int32),
+                ("task_probes", ctypes.c_int64), ("use_hubs", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float),
+                ("worst_ms", ctypes.c_float), ("graph_kernels", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+GS_BATCH_AUTOTUNE = 2
+
+
+class GsRequest(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_int32), ("mask", ctypes.c_uint32), ("fraction", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("z", ctypes.c_double)]
+
+
+class GsRequestStats(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("batch_size", ctypes.c_int64), ("queue_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("est_bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class GsServerStats(ctypes.Structure):
+    _fields_ = [("graphs", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("mean_batch", ctypes.c_double), ("peak_reserved_bytes", ctypes.c_uint64),
+                ("budget_bytes", ctypes.c_uint64), ("peak_in_flight", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib_handle = None
 
 
@@ -119,6 +157,21 @@ def lib() -> ctypes.CDLL:
                               ctypes.c_int32),
         "gs_workspace_set_timing": ([P, ctypes.c_int], ctypes.c_int32),
         "gs_count3_static": ([P, P, I64, U32, ctypes.POINTER(GsSums), P], ctypes.c_int32),
+        "gs_workspace_set_tuning": ([P, ctypes.c_int, ctypes.c_int, I64, ctypes.c_int],
+                                    ctypes.c_int32),
+        "gs_batch_create": ([P, P, P, I64, I64, I64, U32, U32, U64, P, PP], ctypes.c_int32),
+        "gs_batch_count": ([P, ctypes.POINTER(GsSums), P], ctypes.c_int32),
+        "gs_batch_info": ([P, ctypes.POINTER(GsBatchStats)], ctypes.c_int32),
+        "gs_batch_destroy": ([P], ctypes.c_int32),
+        "gs_server_create": ([U64, ctypes.c_int32, ctypes.c_int32, PP], ctypes.c_int32),
+        "gs_server_add_graph": ([P, P, P, I64, I64, ctypes.POINTER(ctypes.c_int32)],
+                                ctypes.c_int32),
+        "gs_server_start": ([P, U32, U64, P], ctypes.c_int32),
+        "gs_server_submit": ([P, ctypes.POINTER(GsRequest), ctypes.POINTER(U64)], ctypes.c_int32),
+        "gs_server_wait": ([P, U64, D, ctypes.POINTER(GsResult), ctypes.POINTER(GsRequestStats)],
+                           ctypes.c_int32),
+        "gs_server_info": ([P, ctypes.POINTER(GsServerStats)], ctypes.c_int32),
+        "gs_server_destroy": ([P], ctypes.c_int32),
         "gs_count_stats": ([P, ctypes.POINTER(GsStats)], ctypes.c_int32),
     }
     for name, (args, res) in sig.items():
@@ -244,6 +297,42 @@ def gs_count3_static(graph: int, pairs, k: int, mask: int = GS_THREE_NODE,
     return out
 
 
+def gs_workspace_set_tuning(handle: int, tri_blocks_per_sm: int, quad_blocks_per_sm: int,
+                            task_probes: int, use_hubs: bool) -> None:
+    _check(lib().gs_workspace_set_tuning(handle, tri_blocks_per_sm, quad_blocks_per_sm,
+                                         task_probes, int(use_hubs)))
+
+
+def gs_batch_create(vtx_off, row_ptr, col, mask: int = GS_CONNECTED, flags: int = GS_VALIDATE,
+                    hub_budget_bytes: int = 0, stream=None) -> int:
+    """vtx_off: CUDA int64 [G+1]; row_ptr: CUDA int64 [N+1] (offsets into col);
+    col: CUDA int32 [nnz] with graph-local ids."""
+    import torch
+    h = ctypes.c_void_p()
+    _check(lib().gs_batch_create(_dev(vtx_off, torch.int64, "vtx_off"),
+                                 _dev(row_ptr, torch.int64, "row_ptr"),
+                                 _dev(col, torch.int32, "col") if col.numel() else None,
+                                 vtx_off.numel() - 1, row_ptr.numel() - 1, col.numel(), mask, flags,
+                                 hub_budget_bytes, _stream_ptr(stream), ctypes.byref(h)))
+    return h.value
+
+
+def gs_batch_count(handle: int, num_graphs: int, stream=None):
+    out = (GsSums * num_graphs)()
+    _check(lib().gs_batch_count(handle, out, _stream_ptr(stream)))
+    return out
+
+
+def gs_batch_info(handle: int) -> dict:
+    out = GsBatchStats()
+    _check(lib().gs_batch_info(handle, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def gs_batch_destroy(handle: int) -> None:
+    _check(lib().gs_batch_destroy(handle))
+
+
 def gs_estimate(sums: GsSums, z: float = 1.96) -> GsResult:
     out = GsResult()
     _check(lib().gs_estimate(ctypes.byref(sums), z, ctypes.byref(out)))
@@ -270,6 +359,11 @@ class Workspace:
 
     def set_timing(self, enable: bool = True) -> None:
         gs_workspace_set_timing(self.handle, enable)
+
+    def set_tuning(self, tri_blocks_per_sm: int = 4, quad_blocks_per_sm: int = 8,
+                   task_probes: int = 1024, use_hubs: bool = True) -> None:
+        gs_workspace_set_tuning(self.handle, tri_blocks_per_sm, quad_blocks_per_sm, task_probes,
+                                use_hubs)
 
     def stats(self) -> dict:
         return gs_count_stats(self.handle).as_dict()
@@ -333,6 +427,152 @@ class Graph:
             self.ws.close()
         if getattr(self, "handle", None):
             gs_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many small graphs counted exactly in one CUDA-graph launch."""
+
+    def __init__(self, vtx_off, row_ptr, col, mask: int = GS_CONNECTED, autotune: bool = True,
+                 validate: bool = True, hub_budget_bytes: int = 0, stream=None):
+        self.vtx_off, self.row_ptr, self.col = vtx_off, row_ptr, col
+        self.num_graphs = vtx_off.numel() - 1
+        flags = (GS_VALIDATE if validate else 0) | (GS_BATCH_AUTOTUNE if autotune else 0)
+        self.handle = gs_batch_create(vtx_off, row_ptr, col, mask, flags, hub_budget_bytes, stream)
+
+    @classmethod
+    def from_graphs(cls, graphs, device="cuda", **kw):
+        """graphs: list of (row_ptr, col) numpy arrays (local ids)."""
+        import numpy as np
+        import torch
+        g = len(graphs)
+        vtx_off = np.zeros(g + 1, dtype=np.int64)
+        nnz_off = np.zeros(g + 1, dtype=np.int64)
+        for i, (rp, c) in enumerate(graphs):
+            vtx_off[i + 1] = vtx_off[i] + len(rp) - 1
+            nnz_off[i + 1] = nnz_off[i] + len(c)
+        row_ptr = np.empty(vtx_off[-1] + 1, dtype=np.int64)
+        col = np.empty(nnz_off[-1], dtype=np.int32)
+        for i, (rp, c) in enumerate(graphs):
+            row_ptr[vtx_off[i]:vtx_off[i + 1]] = rp[:-1] + nnz_off[i]
+            col[nnz_off[i]:nnz_off[i + 1]] = c
+        row_ptr[-1] = nnz_off[-1]
+        t = lambda a, dt: torch.as_tensor(a, dtype=dt).to(device)  # noqa: E731
+        return cls(t(vtx_off, torch.int64), t(row_ptr, torch.int64), t(col, torch.int32), **kw)
+
+    def count(self, stream=None):
+        return gs_batch_count(self.handle, self.num_graphs, stream)
+
+    def exact(self, stream=None) -> list:
+        """Exact counts {graphlet: count} per graph."""
+        out = []
+        for s in self.count(stream):
+            r = gs_estimate(s).as_dict()
+            out.append({g: r[g]["exact"] if s.k > 0 else 0 for g in r})
+        return out
+
+    def info(self) -> dict:
+        return gs_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ serving
+
+def gs_server_create(hbm_budget_bytes: int, max_batch: int = 64, lanes: int = 2) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().gs_server_create(hbm_budget_bytes, max_batch, lanes, ctypes.byref(h)))
+    return h.value
+
+
+def gs_server_add_graph(server: int, row_ptr, col) -> int:
+    import torch
+    gid = ctypes.c_int32()
+    _check(lib().gs_server_add_graph(server, _dev(row_ptr, torch.int64, "row_ptr"),
+                                     _dev(col, torch.int32, "col") if col.numel() else None,
+                                     row_ptr.numel() - 1, col.numel(), ctypes.byref(gid)))
+    return gid.value
+
+
+def gs_server_start(server: int, validate: bool = True, hub_budget_bytes: int = 0,
+                    stream=None) -> None:
+    _check(lib().gs_server_start(server, GS_VALIDATE if validate else 0, hub_budget_bytes,
+                                 _stream_ptr(stream)))
+
+
+def gs_server_submit(server: int, graph: int, fraction: float, seed: int,
+                     mask: int = GS_CONNECTED, z: float = 1.96) -> int:
+    req = GsRequest(graph, mask, float(fraction), seed & (2**64 - 1), z)
+    t = ctypes.c_uint64()
+    _check(lib().gs_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def gs_server_wait(server: int, ticket: int, timeout_s: float = 600.0):
+    res = GsResult()
+    st = GsRequestStats()
+    _check(lib().gs_server_wait(server, ticket, timeout_s, ctypes.byref(res), ctypes.byref(st)))
+    return res, st.as_dict()
+
+
+def gs_server_info(server: int) -> dict:
+    out = GsServerStats()
+    _check(lib().gs_server_info(server, ctypes.byref(out)))
+    return out.as_dict()
+
+
+def gs_server_destroy(server: int) -> None:
+    _check(lib().gs_server_destroy(server))
+
+
+class Server:
+    """Continuous-batching estimation server over resident graphs."""
+
+    def __init__(self, hbm_budget_bytes: int = 40 << 30, max_batch: int = 64, lanes: int = 2):
+        self.handle = gs_server_create(hbm_budget_bytes, max_batch, lanes)
+        self._keep = []
+
+    def add_graph(self, row_ptr, col) -> int:
+        self._keep.append((row_ptr, col))
+        return gs_server_add_graph(self.handle, row_ptr, col)
+
+    def add_numpy(self, row_ptr, col, device="cuda") -> int:
+        import torch
+        return self.add_graph(torch.as_tensor(row_ptr, dtype=torch.int64).to(device),
+                              torch.as_tensor(col, dtype=torch.int32).to(device))
+
+    def start(self, validate: bool = True, hub_budget_bytes: int = 0):
+        gs_server_start(self.handle, validate, hub_budget_bytes)
+        self._keep = []  # the union copy is made; inputs may be released
+
+    def submit(self, graph: int, fraction: float, seed: int, mask: int = GS_CONNECTED,
+               z: float = 1.96) -> int:
+        return gs_server_submit(self.handle, graph, fraction, seed, mask, z)
+
+    def wait(self, ticket: int, timeout_s: float = 600.0):
+        return gs_server_wait(self.handle, ticket, timeout_s)
+
+    def info(self) -> dict:
+        return gs_server_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gs_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

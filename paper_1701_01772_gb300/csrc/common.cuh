@@ -157,7 +157,19 @@ struct gs_graph {
   uint32_t* hm_bits;
 };
 
+namespace gs {
+// Launch-time choices of the counting kernels (the autotuner's knobs).
+struct Tuning {
+  int tri_blocks_per_sm;    // resident CTAs per SM of the triangle pass
+  int quad_blocks_per_sm;   // resident CTAs per SM of the 4-node pass
+  int64_t task_probes;      // membership tests per 4-node work unit
+  int use_hubs;             // 0: ignore bitmaps / co-degree table / hub matrix
+};
+}  // namespace gs
+
 struct gs_workspace {
+  int has_tuning;
+  gs::Tuning tuning;
   void* buf[4];
   size_t cap[4];
   cudaStream_t last_stream;
@@ -176,6 +188,65 @@ gs_status ws_reserve(gs_workspace* ws, int slot, size_t bytes, cudaStream_t stre
 gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
                       int32_t* d_pairs, int64_t max_k, int64_t* k_out, int32_t** pairs_out,
                       cudaStream_t stream);
+// Samples canonical edges [e0, e0 + m) (hash index relative to e0).
+gs_status sample_range(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
+                       int64_t e0, int64_t m, int32_t* d_pairs, int64_t max_k, int64_t* k_out,
+                       int32_t** pairs_out, cudaStream_t stream);
+}  // namespace gs
+
+namespace gs {
+// Device buffers of one counting run.
+struct CountBufs {
+  int64_t K = 0, P = 0, groups = 0, tsum = 0, dup_cap = 0, nseg = 0;
+  int fold_blocks = 0;
+  DevError* err = nullptr;
+  unsigned long long* sums = nullptr;   // [32] single-segment result
+  unsigned long long* stats = nullptr;  // [8]
+  int32_t* pairs_all = nullptr;
+  int2* uv = nullptr;
+  int64_t* off = nullptr;
+  int64_t* toff = nullptr;
+  unsigned long long *t = nullptr, *k2 = nullptr, *q = nullptr;
+  int64_t* tdeg = nullptr;
+  int64_t* tmp0 = nullptr;
+  unsigned long long* dup = nullptr;
+  unsigned __int128* part = nullptr;
+  unsigned long long* limbs = nullptr;     // [nseg][16][4]
+  unsigned long long* seg_sums = nullptr;  // [nseg][16][2]
+  uint32_t* tbits = nullptr;
+  int64_t* chunk_cost = nullptr;
+  int64_t* task_off = nullptr;
+  int64_t* tmp1 = nullptr;
+  int32_t* T = nullptr;
+};
+
+Tuning default_tuning();
+int quad_blocks_limit();
+DevGraph graph_view(const gs_graph* gr, const Tuning& tu);
+size_t count_front_bytes(int64_t K, bool all_edges, bool check_dup, int64_t nseg);
+void carve_front(void* base, int64_t K, bool all_edges, bool check_dup, int64_t nseg,
+                 CountBufs& b);
+size_t count_mid_bytes(int64_t P);
+void carve_mid(void* base, int64_t P, CountBufs& b);
+int64_t launch_front(const gs_graph* gr, const DevGraph& g, const int32_t* pairs, bool four,
+                     CountBufs& b, cudaStream_t stream);
+int64_t launch_tri(const DevGraph& g, bool four, const Tuning& tu, CountBufs& b,
+                   cudaStream_t stream);
+int64_t launch_scan_t(CountBufs& b, cudaStream_t stream);
+int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
+                    cudaStream_t stream);
+int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
+                    cudaStream_t stream);
+int64_t launch_fold(const gs_graph* gr, const DevGraph& g, bool four, bool need_k, bool need_q,
+                    int64_t* per_edge, CountBufs& b, cudaStream_t stream);
+int64_t launch_fold_seg(const DevGraph& g, bool four, const int64_t* seg_off, CountBufs& b,
+                        cudaStream_t stream);
+gs_status fetch_error(DevError* d_err, cudaStream_t stream, const char* what);
+void store_sums(const unsigned long long* h, uint32_t mask, gs_sums* out);
+gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs, int64_t K,
+                    uint32_t mask, bool check_dup, int64_t* d_per_edge, const int64_t* seg_off,
+                    int64_t nseg, const Tuning& tu, CountBufs& b, cudaStream_t stream,
+                    const char* what);
 }  // namespace gs
 
 // Byte-offset bump allocator inside one workspace slot.

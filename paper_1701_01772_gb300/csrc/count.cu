@@ -29,7 +29,7 @@
 //            count of each item (iterate the shorter list, test in the
 //            longer); constant terms (the -1s, table co-degrees) added
 //            directly.
-//   quad     chunks are cut into tasks of kTaskProbes tests; tasks are split
+//   quad     chunks are cut into tasks of task_probes tests; tasks are split
 //            evenly over all warps; inside a task lanes take consecutive
 //            tests and find their item by a search over the warp's scanned
 //            costs (load-balanced search).
@@ -47,7 +47,6 @@ constexpr int kBlocksPerSm = 4;
 #define GS_QUAD_BLOCKS_PER_SM 8
 #endif
 constexpr int kQuadBlocksPerSm = GS_QUAD_BLOCKS_PER_SM;
-constexpr int64_t kTaskProbes = 1024;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr unsigned long long kEmpty = ~0ull;
 
@@ -387,8 +386,9 @@ __global__ void __launch_bounds__(kThreads)
     k_chunk_cost(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
                  const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
                  const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T, int need_k,
-                 int need_q, int64_t* __restrict__ chunk_cost, int64_t* __restrict__ task_cnt,
-                 unsigned long long* __restrict__ q, unsigned long long* __restrict__ stats) {
+                 int need_q, int64_t task_probes, int64_t* __restrict__ chunk_cost,
+                 int64_t* __restrict__ task_cnt, unsigned long long* __restrict__ q,
+                 unsigned long long* __restrict__ stats) {
   unsigned long long tests = 0;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(kThreads)
     int64_t qc = warp_sum<int64_t>(it.qconst);
     if (lane == 0) {
       chunk_cost[gi] = cost;
-      task_cnt[gi] = (cost + kTaskProbes - 1) / kTaskProbes;
+      task_cnt[gi] = (cost + task_probes - 1) / task_probes;
       if (qc != 0) atomicAdd(q + e, (unsigned long long)qc);
       tests += cost;
     }
@@ -438,7 +438,8 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
            const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
            const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
            const int64_t* __restrict__ task_off, int64_t groups, int need_k, int need_q,
-           unsigned long long* __restrict__ k_out, unsigned long long* __restrict__ q) {
+           int64_t task_probes, unsigned long long* __restrict__ k_out,
+           unsigned long long* __restrict__ q) {
   __shared__ SharedItem items[kThreads / 32][32];
   const int lane = threadIdx.x & 31;
   SharedItem* my = items[threadIdx.x >> 5];
@@ -504,8 +505,8 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
       cur = gi;
       cur_e = e;
     }
-    const int64_t lo = (task - __ldg(task_off + gi)) * kTaskProbes;
-    const int32_t len = (int32_t)min(ctotal - lo, kTaskProbes);
+    const int64_t lo = (task - __ldg(task_off + gi)) * task_probes;
+    const int32_t len = (int32_t)min(ctotal - lo, task_probes);
     for (int32_t r = lane; r - lane < len; r += 32) {
       const int64_t rr = lo + r;
       // item j = last lane whose start <= rr
@@ -646,12 +647,266 @@ __global__ void k_fold_final(const u128* __restrict__ part, int blocks,
   }
 }
 
+
+// Per-segment exact sums. Edges [seg_off[s], seg_off[s+1]) form segment s
+// (one graph of a batch, one request of a serving step). Each of the 16
+// values (8 sums in two's complement, 8 sums of squares) is accumulated as
+// four 32-bit limbs in 64-bit counters: a limb sum stays below 2^64 for
+// fewer than 2^32 additions, so the 128-bit total is recovered exactly.
+// Lanes of a warp are reduced per segment first (segmented shuffle scan).
+__global__ void __launch_bounds__(kThreads)
+    k_fold_seg(DevGraph g, const int2* __restrict__ uv, int64_t K,
+               const unsigned long long* __restrict__ t, const unsigned long long* __restrict__ k2,
+               const unsigned long long* __restrict__ q, const int64_t* __restrict__ seg_off,
+               int64_t nseg, unsigned long long* __restrict__ limbs) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < K;
+       base += stride) {
+    const int64_t e = base + lane;
+    int64_t seg = -1;
+    u128 val[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) val[i] = 0;
+    if (e < K) {
+      seg = last_le(seg_off, nseg, e);
+      int2 pr = uv[e];
+      int64_t bu, bv;
+      const i128 du = deg_of(g.row_ptr, pr.x, &bu), dv = deg_of(g.row_ptr, pr.y, &bv);
+      const i128 tt = (i128)t[e];
+      const i128 kk = k2 != nullptr ? (i128)k2[e] : 0;
+      const i128 qq = q != nullptr ? (i128)(long long)q[e] : 0;
+      const i128 a = du - 1 - tt, b = dv - 1 - tt;
+      const i128 n8 = tt * (tt - 1) / 2 - kk;
+      i128 N[8];
+      N[0] = tt;
+      N[1] = a + b;
+      N[2] = kk;
+      N[3] = n8;
+      N[4] = tt * (a + b) - 4 * n8;
+      N[5] = qq;
+      N[6] = 2 * (a * (a - 1) / 2 + b * (b - 1) / 2) - tt * (a + b) + 4 * n8;
+      N[7] = a * b - qq;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        val[i] = (u128)N[i];
+        u128 m = (u128)(N[i] < 0 ? -N[i] : N[i]);
+        val[8 + i] = m * m;
+      }
+    }
+    // segmented inclusive scan over the warp (segments are contiguous)
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t sd = __shfl_up_sync(kFull, seg, d);
+      const bool take = lane >= d && sd == seg;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        unsigned long long lo = __shfl_up_sync(kFull, (unsigned long long)val[i], d);
+        unsigned long long hi = __shfl_up_sync(kFull, (unsigned long long)(val[i] >> 64), d);
+        if (take) val[i] += ((u128)hi << 64) | lo;
+      }
+    }
+    const int64_t next = __shfl_down_sync(kFull, seg, 1);
+    const bool tail = seg >= 0 && (lane == 31 || next != seg);
+    if (tail) {
+      unsigned long long* dst = limbs + seg * 64;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const unsigned long long limb = (unsigned long long)((val[i] >> (32 * l)) & 0xffffffffu);
+          if (limb) atomicAdd(dst + i * 4 + l, limb);
+        }
+      }
+    }
+  }
+}
+
+// Recombines the limbs: sums[s][i] = sum_l limb_l << 32 l (mod 2^128), as
+// (low, high) 64-bit words.
+__global__ void k_fold_seg_final(const unsigned long long* __restrict__ limbs, int64_t nseg,
+                                 unsigned long long* __restrict__ sums) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nseg * 16;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    u128 s = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) s += (u128)limbs[x * 4 + l] << (32 * l);
+    sums[2 * x] = (unsigned long long)s;
+    sums[2 * x + 1] = (unsigned long long)(s >> 64);
+  }
+}
+
 }  // namespace gs
 
-// =================================================================== C ABI
-using namespace gs;
+// =================================================================== host side
+namespace gs {
 
-static gs_status fetch_error(DevError* d_err, cudaStream_t stream, const char* what) {
+Tuning default_tuning() { return Tuning{4, kQuadBlocksPerSm, 1024, 1}; }
+
+int quad_blocks_limit() { return kQuadBlocksPerSm; }
+
+DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
+  DevGraph g = gr->dev;
+  if (!tu.use_hubs) {
+    g.bm_slot = nullptr;
+    g.bm_bits = nullptr;
+    g.bm_count = 0;
+    g.tb_slot = nullptr;
+    g.tb_codeg = nullptr;
+    g.tb_count = 0;
+    g.hm_bits = nullptr;
+  }
+  return g;
+}
+
+size_t count_front_bytes(int64_t K, bool all_edges, bool check_dup, int64_t nseg) {
+  int64_t dup_cap = 1;
+  while (dup_cap < 2 * K) dup_cap <<= 1;
+  const int fold_blocks = grid_for(K, kThreads, 2);
+  return Carve::bytes_for<DevError>(1) + Carve::bytes_for<unsigned long long>(32) +
+         Carve::bytes_for<unsigned long long>(8) +
+         (all_edges ? Carve::bytes_for<int32_t>(2 * K) : 0) + Carve::bytes_for<int2>(K) +
+         Carve::bytes_for<int64_t>(K + 1) * 2 + Carve::bytes_for<unsigned long long>(K) * 3 +
+         Carve::bytes_for<int64_t>(K) + Carve::bytes_for<int64_t>(scan_tmp_elems(K + 1)) +
+         (check_dup ? Carve::bytes_for<unsigned long long>(dup_cap) : 0) +
+         Carve::bytes_for<u128>((int64_t)fold_blocks * 16) +
+         (nseg > 0 ? Carve::bytes_for<unsigned long long>(nseg * 64) +
+                         Carve::bytes_for<unsigned long long>(nseg * 32)
+                   : 0);
+}
+
+void carve_front(void* base, int64_t K, bool all_edges, bool check_dup, int64_t nseg,
+                 CountBufs& b) {
+  Carve c{(char*)base, 0};
+  int64_t dup_cap = 1;
+  while (dup_cap < 2 * K) dup_cap <<= 1;
+  b.K = K;
+  b.dup_cap = dup_cap;
+  b.fold_blocks = grid_for(K, kThreads, 2);
+  b.err = c.take<DevError>(1);
+  b.sums = c.take<unsigned long long>(32);
+  b.stats = c.take<unsigned long long>(8);
+  b.pairs_all = all_edges ? c.take<int32_t>(2 * K) : nullptr;
+  b.uv = c.take<int2>(K);
+  b.off = c.take<int64_t>(K + 1);
+  b.toff = c.take<int64_t>(K + 1);
+  b.t = c.take<unsigned long long>(K);
+  b.k2 = c.take<unsigned long long>(K);
+  b.q = c.take<unsigned long long>(K);
+  b.tdeg = c.take<int64_t>(K);
+  b.tmp0 = c.take<int64_t>(scan_tmp_elems(K + 1));
+  b.dup = check_dup ? c.take<unsigned long long>(dup_cap) : nullptr;
+  b.part = c.take<u128>((int64_t)b.fold_blocks * 16);
+  b.nseg = nseg;
+  b.limbs = nseg > 0 ? c.take<unsigned long long>(nseg * 64) : nullptr;
+  b.seg_sums = nseg > 0 ? c.take<unsigned long long>(nseg * 32) : nullptr;
+}
+
+size_t count_mid_bytes(int64_t P) {
+  const int64_t groups = (P + 31) / 32;
+  return Carve::bytes_for<uint32_t>(groups) + Carve::bytes_for<int64_t>(groups) +
+         Carve::bytes_for<int64_t>(groups + 1) +
+         Carve::bytes_for<int64_t>(scan_tmp_elems(groups + 1));
+}
+
+void carve_mid(void* base, int64_t P, CountBufs& b) {
+  Carve c{(char*)base, 0};
+  b.P = P;
+  b.groups = (P + 31) / 32;
+  b.tbits = c.take<uint32_t>(b.groups);
+  b.chunk_cost = c.take<int64_t>(b.groups);
+  b.task_off = c.take<int64_t>(b.groups + 1);
+  b.tmp1 = c.take<int64_t>(scan_tmp_elems(b.groups + 1));
+}
+
+// memsets + (all-pair enumeration) + prep + position scan. No host sync.
+int64_t launch_front(const gs_graph* gr, const DevGraph& g, const int32_t* pairs, bool four,
+                     CountBufs& b, cudaStream_t stream) {
+  int64_t launches = 0;
+  const int64_t K = b.K;
+  cudaMemsetAsync(b.err, 0, sizeof(DevError), stream);
+  cudaMemsetAsync(b.stats, 0, sizeof(unsigned long long) * 8, stream);
+  cudaMemsetAsync(b.t, 0, sizeof(unsigned long long) * K, stream);
+  if (four) {
+    cudaMemsetAsync(b.k2, 0, sizeof(unsigned long long) * K, stream);
+    cudaMemsetAsync(b.q, 0, sizeof(unsigned long long) * K, stream);
+  }
+  if (b.dup != nullptr) cudaMemsetAsync(b.dup, 0xff, sizeof(unsigned long long) * b.dup_cap, stream);
+  if (pairs == nullptr) {
+    k_all_pairs<<<grid_for(g.n * 32, kThreads, 8), kThreads, 0, stream>>>(
+        g.row_ptr, g.col, gr->up_ptr, gr->edge_off, g.n, b.pairs_all);
+    pairs = b.pairs_all;
+    ++launches;
+  }
+  k_prep<<<grid_for(K, kThreads, 8), kThreads, 0, stream>>>(g, pairs, K, four ? 1 : 0, b.dup,
+                                                            b.dup_cap - 1, b.uv, b.off, b.err);
+  exclusive_scan_i64(b.off, b.off, K, b.tmp0, stream);
+  return launches + 4;
+}
+
+int64_t launch_tri(const DevGraph& g, bool four, const Tuning& tu, CountBufs& b,
+                   cudaStream_t stream) {
+  const int grid = sm_count() * tu.tri_blocks_per_sm;
+  if (four)
+    k_tri<true><<<grid, kThreads, 0, stream>>>(g, b.uv, b.off, b.K, b.t, b.tbits);
+  else
+    k_tri<false><<<grid, kThreads, 0, stream>>>(g, b.uv, b.off, b.K, b.t, nullptr);
+  return 1;
+}
+
+int64_t launch_scan_t(CountBufs& b, cudaStream_t stream) {
+  exclusive_scan_i64((const int64_t*)b.t, b.toff, b.K, b.tmp0, stream);
+  return 3;
+}
+
+// compact T, chunk costs, task scan. T must hold b.toff[K] entries. No host
+// sync.
+int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
+                    cudaStream_t stream) {
+  k_compact_T<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(g, b.uv, b.off, b.toff,
+                                                                          b.K, b.tbits, b.T,
+                                                                          b.tdeg);
+  k_chunk_cost<<<sm_count() * kBlocksPerSm, kThreads, 0, stream>>>(
+      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T, need_k, need_q, tu.task_probes,
+      b.chunk_cost, b.task_off, b.q, b.stats);
+  exclusive_scan_i64(b.task_off, b.task_off, b.groups, b.tmp1, stream);
+  return 5;
+}
+
+// The 4-node membership tests (k_quad). No host sync.
+int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
+                    cudaStream_t stream) {
+  const int sms = sm_count();
+  const int qb = tu.quad_blocks_per_sm < 1 ? 1
+                 : tu.quad_blocks_per_sm > kQuadBlocksPerSm ? kQuadBlocksPerSm
+                                                            : tu.quad_blocks_per_sm;
+  k_quad<<<sms * qb, kThreads, 0, stream>>>(g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T,
+                                            b.task_off, b.groups, need_k, need_q,
+                                            tu.task_probes, b.k2, b.q);
+  return 1;
+}
+
+int64_t launch_fold(const gs_graph* gr, const DevGraph& g, bool four, bool need_k, bool need_q,
+                    int64_t* per_edge, CountBufs& b, cudaStream_t stream) {
+  k_fold<<<b.fold_blocks, kThreads, 0, stream>>>(g, b.uv, b.K, b.t, four ? b.k2 : nullptr,
+                                                  four ? b.q : nullptr, four ? b.tdeg : nullptr,
+                                                  gr->nbr_degsum, need_k, need_q, per_edge, b.part,
+                                                  b.stats);
+  k_fold_final<<<1, 32, 0, stream>>>(b.part, b.fold_blocks, b.sums);
+  return 2;
+}
+
+int64_t launch_fold_seg(const DevGraph& g, bool four, const int64_t* seg_off, CountBufs& b,
+                        cudaStream_t stream) {
+  cudaMemsetAsync(b.limbs, 0, sizeof(unsigned long long) * b.nseg * 64, stream);
+  k_fold_seg<<<grid_for(b.K, kThreads, 4), kThreads, 0, stream>>>(
+      g, b.uv, b.K, b.t, four ? b.k2 : nullptr, four ? b.q : nullptr, seg_off, b.nseg, b.limbs);
+  k_fold_seg_final<<<grid_for(b.nseg * 16, 256, 4), 256, 0, stream>>>(b.limbs, b.nseg,
+                                                                       b.seg_sums);
+  return 2;
+}
+
+gs_status fetch_error(DevError* d_err, cudaStream_t stream, const char* what) {
   DevError h;
   GS_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(h), cudaMemcpyDeviceToHost, stream));
   GS_CUDA(cudaStreamSynchronize(stream));
@@ -665,21 +920,110 @@ static gs_status fetch_error(DevError* d_err, cudaStream_t stream, const char* w
   return GS_OK;
 }
 
-static const uint32_t kKnownMask = GS_CONNECTED;
+void store_sums(const unsigned long long* h, uint32_t mask, gs_sums* out) {
+  static const uint32_t bit[8] = {GS_G3, GS_G4, GS_G7, GS_G8, GS_G9, GS_G10, GS_G11, GS_G12};
+  for (int i = 0; i < 8; ++i) {
+    if (!(mask & bit[i])) continue;
+    out->sum[i][0] = h[2 * i];
+    out->sum[i][1] = h[2 * i + 1];
+    out->sumsq[i][0] = h[2 * (8 + i)];
+    out->sumsq[i][1] = h[2 * (8 + i) + 1];
+  }
+}
 
-namespace {
-// Start/stop events of the six phases when timing is on.
-struct PhaseTimer {
-  gs_workspace* ws;
-  cudaStream_t stream;
-  void start(int phase) {
-    if (ws->timing) cudaEventRecord(ws->ev[2 * phase], stream);
+// Full counting run with host synchronisation for sizing (gs_count and the
+// sizing pass of the batched and served paths). seg_off != NULL selects the
+// per-segment fold (results in b.seg_sums) instead of the single sum.
+gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs, int64_t K,
+                    uint32_t mask, bool check_dup, int64_t* d_per_edge, const int64_t* seg_off,
+                    int64_t nseg, const Tuning& tu, CountBufs& b, cudaStream_t stream,
+                    const char* what) {
+  const bool need_k = (mask & (GS_G7 | GS_G8 | GS_G9 | GS_G11)) != 0;
+  const bool need_q = (mask & (GS_G10 | GS_G12)) != 0;
+  const bool four = need_k || need_q;
+  const bool all_edges = d_pairs == nullptr;
+  const DevGraph g = graph_view(gr, tu);
+  int64_t launches = 0;
+  struct Timer {
+    gs_workspace* ws;
+    cudaStream_t s;
+    void start(int p) {
+      if (ws->timing) cudaEventRecord(ws->ev[2 * p], s);
+    }
+    void stop(int p) {
+      if (ws->timing) cudaEventRecord(ws->ev[2 * p + 1], s);
+    }
+  } timer{ws, stream};
+
+  void* base0 = nullptr;
+  GS_TRY(ws_reserve(ws, 0, count_front_bytes(K, all_edges, check_dup, seg_off ? nseg : 0), stream,
+                    &base0));
+  carve_front(base0, K, all_edges, check_dup, seg_off ? nseg : 0, b);
+  timer.start(0);
+  launches += launch_front(gr, g, d_pairs, four, b, stream);
+  timer.stop(0);
+  GS_CUDA(cudaGetLastError());
+  int64_t P = 0;
+  GS_CUDA(cudaMemcpyAsync(&P, b.off + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+  gs_status es = fetch_error(b.err, stream, what);
+  ws->launches_total += launches;
+  if (es != GS_OK) return es;
+
+  void* base1 = nullptr;
+  GS_TRY(ws_reserve(ws, 1, four ? count_mid_bytes(P) : 256, stream, &base1));
+  if (four) {
+    carve_mid(base1, P, b);
+  } else {
+    b.P = P;
+    b.groups = (P + 31) / 32;
+    b.tbits = nullptr;
   }
-  void stop(int phase) {
-    if (ws->timing) cudaEventRecord(ws->ev[2 * phase + 1], stream);
+  int64_t more = 0;
+  timer.start(1);
+  more += launch_tri(g, four, tu, b, stream);
+  timer.stop(1);
+  GS_CUDA(cudaGetLastError());
+  b.tsum = 0;
+  if (four) {
+    timer.start(2);
+    more += launch_scan_t(b, stream);
+    GS_CUDA(cudaMemcpyAsync(&b.tsum, b.toff + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    GS_CUDA(cudaStreamSynchronize(stream));
+    void* base2 = nullptr;
+    GS_TRY(ws_reserve(ws, 2, Carve::bytes_for<int32_t>(b.tsum), stream, &base2));
+    b.T = (int32_t*)base2;
+    timer.stop(2);
+    timer.start(3);
+    more += launch_cost(g, need_k, need_q, tu, b, stream);
+    timer.stop(3);
+    timer.start(4);
+    more += launch_quad(g, need_k, need_q, tu, b, stream);
+    timer.stop(4);
+    GS_CUDA(cudaGetLastError());
+  } else {
+    for (int ph = 2; ph <= 4; ++ph) {
+      timer.start(ph);
+      timer.stop(ph);
+    }
   }
-};
-}  // namespace
+  timer.start(5);
+  if (seg_off != nullptr)
+    more += launch_fold_seg(g, four, seg_off, b, stream);
+  else
+    more += launch_fold(gr, g, four, need_k, need_q, d_per_edge, b, stream);
+  timer.stop(5);
+  GS_CUDA(cudaGetLastError());
+  ws->launches_total += more;
+  ws->stats.launches = launches + more;
+  return GS_OK;
+}
+
+}  // namespace gs
+
+// =================================================================== C ABI
+using namespace gs;
+
+static const uint32_t kKnownMask = GS_CONNECTED;
 
 extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs,
                               int64_t K, uint32_t mask, int64_t* d_per_edge, gs_sums* h_sums,
@@ -701,155 +1045,21 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
     set_error("gs_count: with d_pairs = NULL, k must equal the edge count %lld", (long long)gr->m);
     return GS_EINVAL;
   }
-  const DevGraph& g = gr->dev;
-  const bool need_k = (mask & (GS_G7 | GS_G8 | GS_G9 | GS_G11)) != 0;
-  const bool need_q = (mask & (GS_G10 | GS_G12)) != 0;
-  const bool four = need_k || need_q;
-  const int sms = sm_count();
-  const int fold_blocks = grid_for(K, kThreads, 2);
-  const bool check_dup = d_pairs != nullptr;
-  int64_t dup_cap = 1;
-  while (dup_cap < 2 * K) dup_cap <<= 1;
-  int64_t launches = 0;
-  PhaseTimer timer{ws, stream};
-
-  // ---- slot 0: per-edge arrays
-  size_t b0 = Carve::bytes_for<DevError>(1) + Carve::bytes_for<unsigned long long>(32) +
-              Carve::bytes_for<unsigned long long>(8) +
-              (d_pairs == nullptr ? Carve::bytes_for<int32_t>(2 * K) : 0) +
-              Carve::bytes_for<int2>(K) + Carve::bytes_for<int64_t>(K + 1) * 2 +
-              Carve::bytes_for<unsigned long long>(K) * 3 + Carve::bytes_for<int64_t>(K) +
-              Carve::bytes_for<int64_t>(scan_tmp_elems(K + 1)) +
-              (check_dup ? Carve::bytes_for<unsigned long long>(dup_cap) : 0) +
-              Carve::bytes_for<u128>((int64_t)fold_blocks * 16);
-  void* base0 = nullptr;
-  GS_TRY(ws_reserve(ws, 0, b0, stream, &base0));
-  Carve c0{(char*)base0, 0};
-  DevError* d_err = c0.take<DevError>(1);
-  unsigned long long* d_sums = c0.take<unsigned long long>(32);
-  unsigned long long* d_stats = c0.take<unsigned long long>(8);
-  int32_t* pairs_all = d_pairs == nullptr ? c0.take<int32_t>(2 * K) : nullptr;
-  int2* uv = c0.take<int2>(K);
-  int64_t* off = c0.take<int64_t>(K + 1);
-  int64_t* toff = c0.take<int64_t>(K + 1);
-  unsigned long long* t = c0.take<unsigned long long>(K);
-  unsigned long long* k2 = c0.take<unsigned long long>(K);
-  unsigned long long* q = c0.take<unsigned long long>(K);
-  int64_t* tdeg = c0.take<int64_t>(K);
-  int64_t* tmp0 = c0.take<int64_t>(scan_tmp_elems(K + 1));
-  unsigned long long* dup = check_dup ? c0.take<unsigned long long>(dup_cap) : nullptr;
-  u128* part = c0.take<u128>((int64_t)fold_blocks * 16);
-
-  timer.start(0);
-  GS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(DevError), stream));
-  GS_CUDA(cudaMemsetAsync(d_stats, 0, sizeof(unsigned long long) * 8, stream));
-  GS_CUDA(cudaMemsetAsync(t, 0, sizeof(unsigned long long) * K, stream));
-  if (four) {
-    GS_CUDA(cudaMemsetAsync(k2, 0, sizeof(unsigned long long) * K, stream));
-    GS_CUDA(cudaMemsetAsync(q, 0, sizeof(unsigned long long) * K, stream));
-  }
-  if (check_dup) GS_CUDA(cudaMemsetAsync(dup, 0xff, sizeof(unsigned long long) * dup_cap, stream));
-  const int32_t* pairs = d_pairs;
-  if (pairs == nullptr) {
-    k_all_pairs<<<grid_for(g.n * 32, kThreads, 8), kThreads, 0, stream>>>(
-        g.row_ptr, g.col, gr->up_ptr, gr->edge_off, g.n, pairs_all);
-    pairs = pairs_all;
-    ++launches;
-  }
-  k_prep<<<grid_for(K, kThreads, 8), kThreads, 0, stream>>>(g, pairs, K, four ? 1 : 0, dup,
-                                                            dup_cap - 1, uv, off, d_err);
-  GS_TRY(exclusive_scan_i64(off, off, K, tmp0, stream));
-  launches += 4;
-  timer.stop(0);
-  int64_t P = 0;
-  GS_CUDA(cudaMemcpyAsync(&P, off + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
-  gs_status es = fetch_error(d_err, stream, "gs_count");
-  ws->launches_total += launches;
-  if (es != GS_OK) return es;
-
-  // ---- slot 1: per-position arrays
-  const int64_t groups = (P + 31) / 32;
-  size_t b1 = four ? Carve::bytes_for<uint32_t>(groups) + Carve::bytes_for<int64_t>(groups) +
-                         Carve::bytes_for<int64_t>(groups + 1) +
-                         Carve::bytes_for<int64_t>(scan_tmp_elems(groups + 1))
-                   : 256;
-  void* base1 = nullptr;
-  GS_TRY(ws_reserve(ws, 1, b1, stream, &base1));
-  Carve c1{(char*)base1, 0};
-  uint32_t* tbits = four ? c1.take<uint32_t>(groups) : nullptr;
-  int64_t* chunk_cost = four ? c1.take<int64_t>(groups) : nullptr;
-  int64_t* task_off = four ? c1.take<int64_t>(groups + 1) : nullptr;
-  int64_t* tmp1 = four ? c1.take<int64_t>(scan_tmp_elems(groups + 1)) : nullptr;
-
-  const int persist = sms * kBlocksPerSm;
-  int64_t before = launches;
-  timer.start(1);
-  if (four)
-    k_tri<true><<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, tbits);
-  else
-    k_tri<false><<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, nullptr);
-  ++launches;
-  timer.stop(1);
-  GS_CUDA(cudaGetLastError());
-
-  int64_t tsum = 0;
-  if (four) {
-    timer.start(2);
-    GS_TRY(exclusive_scan_i64((const int64_t*)t, toff, K, tmp0, stream));
-    launches += 3;
-    GS_CUDA(cudaMemcpyAsync(&tsum, toff + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
-    GS_CUDA(cudaStreamSynchronize(stream));
-    void* base2 = nullptr;
-    GS_TRY(ws_reserve(ws, 2, Carve::bytes_for<int32_t>(tsum), stream, &base2));
-    int32_t* T = (int32_t*)base2;
-    k_compact_T<<<grid_for(K * 32, kThreads, 8), kThreads, 0, stream>>>(g, uv, off, toff, K, tbits,
-                                                                        T, tdeg);
-    ++launches;
-    timer.stop(2);
-    timer.start(3);
-    k_chunk_cost<<<persist, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, need_k,
-                                                   need_q, chunk_cost, task_off, q, d_stats);
-    GS_TRY(exclusive_scan_i64(task_off, task_off, groups, tmp1, stream));
-    launches += 4;
-    timer.stop(3);
-    timer.start(4);
-    k_quad<<<sms * kQuadBlocksPerSm, kThreads, 0, stream>>>(g, uv, off, K, t, toff, tbits, T, task_off, groups,
-                                             need_k, need_q, k2, q);
-    ++launches;
-    timer.stop(4);
-    GS_CUDA(cudaGetLastError());
-  } else {
-    for (int ph = 2; ph <= 4; ++ph) {
-      timer.start(ph);
-      timer.stop(ph);
-    }
-  }
-  timer.start(5);
-  k_fold<<<fold_blocks, kThreads, 0, stream>>>(g, uv, K, t, four ? k2 : nullptr, four ? q : nullptr,
-                                                four ? tdeg : nullptr, gr->nbr_degsum, need_k,
-                                                need_q, d_per_edge, part, d_stats);
-  k_fold_final<<<1, 32, 0, stream>>>(part, fold_blocks, d_sums);
-  launches += 2;
-  timer.stop(5);
-  ws->launches_total += launches - before;
-  GS_CUDA(cudaGetLastError());
+  CountBufs b;
+  const Tuning tu = ws->has_tuning ? ws->tuning : default_tuning();
+  GS_TRY(count_run(gr, ws, d_pairs, K, mask, d_pairs != nullptr, d_per_edge, nullptr, 0, tu, b,
+                   stream, "gs_count"));
+  const bool four = (mask & (GS_G7 | GS_G8 | GS_G9 | GS_G10 | GS_G11 | GS_G12)) != 0;
   unsigned long long h[32];
   unsigned long long hs[8];
   int64_t ntasks = 0;
-  GS_CUDA(cudaMemcpyAsync(h, d_sums, sizeof(h), cudaMemcpyDeviceToHost, stream));
-  GS_CUDA(cudaMemcpyAsync(hs, d_stats, sizeof(hs), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaMemcpyAsync(h, b.sums, sizeof(h), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaMemcpyAsync(hs, b.stats, sizeof(hs), cudaMemcpyDeviceToHost, stream));
   if (four)
-    GS_CUDA(cudaMemcpyAsync(&ntasks, task_off + groups, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                            stream));
+    GS_CUDA(cudaMemcpyAsync(&ntasks, b.task_off + b.groups, sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, stream));
   GS_CUDA(cudaStreamSynchronize(stream));
-  static const uint32_t bit[8] = {GS_G3, GS_G4, GS_G7, GS_G8, GS_G9, GS_G10, GS_G11, GS_G12};
-  for (int i = 0; i < 8; ++i) {
-    if (!(mask & bit[i])) continue;
-    h_sums->sum[i][0] = h[2 * i];
-    h_sums->sum[i][1] = h[2 * i + 1];
-    h_sums->sumsq[i][0] = h[2 * (8 + i)];
-    h_sums->sumsq[i][1] = h[2 * (8 + i) + 1];
-  }
+  store_sums(h, mask, h_sums);
   gs_stats& st = ws->stats;
   st.k = K;
   st.tri_tests = (int64_t)hs[0];
@@ -857,13 +1067,27 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   st.model_bytes = hs[2] + hs[3];
   st.model_tri_bytes = hs[2];
   st.model_quad_bytes = hs[3];
-  st.t_sum = tsum;
+  st.t_sum = b.tsum;
   st.tasks = ntasks;
-  st.launches = launches;
   st.timed = ws->timing;
   if (ws->timing) {
     float* ms[6] = {&st.ms_prep, &st.ms_tri, &st.ms_compact, &st.ms_cost, &st.ms_quad, &st.ms_fold};
     for (int ph = 0; ph < 6; ++ph) cudaEventElapsedTime(ms[ph], ws->ev[2 * ph], ws->ev[2 * ph + 1]);
   }
+  return GS_OK;
+}
+
+extern "C" gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_per_sm,
+                                             int quad_blocks_per_sm, int64_t task_probes,
+                                             int use_hubs) {
+  if (ws == nullptr || tri_blocks_per_sm < 1 || tri_blocks_per_sm > 8 || quad_blocks_per_sm < 1 ||
+      quad_blocks_per_sm > kQuadBlocksPerSm || task_probes < 32 || task_probes > (1 << 20)) {
+    set_error("gs_workspace_set_tuning: out-of-range parameter (tri 1..8, quad 1..%d, task "
+              "32..2^20)",
+              kQuadBlocksPerSm);
+    return GS_EINVAL;
+  }
+  ws->tuning = Tuning{tri_blocks_per_sm, quad_blocks_per_sm, task_probes, use_hubs ? 1 : 0};
+  ws->has_tuning = 1;
   return GS_OK;
 }

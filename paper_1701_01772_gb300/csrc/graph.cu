@@ -514,6 +514,9 @@ constexpr int kSampThreads = 256;
 constexpr int kSampItems = 16;
 constexpr int64_t kSampTile = (int64_t)kSampThreads * kSampItems;
 
+// Edges [e0, e0 + m) of the canonical order are sampled; the hash input is
+// the index relative to e0 (so a graph inside a disjoint union samples
+// exactly as it does on its own).
 __global__ void k_sample_count(int64_t m, uint64_t seed, uint64_t threshold,
                                int64_t* __restrict__ tile_cnt) {
   int64_t base = (int64_t)blockIdx.x * kSampTile + (int64_t)threadIdx.x * kSampItems;
@@ -533,8 +536,8 @@ __global__ void k_sample_count(int64_t m, uint64_t seed, uint64_t threshold,
 }
 
 __global__ void k_sample_write(const int32_t* __restrict__ col, const int64_t* __restrict__ up_ptr,
-                               const int64_t* __restrict__ edge_off, int64_t n, int64_t m,
-                               uint64_t seed, uint64_t threshold,
+                               const int64_t* __restrict__ edge_off, int64_t n, int64_t e0,
+                               int64_t m, uint64_t seed, uint64_t threshold,
                                const int64_t* __restrict__ tile_off, int32_t* __restrict__ pairs) {
   __shared__ int wsum[kSampThreads / 32];
   int64_t base = (int64_t)blockIdx.x * kSampTile + (int64_t)threadIdx.x * kSampItems;
@@ -558,7 +561,7 @@ __global__ void k_sample_write(const int32_t* __restrict__ col, const int64_t* _
   while (bits) {
     int j = __ffs(bits) - 1;
     bits &= bits - 1;
-    int64_t i = base + j;
+    int64_t i = e0 + base + j;
     // row u owning canonical edge i: the last u with edge_off[u] <= i
     int64_t lo = 0, len = n;
     while (len > 1) {
@@ -582,7 +585,12 @@ namespace gs {
 gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
                       int32_t* d_pairs, int64_t max_k, int64_t* k_out, int32_t** pairs_out,
                       cudaStream_t stream) {
-  const int64_t m = g->m;
+  return sample_range(g, ws, fraction, seed, 0, g->m, d_pairs, max_k, k_out, pairs_out, stream);
+}
+
+gs_status sample_range(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
+                       int64_t e0, int64_t m, int32_t* d_pairs, int64_t max_k, int64_t* k_out,
+                       int32_t** pairs_out, cudaStream_t stream) {
   *k_out = 0;
   if (pairs_out) *pairs_out = d_pairs;
   if (m == 0) return GS_OK;
@@ -615,7 +623,7 @@ gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint
   }
   if (kept > 0) {
     k_sample_write<<<(unsigned)tiles, kSampThreads, 0, stream>>>(
-        g->dev.col, g->up_ptr, g->edge_off, g->dev.n, m, seed, threshold, off, d_pairs);
+        g->dev.col, g->up_ptr, g->edge_off, g->dev.n, e0, m, seed, threshold, off, d_pairs);
     ws->launches_total += 1;
   }
   GS_CUDA(cudaGetLastError());

@@ -1,0 +1,477 @@
+// Serving: continuous batching of estimation requests over resident graphs.
+//
+// All graphs added to a server are registered as one disjoint union (vertex
+// ids shifted per graph), so requests on different graphs can share one
+// counting pass: each request's sampled edges are drawn from its graph's
+// range of the union's canonical edge order (the hash index is relative to
+// that range, so the sample equals the one gs_sample draws on the graph
+// alone), the edge lists of a batch are concatenated, and the fold sums each
+// request's range separately. Per-edge counts do not depend on the other
+// edges of the pass, so every result is identical alone and in any mix.
+//
+// Worker lanes (host threads, each with its own CUDA stream and workspace)
+// take requests from a FIFO queue. A lane admits requests while their
+// estimated device memory fits the server's budget together with what the
+// other lanes hold; the estimate is reserved until the batch finishes.
+// Requests that arrive while a lane's batch is on the GPU are picked up by
+// the next free lane, so batches overlap on the device.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gs {
+
+// Per-graph sum of roundup32(min(d_u, d_v)) over canonical edges u < v
+// (4-node positions), for the memory estimate. One warp per vertex.
+__global__ void k_positions_per_graph(const int64_t* __restrict__ row_ptr,
+                                      const int32_t* __restrict__ col,
+                                      const int64_t* __restrict__ up_ptr, int64_t n,
+                                      const int64_t* __restrict__ vtx_off, int64_t num_graphs,
+                                      unsigned long long* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const int64_t du = row_ptr[u + 1] - row_ptr[u];
+    unsigned long long s = 0;
+    for (int64_t p = up_ptr[u] + lane; p < row_ptr[u + 1]; p += 32) {
+      const int32_t v = col[p];
+      const int64_t dv = row_ptr[v + 1] - row_ptr[v];
+      const int64_t dm = du < dv ? du : dv;
+      s += (unsigned long long)((dm + 31) & ~(int64_t)31);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0 && s) {
+      int64_t lo = 0, len = num_graphs;
+      while (len > 1) {
+        int64_t half = len >> 1;
+        lo = (vtx_off[lo + half] <= u) ? lo + half : lo;
+        len -= half;
+      }
+      atomicAdd(out + lo, s);
+    }
+  }
+}
+
+// Copies graph g's CSR into the union with row offsets shifted by nnz_base
+// and vertex ids by vtx_base.
+__global__ void k_union_copy(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                             int64_t n, int64_t nnz, int64_t vtx_base, int64_t nnz_base,
+                             int64_t* __restrict__ u_row_ptr, int32_t* __restrict__ u_col) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    u_row_ptr[vtx_base + i] = row_ptr[i] + nnz_base;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride)
+    u_col[nnz_base + p] = col[p] + (int32_t)vtx_base;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Source {
+  const int64_t* row_ptr;
+  const int32_t* col;
+  int64_t n, nnz;
+};
+
+struct Req {
+  gs_request r;
+  uint64_t ticket;
+  double t_submit, t_start, t_done;
+  int64_t est_bytes;
+  int64_t k;
+  int64_t batch_size;
+  gs_status status;
+  int done;
+  gs_result res;
+};
+
+}  // namespace
+
+struct gs_server {
+  int device = 0;
+  uint64_t budget;
+  int max_batch;
+  int lanes;
+  std::vector<Source> src;
+  // union
+  int64_t* u_row_ptr = nullptr;
+  int32_t* u_col = nullptr;
+  int64_t* d_vtx_off = nullptr;
+  gs_graph* ug = nullptr;
+  std::vector<int64_t> vtx_off, edge_base, m;
+  std::vector<double> bytes_per_edge;
+  // queue
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Req*> pending;
+  std::unordered_map<uint64_t, Req*> reqs;
+  uint64_t next_ticket = 1;
+  bool started = false, stopping = false;
+  uint64_t reserved = 0, peak_reserved = 0;
+  int in_flight = 0, peak_in_flight = 0;
+  int64_t batches = 0, batched_requests = 0, completed = 0;
+  std::vector<std::thread> threads;
+  gs_status first_error = GS_OK;
+};
+
+namespace {
+
+gs_status run_batch(gs_server* s, gs_workspace* ws, cudaStream_t stream, std::vector<Req*>& batch,
+                    int32_t** pair_buf, int64_t* pair_cap, int64_t** seg_dev, int64_t* seg_cap) {
+  const int64_t nb = (int64_t)batch.size();
+  std::vector<int64_t> seg(nb + 1, 0);
+  uint32_t mask = 0;
+  // sample every request into the concatenated list (union vertex ids)
+  for (int64_t i = 0; i < nb; ++i) {
+    Req* q = batch[i];
+    const int g = q->r.graph;
+    mask |= q->r.mask;
+    int64_t k = 0;
+    // count first (no output), then make room and write
+    int32_t* dst = nullptr;
+    GS_TRY(sample_range(s->ug, ws, q->r.fraction, q->r.seed, s->edge_base[g], s->m[g], nullptr, 0,
+                        &k, &dst, stream));
+    // sample_range with d_pairs == NULL wrote into workspace slot 3; move it
+    if (seg[i] + k > *pair_cap) {
+      int64_t cap = std::max<int64_t>(2 * *pair_cap, seg[i] + k + 1024);
+      int32_t* nbuf = nullptr;
+      GS_CUDA(cudaMalloc(&nbuf, sizeof(int32_t) * 2 * cap));
+      if (*pair_buf != nullptr) {
+        GS_CUDA(cudaMemcpyAsync(nbuf, *pair_buf, sizeof(int32_t) * 2 * seg[i],
+                                cudaMemcpyDeviceToDevice, stream));
+        GS_CUDA(cudaStreamSynchronize(stream));
+        cudaFree(*pair_buf);
+      }
+      *pair_buf = nbuf;
+      *pair_cap = cap;
+    }
+    if (k > 0)
+      GS_CUDA(cudaMemcpyAsync(*pair_buf + 2 * seg[i], dst, sizeof(int32_t) * 2 * k,
+                              cudaMemcpyDeviceToDevice, stream));
+    q->k = k;
+    seg[i + 1] = seg[i] + k;
+  }
+  const int64_t K = seg[nb];
+  if (nb + 1 > *seg_cap) {
+    cudaFree(*seg_dev);
+    GS_CUDA(cudaMalloc(seg_dev, sizeof(int64_t) * (nb + 1)));
+    *seg_cap = nb + 1;
+  }
+  GS_CUDA(cudaMemcpyAsync(*seg_dev, seg.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
+                          stream));
+  std::vector<unsigned long long> h((size_t)nb * 32, 0);
+  if (K > 0) {
+    CountBufs b;
+    GS_TRY(count_run(s->ug, ws, *pair_buf, K, mask, false, nullptr, *seg_dev, nb,
+                     ws->has_tuning ? ws->tuning : default_tuning(), b, stream, "gs_server"));
+    GS_CUDA(cudaMemcpyAsync(h.data(), b.seg_sums, sizeof(unsigned long long) * nb * 32,
+                            cudaMemcpyDeviceToHost, stream));
+  }
+  GS_CUDA(cudaStreamSynchronize(stream));
+  for (int64_t i = 0; i < nb; ++i) {
+    Req* q = batch[i];
+    gs_sums sums;
+    memset(&sums, 0, sizeof(sums));
+    sums.k = q->k;
+    sums.m = s->m[q->r.graph];
+    sums.mask = q->r.mask;
+    store_sums(h.data() + 32 * i, q->r.mask, &sums);
+    q->status = gs_estimate(&sums, q->r.z, &q->res);
+  }
+  return GS_OK;
+}
+
+void lane_main(gs_server* s) {
+  cudaStream_t stream = nullptr;
+  gs_workspace* ws = nullptr;
+  int32_t* pair_buf = nullptr;
+  int64_t pair_cap = 0;
+  int64_t* seg_dev = nullptr;
+  int64_t seg_cap = 0;
+  cudaSetDevice(s->device);
+  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  gs_workspace_create(&ws);
+  for (;;) {
+    std::vector<Req*> batch;
+    int64_t est = 0;
+    {
+      std::unique_lock<std::mutex> lock(s->mu);
+      s->cv_work.wait(lock, [&] { return s->stopping || !s->pending.empty(); });
+      if (s->stopping && s->pending.empty()) break;
+      // admit FIFO while the estimate fits the budget next to other lanes
+      while (!s->pending.empty() && (int)batch.size() < s->max_batch) {
+        Req* q = s->pending.front();
+        const bool alone = batch.empty() && s->reserved == 0;
+        if (!alone && s->reserved + est + (uint64_t)q->est_bytes > s->budget) break;
+        s->pending.pop_front();
+        batch.push_back(q);
+        est += q->est_bytes;
+      }
+      if (batch.empty()) {
+        // the head request must wait for memory held by another lane
+        s->cv_work.wait_for(lock, std::chrono::milliseconds(1));
+        continue;
+      }
+      s->reserved += est;
+      s->peak_reserved = std::max(s->peak_reserved, s->reserved);
+      s->in_flight += 1;
+      s->peak_in_flight = std::max(s->peak_in_flight, s->in_flight);
+      s->batches += 1;
+      s->batched_requests += (int64_t)batch.size();
+    }
+    const double t0 = now_s();
+    for (Req* q : batch) {
+      q->t_start = t0;
+      q->batch_size = (int64_t)batch.size();
+    }
+    gs_status st = run_batch(s, ws, stream, batch, &pair_buf, &pair_cap, &seg_dev, &seg_cap);
+    const double t1 = now_s();
+    {
+      std::lock_guard<std::mutex> lock(s->mu);
+      for (Req* q : batch) {
+        if (st != GS_OK) q->status = st;
+        q->t_done = t1;
+        q->done = 1;
+        s->completed += 1;
+      }
+      if (st != GS_OK && s->first_error == GS_OK) s->first_error = st;
+      s->reserved -= est;
+      s->in_flight -= 1;
+    }
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+  }
+  cudaStreamSynchronize(stream);
+  cudaFree(pair_buf);
+  cudaFree(seg_dev);
+  gs_workspace_destroy(ws);
+  cudaStreamDestroy(stream);
+}
+
+}  // namespace
+
+extern "C" gs_status gs_server_create(uint64_t hbm_budget_bytes, int32_t max_batch, int32_t lanes,
+                                      gs_server** out) {
+  if (out == nullptr || hbm_budget_bytes == 0 || max_batch < 1 || lanes < 1 || lanes > 16) {
+    set_error("gs_server_create: invalid arguments (budget > 0, max_batch >= 1, lanes 1..16)");
+    return GS_EINVAL;
+  }
+  gs_server* s = new gs_server();
+  s->budget = hbm_budget_bytes;
+  s->max_batch = max_batch;
+  s->lanes = lanes;
+  *out = s;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_server_add_graph(gs_server* s, const int64_t* d_row_ptr,
+                                         const int32_t* d_col, int64_t n, int64_t nnz,
+                                         int32_t* graph_id) {
+  if (s == nullptr || graph_id == nullptr || d_row_ptr == nullptr || n < 0 || nnz < 0 ||
+      (nnz > 0 && d_col == nullptr)) {
+    set_error("gs_server_add_graph: invalid arguments");
+    return GS_EINVAL;
+  }
+  if (s->started) {
+    set_error("gs_server_add_graph: graphs must be added before gs_server_start");
+    return GS_EINVAL;
+  }
+  *graph_id = (int32_t)s->src.size();
+  s->src.push_back(Source{d_row_ptr, d_col, n, nnz});
+  return GS_OK;
+}
+
+extern "C" gs_status gs_server_start(gs_server* s, uint32_t flags, uint64_t hub_budget_bytes,
+                                     void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (s == nullptr || s->started || s->src.empty()) {
+    set_error("gs_server_start: no graphs added, or already started");
+    return GS_EINVAL;
+  }
+  GS_CUDA(cudaGetDevice(&s->device));
+  const int64_t G = (int64_t)s->src.size();
+  int64_t N = 0, NNZ = 0;
+  s->vtx_off.assign(G + 1, 0);
+  std::vector<int64_t> nnz_off(G + 1, 0);
+  for (int64_t g = 0; g < G; ++g) {
+    s->vtx_off[g + 1] = s->vtx_off[g] + s->src[g].n;
+    nnz_off[g + 1] = nnz_off[g] + s->src[g].nnz;
+  }
+  N = s->vtx_off[G];
+  NNZ = nnz_off[G];
+  if (N > INT32_MAX) {
+    set_error("gs_server_start: the resident graphs exceed 2^31 vertices in total");
+    return GS_EINVAL;
+  }
+  GS_CUDA(cudaMalloc(&s->u_row_ptr, sizeof(int64_t) * (N + 1)));
+  GS_CUDA(cudaMalloc(&s->u_col, sizeof(int32_t) * (NNZ > 0 ? NNZ : 1)));
+  GS_CUDA(cudaMalloc(&s->d_vtx_off, sizeof(int64_t) * (G + 1)));
+  for (int64_t g = 0; g < G; ++g) {
+    const Source& c = s->src[g];
+    const int64_t work = std::max(c.n, c.nnz);
+    if (work > 0)
+      k_union_copy<<<grid_for(work, 256, 8), 256, 0, stream>>>(c.row_ptr, c.col, c.n, c.nnz,
+                                                               s->vtx_off[g], nnz_off[g],
+                                                               s->u_row_ptr, s->u_col);
+  }
+  GS_CUDA(cudaMemcpyAsync(s->u_row_ptr + N, &NNZ, sizeof(int64_t), cudaMemcpyHostToDevice, stream));
+  GS_CUDA(cudaMemcpyAsync(s->d_vtx_off, s->vtx_off.data(), sizeof(int64_t) * (G + 1),
+                          cudaMemcpyHostToDevice, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  GS_TRY(gs_graph_create(s->u_row_ptr, s->u_col, N, NNZ, flags, hub_budget_bytes, stream, &s->ug));
+  // canonical edge ranges per graph and the memory model
+  std::vector<int64_t> eoff(G + 1);
+  for (int64_t g = 0; g <= G; ++g)
+    GS_CUDA(cudaMemcpyAsync(&eoff[g], s->ug->edge_off + s->vtx_off[g], sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, stream));
+  unsigned long long* d_pos = nullptr;
+  GS_CUDA(cudaMalloc(&d_pos, sizeof(unsigned long long) * G));
+  GS_CUDA(cudaMemsetAsync(d_pos, 0, sizeof(unsigned long long) * G, stream));
+  if (N > 0)
+    k_positions_per_graph<<<grid_for(N * 32, 256, 8), 256, 0, stream>>>(
+        s->u_row_ptr, s->u_col, s->ug->up_ptr, N, s->d_vtx_off, G, d_pos);
+  std::vector<unsigned long long> pos(G);
+  GS_CUDA(cudaMemcpyAsync(pos.data(), d_pos, sizeof(unsigned long long) * G,
+                          cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  cudaFree(d_pos);
+  s->edge_base.assign(G, 0);
+  s->m.assign(G, 0);
+  s->bytes_per_edge.assign(G, 0);
+  for (int64_t g = 0; g < G; ++g) {
+    s->edge_base[g] = eoff[g];
+    s->m[g] = eoff[g + 1] - eoff[g];
+    // per sampled edge: ~120 B of per-edge arrays plus, per 4-node position,
+    // T-bit / cost / task words (20/32 B) and a T entry allowance (1 B)
+    const double pp = s->m[g] > 0 ? (double)pos[g] / (double)s->m[g] : 0.0;
+    s->bytes_per_edge[g] = 120.0 + 1.625 * pp;
+  }
+  s->started = true;
+  for (int i = 0; i < s->lanes; ++i) s->threads.emplace_back(lane_main, s);
+  return GS_OK;
+}
+
+extern "C" gs_status gs_server_submit(gs_server* s, const gs_request* r, uint64_t* ticket) {
+  if (s == nullptr || r == nullptr || ticket == nullptr || !s->started) {
+    set_error("gs_server_submit: invalid arguments or server not started");
+    return GS_EINVAL;
+  }
+  if (r->graph < 0 || r->graph >= (int32_t)s->src.size() || r->mask == 0 ||
+      (r->mask & ~(uint32_t)GS_CONNECTED) != 0 || !(r->fraction >= 0.0 && r->fraction <= 1.0) ||
+      !(r->z >= 0.0)) {
+    set_error("gs_server_submit: bad request (graph id, mask, fraction in [0,1], z >= 0)");
+    return GS_EINVAL;
+  }
+  Req* q = new Req();
+  memset(q, 0, sizeof(*q));
+  q->r = *r;
+  q->t_submit = now_s();
+  const double kexp = r->fraction * (double)s->m[r->graph];
+  q->est_bytes = (int64_t)((kexp + 4.0 * sqrt(kexp + 1.0) + 64.0) * s->bytes_per_edge[r->graph]);
+  if ((uint64_t)q->est_bytes > s->budget) {
+    delete q;
+    set_error("gs_server_submit: the request's estimated memory exceeds the server budget");
+    return GS_EBUDGET;
+  }
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    q->ticket = s->next_ticket++;
+    s->reqs[q->ticket] = q;
+    s->pending.push_back(q);
+    *ticket = q->ticket;
+  }
+  s->cv_work.notify_one();
+  return GS_OK;
+}
+
+static void fill_req_stats(const Req* q, gs_request_stats* st) {
+  if (st == nullptr) return;
+  st->k = q->k;
+  st->batch_size = q->batch_size;
+  st->queue_s = q->t_start - q->t_submit;
+  st->latency_s = q->t_done - q->t_submit;
+  st->est_bytes = q->est_bytes;
+}
+
+extern "C" gs_status gs_server_wait(gs_server* s, uint64_t ticket, double timeout_s,
+                                    gs_result* out, gs_request_stats* st) {
+  if (s == nullptr || out == nullptr) {
+    set_error("gs_server_wait: invalid arguments");
+    return GS_EINVAL;
+  }
+  std::unique_lock<std::mutex> lock(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) {
+    set_error("gs_server_wait: unknown ticket %llu", (unsigned long long)ticket);
+    return GS_EINVAL;
+  }
+  Req* q = it->second;
+  const auto until = std::chrono::steady_clock::now() +
+                     std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                         std::chrono::duration<double>(timeout_s));
+  if (!s->cv_done.wait_until(lock, until, [&] { return q->done != 0; })) {
+    set_error("gs_server_wait: request %llu not finished within %.3f s",
+              (unsigned long long)ticket, timeout_s);
+    return GS_ETIMEOUT;
+  }
+  *out = q->res;
+  fill_req_stats(q, st);
+  gs_status status = q->status;
+  s->reqs.erase(it);
+  delete q;
+  if (status != GS_OK) set_error("gs_server_wait: request %llu failed", (unsigned long long)ticket);
+  return status;
+}
+
+extern "C" gs_status gs_server_info(gs_server* s, gs_server_stats* out) {
+  if (s == nullptr || out == nullptr) {
+    set_error("gs_server_info: invalid arguments");
+    return GS_EINVAL;
+  }
+  std::lock_guard<std::mutex> lock(s->mu);
+  memset(out, 0, sizeof(*out));
+  out->graphs = (int64_t)s->src.size();
+  out->batches = s->batches;
+  out->completed = s->completed;
+  out->pending = (int64_t)s->pending.size();
+  out->mean_batch = s->batches ? (double)s->batched_requests / (double)s->batches : 0.0;
+  out->peak_reserved_bytes = s->peak_reserved;
+  out->peak_in_flight = s->peak_in_flight;
+  out->budget_bytes = s->budget;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_server_destroy(gs_server* s) {
+  if (s == nullptr) return GS_OK;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->stopping = true;
+  }
+  s->cv_work.notify_all();
+  for (auto& t : s->threads) t.join();
+  for (auto& kv : s->reqs) delete kv.second;
+  if (s->ug) gs_graph_destroy(s->ug);
+  cudaFree(s->u_row_ptr);
+  cudaFree(s->u_col);
+  cudaFree(s->d_vtx_off);
+  delete s;
+  return GS_OK;
+}
