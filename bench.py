@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=("chung_lu_1m", "batch", "serve"), default="chung_lu_1m",
+                    help="chung_lu_1m = the headline line; batch / serve = the batched and "
+                         "served paths against one plain launch per graph / request")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
 
 
@@ -368,6 +374,182 @@ def run_reference(args, rank, world):
     }
 
 
+# ------------------------------------------------------------------ batched
+
+def run_batch_bench(args):
+    """4096 small graphs (n ~ U{50..5000}, mean degree ~ U[4,40], ER /
+    Chung-Lu 2.3 / 2-D RGG): exact connected counts for every graph in one
+    CUDA-graph launch, against one gs_count per graph (each graph registered
+    beforehand, counting only in the timed region)."""
+    import numpy as np
+    import torch
+
+    import paper_1701_01772_gb300 as gs
+    import synth
+
+    gs.build()
+    t0 = time.time()
+    graphs = synth.batch_4096(args.batch_graphs)
+    gen_s = time.time() - t0
+    edges = sum(len(c) // 2 for _, c in graphs)
+    t0 = time.time()
+    b = gs.Batch.from_graphs(graphs, autotune=True)
+    create_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.count()
+    ms = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sums = b.count()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    batched_ms = statistics.median(ms)
+    # baseline: one plain gs_count launch sequence per graph
+    # (small per-graph hub index: 4096 full-size co-degree tables would not fit)
+    singles = [gs.Graph.from_numpy(rp, col, hub_budget_bytes=1 << 20) for rp, col in graphs]
+    for g in singles[:8]:
+        g.count(None, gs.GS_CONNECTED)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    per_graph = [g.count(None, gs.GS_CONNECTED) for g in singles]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1)
+    same = all(a.sums() == c.sums() for a, c in zip(sums, per_graph))
+    info = b.info()
+    for g in singles:
+        g.close()
+    b.close()
+    return {
+        "metric": "graphs/s for exact connected 3- and 4-node counts (batched)",
+        "value": round(len(graphs) / (batched_ms / 1e3), 1), "unit": "graphs/s",
+        "edges_per_s": round(edges / (batched_ms / 1e3), 1),
+        "ms_per_step": round(batched_ms, 3), "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"batch: {len(graphs)} graphs, {edges} edges, n ~ U{{50..5000}}, "
+                               "mean degree ~ U[4,40], ER / Chung-Lu 2.3 / RGG",
+                   "generation_s": round(gen_s, 1), "create_and_autotune_s": round(create_s, 2)},
+        "autotune": info,
+        "baseline_one_launch_per_graph_ms": round(single_ms, 3),
+        "speedup_vs_per_graph": round(single_ms / batched_ms, 2),
+        "identical_results": same,
+    }
+
+
+# ------------------------------------------------------------------ serving
+
+def run_serve_bench(args):
+    """Poisson request stream over 8 resident graphs (ER 2000 x2, Chung-Lu
+    100k x2, Chung-Lu 1M x2, R-MAT 24 x2); fractions log-uniform in
+    [0.1%, 10%], random seeds and non-empty graphlet masks; 4-node masks are
+    not drawn for the R-MAT graphs (their 4-node requests take seconds to a
+    minute each). The server (40 GB budget, 2 lanes) against the same
+    requests run one by one with gs_count_estimate on the same GPU."""
+    import numpy as np
+    import torch
+
+    import paper_1701_01772_gb300 as gs
+    import synth
+
+    gs.build()
+    base = synth.BASE_SEED + 4
+    specs = [("er_2000", lambda s: synth.er(2000, 20000, s)),
+             ("chung_lu_100k", lambda s: synth.chung_lu_100k(s)),
+             ("chung_lu_1m", lambda s: synth.chung_lu(1_000_000, 20_000_000, 2.1, 50_000.0, s)),
+             ("rmat_24", lambda s: synth.rmat(24, 16, s))]
+    t0 = time.time()
+    graphs, names = [], []
+    for name, make in specs:
+        for rep in range(2):
+            graphs.append(make(base + 10 * len(graphs) + rep))
+            names.append(name)
+    gen_s = time.time() - t0
+    rng = np.random.default_rng(base)
+    n_req = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n_req))
+    gidx = rng.integers(0, len(graphs), size=n_req)
+    frac = 10 ** rng.uniform(-3, -1, size=n_req)
+    seeds = rng.integers(1, 2**62, size=n_req)
+    all_bits = [3, 4, 7, 8, 9, 10, 11, 12]
+    masks = []
+    for i in range(n_req):
+        bits = [b for b in all_bits if rng.random() < 0.5] or [3]
+        if names[gidx[i]] == "rmat_24":
+            bits = [b for b in bits if b in (3, 4)] or [3]
+        masks.append(sum(1 << b for b in bits))
+    # --- server
+    srv = gs.Server(hbm_budget_bytes=40 << 30, max_batch=64, lanes=2)
+    ids = [srv.add_numpy(rp, col) for rp, col in graphs]
+    t0 = time.time()
+    srv.start()
+    start_s = time.time() - t0
+    # warm-up: one request per graph
+    for gi in range(len(graphs)):
+        srv.wait(srv.submit(ids[gi], 0.001, 1, gs.GS_THREE_NODE))
+    tickets = []
+    lat, served = [], []
+    try:
+        t_begin = time.perf_counter()
+        for i in range(n_req):
+            delay = t_begin + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(ids[gidx[i]], float(frac[i]), int(seeds[i]), masks[i]))
+        for t in tickets:
+            res, st = srv.wait(t, 600.0)
+            lat.append(st["latency_s"] * 1e3)
+            served.append(res)
+        makespan = time.perf_counter() - t_begin
+        info = srv.info()
+    finally:
+        srv.close()
+    torch.cuda.synchronize()
+    # --- baseline: one gs_count_estimate per request, in arrival order
+    singles = [gs.Graph.from_numpy(rp, col) for rp, col in graphs]
+    for g in singles:
+        g.count_estimate(0.001, 1, gs.GS_THREE_NODE)
+    torch.cuda.synchronize()
+    base_lat = []
+    same = True
+    t_begin = time.perf_counter()
+    for i in range(n_req):
+        delay = t_begin + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        res, _ = singles[gidx[i]].count_estimate(float(frac[i]), int(seeds[i]), masks[i])
+        base_lat.append((time.perf_counter() - t_begin - arrivals[i]) * 1e3)
+        a, c = res.as_dict(), served[i].as_dict()
+        for g in a:
+            for key in ("X", "V"):
+                x, y = a[g][key], c[g][key]
+                if not ((x != x and y != y) or x == y):
+                    same = False
+    base_makespan = time.perf_counter() - t_begin
+    for g in singles:
+        g.close()
+    return {
+        "metric": "requests/s served (p50/p99 latency)", "value": round(n_req / makespan, 1),
+        "unit": "req/s", "p50_ms": round(percentile(lat, 50), 3),
+        "p99_ms": round(percentile(lat, 99), 3), "higher_is_better": True, "data": "synthetic",
+        "config": {"workload": "serve: 8 resident graphs (ER 2000 x2, Chung-Lu 100k x2, Chung-Lu "
+                               "1M x2, R-MAT 24 x2), Poisson arrivals, fractions log-uniform "
+                               "[0.1%, 10%], random masks (3-node only on R-MAT)",
+                   "requests": n_req, "offered_rate": args.serve_rate, "budget_gb": 40,
+                   "lanes": 2, "generation_s": round(gen_s, 1), "start_s": round(start_s, 2)},
+        "server": info,
+        "baseline_one_launch_per_request": {"value": round(n_req / base_makespan, 1),
+                                            "p50_ms": round(percentile(base_lat, 50), 3),
+                                            "p99_ms": round(percentile(base_lat, 99), 3)},
+        "identical_results": same,
+    }
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -379,6 +561,12 @@ def main():
         out = run_reference(args, rank, world)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.workload == "batch":
+        print(json.dumps(run_batch_bench(args)), flush=True)
+        return
+    if args.workload == "serve":
+        print(json.dumps(run_serve_bench(args)), flush=True)
         return
     if world > 1:
         import torch

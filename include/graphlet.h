@@ -51,7 +51,8 @@ enum {
   GS_EBUDGET = 10,     /* request exceeds a configured memory budget */
   GS_ETIMEOUT = 11,    /* a bounded device-side wait expired */
   GS_ECUDA = 12,       /* a CUDA runtime call failed (message has details) */
-  GS_ECAPACITY = 13    /* an output buffer is too small (size is reported) */
+  GS_ECAPACITY = 13,   /* an output buffer is too small (size is reported) */
+  GS_ECANCELLED = 14   /* a queued request was dropped by gs_server_destroy */
 };
 
 /* Graphlet mask: bit i set = graphlet G_i requested. */
@@ -262,16 +263,16 @@ gs_status gs_batch_destroy(gs_batch* b);
 /* ------------------------------------------------------------------------
  * Serving: estimation requests over resident graphs, batched continuously.
  *
- * gs_server_add_graph registers a graph (device CSR as for gs_graph_create,
- * borrowed until gs_server_start copies it into the server's union graph);
- * gs_server_start builds the union and its index and starts `lanes` worker
- * threads, each with its own CUDA stream. A request names a graph, a
- * graphlet mask, a sample fraction (Algorithm 1, same sampler and seed
- * semantics as gs_sample on that graph alone), a seed and z. Workers take
- * queued requests in arrival order into a batch while the batch's estimated
- * device memory fits hbm_budget_bytes next to the batches other workers
- * hold, sample them, and count the whole batch in one pass with a separate
- * exact fold per request; a request's result is identical to running it
+ * gs_server_add_graph adds a graph (device CSR as for gs_graph_create,
+ * borrowed until gs_server_destroy); gs_server_start registers every graph
+ * (each with its own hub index) and starts `lanes` worker threads, each
+ * with its own CUDA stream. A request names a graph, a graphlet mask, a
+ * sample fraction (Algorithm 1, same sampler and seed semantics as
+ * gs_sample on that graph), a seed and z. Workers take queued requests in
+ * arrival order into a batch while the batch's estimated device memory fits
+ * hbm_budget_bytes next to the batches other workers hold; a batch's
+ * requests on one graph are sampled and counted in one pass with a separate
+ * exact fold per request, so a request's result is identical to running it
  * alone. gs_server_wait blocks until a ticket's result is ready (or
  * timeout_s passes: GS_ETIMEOUT, the request stays queued). Latencies are
  * measured on the host from submit to completion.
@@ -308,7 +309,9 @@ gs_status gs_server_submit(gs_server* s, const gs_request* r, uint64_t* ticket);
 gs_status gs_server_wait(gs_server* s, uint64_t ticket, double timeout_s, gs_result* out,
                          gs_request_stats* stats);
 gs_status gs_server_info(gs_server* s, gs_server_stats* out);
-/* Stops the workers after the queued requests finish, frees everything. */
+/* Cancels queued requests (GS_ECANCELLED), lets batches already on the
+ * device finish, stops the workers and frees everything. No ticket may be
+ * waited on after this call. */
 gs_status gs_server_destroy(gs_server* s);
 
 /* ------------------------------------------------------------------------

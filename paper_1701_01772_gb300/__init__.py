@@ -30,7 +30,8 @@ GS_F_COMPUTED, GS_F_EXACT, GS_F_VAR_UNDEFINED, GS_F_OVERFLOW = 1, 2, 4, 8
 
 STATUS = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOTSORTED", 3: "GS_ESELFLOOP", 4: "GS_EDUP",
           5: "GS_EASYM", 6: "GS_EEDGE", 7: "GS_EDUPSAMPLE", 8: "GS_EOVERFLOW", 9: "GS_ENOMEM",
-          10: "GS_EBUDGET", 11: "GS_ETIMEOUT", 12: "GS_ECUDA", 13: "GS_ECAPACITY"}
+          10: "GS_EBUDGET", 11: "GS_ETIMEOUT", 12: "GS_ECUDA", 13: "GS_ECAPACITY",
+          14: "GS_ECANCELLED"}
 
 
 class GraphletError(RuntimeError):
@@ -558,7 +559,6 @@ class Server:
 
     def start(self, validate: bool = True, hub_budget_bytes: int = 0):
         gs_server_start(self.handle, validate, hub_budget_bytes)
-        self._keep = []  # the union copy is made; inputs may be released
 
     def submit(self, graph: int, fraction: float, seed: int, mask: int = GS_CONNECTED,
                z: float = 1.96) -> int:
@@ -574,6 +574,7 @@ class Server:
         if getattr(self, "handle", None):
             gs_server_destroy(self.handle)
             self.handle = None
+        self._keep = []
 
     def __del__(self):
         try:

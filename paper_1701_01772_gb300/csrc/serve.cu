@@ -1,20 +1,18 @@
 // Serving: continuous batching of estimation requests over resident graphs.
 //
-// All graphs added to a server are registered as one disjoint union (vertex
-// ids shifted per graph), so requests on different graphs can share one
-// counting pass: each request's sampled edges are drawn from its graph's
-// range of the union's canonical edge order (the hash index is relative to
-// that range, so the sample equals the one gs_sample draws on the graph
-// alone), the edge lists of a batch are concatenated, and the fold sums each
-// request's range separately. Per-edge counts do not depend on the other
-// edges of the pass, so every result is identical alone and in any mix.
-//
-// Worker lanes (host threads, each with its own CUDA stream and workspace)
-// take requests from a FIFO queue. A lane admits requests while their
-// estimated device memory fits the server's budget together with what the
-// other lanes hold; the estimate is reserved until the batch finishes.
-// Requests that arrive while a lane's batch is on the GPU are picked up by
-// the next free lane, so batches overlap on the device.
+// Each resident graph keeps its own registration and hub index (sharing one
+// index between graphs would hand the hub slots to the largest graph and
+// slow every other one down). Worker lanes (host threads, each with its own
+// CUDA stream and workspace) take queued requests in arrival order while the
+// batch's estimated device memory fits the server budget next to what the
+// other lanes hold; the estimate stays reserved until the batch finishes.
+// A batch is counted graph by graph: all its requests on one graph are
+// sampled (the same sampler and seeds as gs_sample), concatenated and
+// counted in one pass whose fold sums each request's edges separately.
+// Per-edge counts do not depend on the other edges of a pass, so a result is
+// identical alone and in any mix. Requests that arrive while a lane's batch
+// is on the GPU are picked up by the next free lane, so batches overlap on
+// the device.
 #include <math.h>
 #include <string.h>
 
@@ -31,47 +29,25 @@
 
 namespace gs {
 
-// Per-graph sum of roundup32(min(d_u, d_v)) over canonical edges u < v
-// (4-node positions), for the memory estimate. One warp per vertex.
-__global__ void k_positions_per_graph(const int64_t* __restrict__ row_ptr,
-                                      const int32_t* __restrict__ col,
-                                      const int64_t* __restrict__ up_ptr, int64_t n,
-                                      const int64_t* __restrict__ vtx_off, int64_t num_graphs,
-                                      unsigned long long* __restrict__ out) {
+// Sum of roundup32(min(d_u, d_v)) over canonical edges u < v (4-node
+// positions), for the memory estimate. One warp per vertex.
+__global__ void k_positions(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const int64_t* __restrict__ up_ptr, int64_t n,
+                            unsigned long long* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long s = 0;
   for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
     const int64_t du = row_ptr[u + 1] - row_ptr[u];
-    unsigned long long s = 0;
     for (int64_t p = up_ptr[u] + lane; p < row_ptr[u + 1]; p += 32) {
       const int32_t v = col[p];
       const int64_t dv = row_ptr[v + 1] - row_ptr[v];
       const int64_t dm = du < dv ? du : dv;
       s += (unsigned long long)((dm + 31) & ~(int64_t)31);
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0 && s) {
-      int64_t lo = 0, len = num_graphs;
-      while (len > 1) {
-        int64_t half = len >> 1;
-        lo = (vtx_off[lo + half] <= u) ? lo + half : lo;
-        len -= half;
-      }
-      atomicAdd(out + lo, s);
-    }
   }
-}
-
-// Copies graph g's CSR into the union with row offsets shifted by nnz_base
-// and vertex ids by vtx_base.
-__global__ void k_union_copy(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                             int64_t n, int64_t nnz, int64_t vtx_base, int64_t nnz_base,
-                             int64_t* __restrict__ u_row_ptr, int32_t* __restrict__ u_col) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    u_row_ptr[vtx_base + i] = row_ptr[i] + nnz_base;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride)
-    u_col[nnz_base + p] = col[p] + (int32_t)vtx_base;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0 && s) atomicAdd(out, s);
 }
 
 }  // namespace gs
@@ -111,12 +87,8 @@ struct gs_server {
   int max_batch;
   int lanes;
   std::vector<Source> src;
-  // union
-  int64_t* u_row_ptr = nullptr;
-  int32_t* u_col = nullptr;
-  int64_t* d_vtx_off = nullptr;
-  gs_graph* ug = nullptr;
-  std::vector<int64_t> vtx_off, edge_base, m;
+  std::vector<gs_graph*> graphs;  // one registration (and hub index) per graph
+  std::vector<int64_t> m;
   std::vector<double> bytes_per_edge;
   // queue
   std::mutex mu;
@@ -136,65 +108,69 @@ namespace {
 
 gs_status run_batch(gs_server* s, gs_workspace* ws, cudaStream_t stream, std::vector<Req*>& batch,
                     int32_t** pair_buf, int64_t* pair_cap, int64_t** seg_dev, int64_t* seg_cap) {
-  const int64_t nb = (int64_t)batch.size();
-  std::vector<int64_t> seg(nb + 1, 0);
-  uint32_t mask = 0;
-  // sample every request into the concatenated list (union vertex ids)
-  for (int64_t i = 0; i < nb; ++i) {
-    Req* q = batch[i];
-    const int g = q->r.graph;
-    mask |= q->r.mask;
-    int64_t k = 0;
-    // count first (no output), then make room and write
-    int32_t* dst = nullptr;
-    GS_TRY(sample_range(s->ug, ws, q->r.fraction, q->r.seed, s->edge_base[g], s->m[g], nullptr, 0,
-                        &k, &dst, stream));
-    // sample_range with d_pairs == NULL wrote into workspace slot 3; move it
-    if (seg[i] + k > *pair_cap) {
-      int64_t cap = std::max<int64_t>(2 * *pair_cap, seg[i] + k + 1024);
-      int32_t* nbuf = nullptr;
-      GS_CUDA(cudaMalloc(&nbuf, sizeof(int32_t) * 2 * cap));
-      if (*pair_buf != nullptr) {
-        GS_CUDA(cudaMemcpyAsync(nbuf, *pair_buf, sizeof(int32_t) * 2 * seg[i],
-                                cudaMemcpyDeviceToDevice, stream));
-        GS_CUDA(cudaStreamSynchronize(stream));
-        cudaFree(*pair_buf);
-      }
-      *pair_buf = nbuf;
-      *pair_cap = cap;
-    }
-    if (k > 0)
-      GS_CUDA(cudaMemcpyAsync(*pair_buf + 2 * seg[i], dst, sizeof(int32_t) * 2 * k,
-                              cudaMemcpyDeviceToDevice, stream));
-    q->k = k;
-    seg[i + 1] = seg[i] + k;
-  }
-  const int64_t K = seg[nb];
-  if (nb + 1 > *seg_cap) {
-    cudaFree(*seg_dev);
-    GS_CUDA(cudaMalloc(seg_dev, sizeof(int64_t) * (nb + 1)));
-    *seg_cap = nb + 1;
-  }
-  GS_CUDA(cudaMemcpyAsync(*seg_dev, seg.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice,
+  // group the batch by graph, keeping arrival order inside a group
+  std::vector<std::vector<Req*>> groups(s->graphs.size());
+  for (Req* q : batch) groups[q->r.graph].push_back(q);
+  for (size_t gi = 0; gi < groups.size(); ++gi) {
+    std::vector<Req*>& grp = groups[gi];
+    if (grp.empty()) continue;
+    gs_graph* gr = s->graphs[gi];
+    const int64_t nb = (int64_t)grp.size();
+    std::vector<int64_t> seg(nb + 1, 0);
+    uint32_t mask = 0;
+    for (int64_t i = 0; i < nb; ++i) {
+      Req* q = grp[i];
+      mask |= q->r.mask;
+      int64_t k = 0;
+      int32_t* dst = nullptr;  // sample into workspace slot 3, then append
+      GS_TRY(sample_range(gr, ws, q->r.fraction, q->r.seed, 0, gr->m, nullptr, 0, &k, &dst,
                           stream));
-  std::vector<unsigned long long> h((size_t)nb * 32, 0);
-  if (K > 0) {
-    CountBufs b;
-    GS_TRY(count_run(s->ug, ws, *pair_buf, K, mask, false, nullptr, *seg_dev, nb,
-                     ws->has_tuning ? ws->tuning : default_tuning(), b, stream, "gs_server"));
-    GS_CUDA(cudaMemcpyAsync(h.data(), b.seg_sums, sizeof(unsigned long long) * nb * 32,
-                            cudaMemcpyDeviceToHost, stream));
-  }
-  GS_CUDA(cudaStreamSynchronize(stream));
-  for (int64_t i = 0; i < nb; ++i) {
-    Req* q = batch[i];
-    gs_sums sums;
-    memset(&sums, 0, sizeof(sums));
-    sums.k = q->k;
-    sums.m = s->m[q->r.graph];
-    sums.mask = q->r.mask;
-    store_sums(h.data() + 32 * i, q->r.mask, &sums);
-    q->status = gs_estimate(&sums, q->r.z, &q->res);
+      if (seg[i] + k > *pair_cap) {
+        int64_t cap = std::max<int64_t>(2 * *pair_cap, seg[i] + k + 1024);
+        int32_t* nbuf = nullptr;
+        GS_CUDA(cudaMalloc(&nbuf, sizeof(int32_t) * 2 * cap));
+        if (*pair_buf != nullptr) {
+          GS_CUDA(cudaMemcpyAsync(nbuf, *pair_buf, sizeof(int32_t) * 2 * seg[i],
+                                  cudaMemcpyDeviceToDevice, stream));
+          GS_CUDA(cudaStreamSynchronize(stream));
+          cudaFree(*pair_buf);
+        }
+        *pair_buf = nbuf;
+        *pair_cap = cap;
+      }
+      if (k > 0)
+        GS_CUDA(cudaMemcpyAsync(*pair_buf + 2 * seg[i], dst, sizeof(int32_t) * 2 * k,
+                                cudaMemcpyDeviceToDevice, stream));
+      q->k = k;
+      seg[i + 1] = seg[i] + k;
+    }
+    const int64_t K = seg[nb];
+    if (nb + 1 > *seg_cap) {
+      cudaFree(*seg_dev);
+      GS_CUDA(cudaMalloc(seg_dev, sizeof(int64_t) * (nb + 1)));
+      *seg_cap = nb + 1;
+    }
+    GS_CUDA(cudaMemcpyAsync(*seg_dev, seg.data(), sizeof(int64_t) * (nb + 1),
+                            cudaMemcpyHostToDevice, stream));
+    std::vector<unsigned long long> h((size_t)nb * 32, 0);
+    if (K > 0) {
+      CountBufs b;
+      GS_TRY(count_run(gr, ws, *pair_buf, K, mask, false, nullptr, *seg_dev, nb,
+                       ws->has_tuning ? ws->tuning : default_tuning(), b, stream, "gs_server"));
+      GS_CUDA(cudaMemcpyAsync(h.data(), b.seg_sums, sizeof(unsigned long long) * nb * 32,
+                              cudaMemcpyDeviceToHost, stream));
+    }
+    GS_CUDA(cudaStreamSynchronize(stream));
+    for (int64_t i = 0; i < nb; ++i) {
+      Req* q = grp[i];
+      gs_sums sums;
+      memset(&sums, 0, sizeof(sums));
+      sums.k = q->k;
+      sums.m = gr->m;
+      sums.mask = q->r.mask;
+      store_sums(h.data() + 32 * i, q->r.mask, &sums);
+      q->status = gs_estimate(&sums, q->r.z, &q->res);
+    }
   }
   return GS_OK;
 }
@@ -215,7 +191,7 @@ void lane_main(gs_server* s) {
     {
       std::unique_lock<std::mutex> lock(s->mu);
       s->cv_work.wait(lock, [&] { return s->stopping || !s->pending.empty(); });
-      if (s->stopping && s->pending.empty()) break;
+      if (s->stopping) break;
       // admit FIFO while the estimate fits the budget next to other lanes
       while (!s->pending.empty() && (int)batch.size() < s->max_batch) {
         Req* q = s->pending.front();
@@ -307,63 +283,33 @@ extern "C" gs_status gs_server_start(gs_server* s, uint32_t flags, uint64_t hub_
     return GS_EINVAL;
   }
   GS_CUDA(cudaGetDevice(&s->device));
-  const int64_t G = (int64_t)s->src.size();
-  int64_t N = 0, NNZ = 0;
-  s->vtx_off.assign(G + 1, 0);
-  std::vector<int64_t> nnz_off(G + 1, 0);
-  for (int64_t g = 0; g < G; ++g) {
-    s->vtx_off[g + 1] = s->vtx_off[g] + s->src[g].n;
-    nnz_off[g + 1] = nnz_off[g] + s->src[g].nnz;
-  }
-  N = s->vtx_off[G];
-  NNZ = nnz_off[G];
-  if (N > INT32_MAX) {
-    set_error("gs_server_start: the resident graphs exceed 2^31 vertices in total");
-    return GS_EINVAL;
-  }
-  GS_CUDA(cudaMalloc(&s->u_row_ptr, sizeof(int64_t) * (N + 1)));
-  GS_CUDA(cudaMalloc(&s->u_col, sizeof(int32_t) * (NNZ > 0 ? NNZ : 1)));
-  GS_CUDA(cudaMalloc(&s->d_vtx_off, sizeof(int64_t) * (G + 1)));
-  for (int64_t g = 0; g < G; ++g) {
-    const Source& c = s->src[g];
-    const int64_t work = std::max(c.n, c.nnz);
-    if (work > 0)
-      k_union_copy<<<grid_for(work, 256, 8), 256, 0, stream>>>(c.row_ptr, c.col, c.n, c.nnz,
-                                                               s->vtx_off[g], nnz_off[g],
-                                                               s->u_row_ptr, s->u_col);
-  }
-  GS_CUDA(cudaMemcpyAsync(s->u_row_ptr + N, &NNZ, sizeof(int64_t), cudaMemcpyHostToDevice, stream));
-  GS_CUDA(cudaMemcpyAsync(s->d_vtx_off, s->vtx_off.data(), sizeof(int64_t) * (G + 1),
-                          cudaMemcpyHostToDevice, stream));
-  GS_CUDA(cudaStreamSynchronize(stream));
-  GS_TRY(gs_graph_create(s->u_row_ptr, s->u_col, N, NNZ, flags, hub_budget_bytes, stream, &s->ug));
-  // canonical edge ranges per graph and the memory model
-  std::vector<int64_t> eoff(G + 1);
-  for (int64_t g = 0; g <= G; ++g)
-    GS_CUDA(cudaMemcpyAsync(&eoff[g], s->ug->edge_off + s->vtx_off[g], sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, stream));
+  const size_t G = s->src.size();
   unsigned long long* d_pos = nullptr;
-  GS_CUDA(cudaMalloc(&d_pos, sizeof(unsigned long long) * G));
-  GS_CUDA(cudaMemsetAsync(d_pos, 0, sizeof(unsigned long long) * G, stream));
-  if (N > 0)
-    k_positions_per_graph<<<grid_for(N * 32, 256, 8), 256, 0, stream>>>(
-        s->u_row_ptr, s->u_col, s->ug->up_ptr, N, s->d_vtx_off, G, d_pos);
-  std::vector<unsigned long long> pos(G);
-  GS_CUDA(cudaMemcpyAsync(pos.data(), d_pos, sizeof(unsigned long long) * G,
-                          cudaMemcpyDeviceToHost, stream));
-  GS_CUDA(cudaStreamSynchronize(stream));
-  cudaFree(d_pos);
-  s->edge_base.assign(G, 0);
-  s->m.assign(G, 0);
-  s->bytes_per_edge.assign(G, 0);
-  for (int64_t g = 0; g < G; ++g) {
-    s->edge_base[g] = eoff[g];
-    s->m[g] = eoff[g + 1] - eoff[g];
+  GS_CUDA(cudaMalloc(&d_pos, sizeof(unsigned long long)));
+  for (size_t g = 0; g < G; ++g) {
+    const Source& c = s->src[g];
+    gs_graph* gr = nullptr;
+    gs_status st = gs_graph_create(c.row_ptr, c.col, c.n, c.nnz, flags, hub_budget_bytes, stream,
+                                   &gr);
+    if (st != GS_OK) {
+      cudaFree(d_pos);
+      return st;
+    }
+    s->graphs.push_back(gr);
+    unsigned long long pos = 0;
+    GS_CUDA(cudaMemsetAsync(d_pos, 0, sizeof(unsigned long long), stream));
+    if (c.n > 0)
+      k_positions<<<grid_for(c.n * 32, 256, 8), 256, 0, stream>>>(c.row_ptr, c.col, gr->up_ptr,
+                                                                  c.n, d_pos);
+    GS_CUDA(cudaMemcpyAsync(&pos, d_pos, sizeof(pos), cudaMemcpyDeviceToHost, stream));
+    GS_CUDA(cudaStreamSynchronize(stream));
+    s->m.push_back(gr->m);
     // per sampled edge: ~120 B of per-edge arrays plus, per 4-node position,
     // T-bit / cost / task words (20/32 B) and a T entry allowance (1 B)
-    const double pp = s->m[g] > 0 ? (double)pos[g] / (double)s->m[g] : 0.0;
-    s->bytes_per_edge[g] = 120.0 + 1.625 * pp;
+    const double pp = gr->m > 0 ? (double)pos / (double)gr->m : 0.0;
+    s->bytes_per_edge.push_back(120.0 + 1.625 * pp);
   }
+  cudaFree(d_pos);
   s->started = true;
   for (int i = 0; i < s->lanes; ++i) s->threads.emplace_back(lane_main, s);
   return GS_OK;
@@ -385,7 +331,10 @@ extern "C" gs_status gs_server_submit(gs_server* s, const gs_request* r, uint64_
   q->r = *r;
   q->t_submit = now_s();
   const double kexp = r->fraction * (double)s->m[r->graph];
-  q->est_bytes = (int64_t)((kexp + 4.0 * sqrt(kexp + 1.0) + 64.0) * s->bytes_per_edge[r->graph]);
+  const bool four = (r->mask & ~(uint32_t)GS_THREE_NODE) != 0;
+  // 3-node requests need only the per-edge arrays
+  const double bpe = four ? s->bytes_per_edge[r->graph] : 120.0;
+  q->est_bytes = (int64_t)((kexp + 4.0 * sqrt(kexp + 1.0) + 64.0) * bpe);
   if ((uint64_t)q->est_bytes > s->budget) {
     delete q;
     set_error("gs_server_submit: the request's estimated memory exceeds the server budget");
@@ -462,16 +411,21 @@ extern "C" gs_status gs_server_info(gs_server* s, gs_server_stats* out) {
 extern "C" gs_status gs_server_destroy(gs_server* s) {
   if (s == nullptr) return GS_OK;
   {
+    // queued requests that no worker has taken are cancelled; batches
+    // already on the device finish first
     std::lock_guard<std::mutex> lock(s->mu);
     s->stopping = true;
+    for (Req* q : s->pending) {
+      q->status = GS_ECANCELLED;
+      q->done = 1;
+    }
+    s->pending.clear();
   }
   s->cv_work.notify_all();
+  s->cv_done.notify_all();
   for (auto& t : s->threads) t.join();
   for (auto& kv : s->reqs) delete kv.second;
-  if (s->ug) gs_graph_destroy(s->ug);
-  cudaFree(s->u_row_ptr);
-  cudaFree(s->u_col);
-  cudaFree(s->d_vtx_off);
+  for (gs_graph* g : s->graphs) gs_graph_destroy(g);
   delete s;
   return GS_OK;
 }
