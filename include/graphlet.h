@@ -214,6 +214,13 @@ gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_per_sm, int q
 /* Host output: statistics of the last gs_count that used `ws`. */
 gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
 
+/* Exact merge of the sums of disjoint shards of one sample (host only):
+ * acc += part. Splitting J across GPUs and merging their sums gives the
+ * same result as counting J on one GPU (the only exchange the path needs;
+ * the paper's distributed scheme sends one count vector per worker, Sec. 5).
+ * Both must have the same graph edge count m and mask. */
+gs_status gs_sums_merge(gs_sums* acc, const gs_sums* part);
+
 /* Convenience: gs_sample (fraction < 1) or all edges (fraction == 1), then
  * gs_count and gs_estimate. *k_out (host, may be NULL) receives |J|. */
 gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,

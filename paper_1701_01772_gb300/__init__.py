@@ -160,6 +160,7 @@ def lib() -> ctypes.CDLL:
         "gs_count3_static": ([P, P, I64, U32, ctypes.POINTER(GsSums), P], ctypes.c_int32),
         "gs_workspace_set_tuning": ([P, ctypes.c_int, ctypes.c_int, I64, ctypes.c_int],
                                     ctypes.c_int32),
+        "gs_sums_merge": ([ctypes.POINTER(GsSums), ctypes.POINTER(GsSums)], ctypes.c_int32),
         "gs_batch_create": ([P, P, P, I64, I64, I64, U32, U32, U64, P, PP], ctypes.c_int32),
         "gs_batch_count": ([P, ctypes.POINTER(GsSums), P], ctypes.c_int32),
         "gs_batch_info": ([P, ctypes.POINTER(GsBatchStats)], ctypes.c_int32),
@@ -332,6 +333,24 @@ def gs_batch_info(handle: int) -> dict:
 
 def gs_batch_destroy(handle: int) -> None:
     _check(lib().gs_batch_destroy(handle))
+
+
+def gs_sums_merge(acc: GsSums, part: GsSums) -> GsSums:
+    """acc += part (exact, host only), for shards of one sample."""
+    _check(lib().gs_sums_merge(ctypes.byref(acc), ctypes.byref(part)))
+    return acc
+
+
+def sums_from_ints(k: int, m: int, mask: int, sums: dict, sq: dict) -> GsSums:
+    """Packs exact Python-int sums {graphlet: value} into a GsSums."""
+    out = GsSums()
+    out.k, out.m, out.mask = k, m, mask
+    for i, g in enumerate(GRAPHLETS):
+        s = sums.get(g, 0) % (1 << 128)
+        q = sq.get(g, 0)
+        out.sum[i][0], out.sum[i][1] = s & (2**64 - 1), s >> 64
+        out.sumsq[i][0], out.sumsq[i][1] = q & (2**64 - 1), q >> 64
+    return out
 
 
 def gs_estimate(sums: GsSums, z: float = 1.96) -> GsResult:

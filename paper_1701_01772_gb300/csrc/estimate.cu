@@ -118,6 +118,27 @@ extern "C" gs_status gs_estimate(const gs_sums* s, double z, gs_result* out) {
   return GS_OK;
 }
 
+extern "C" gs_status gs_sums_merge(gs_sums* acc, const gs_sums* part) {
+  if (acc == nullptr || part == nullptr || acc->m != part->m || acc->mask != part->mask ||
+      part->k < 0 || acc->k < 0 || acc->k + part->k > acc->m) {
+    gs::set_error("gs_sums_merge: sums must come from the same graph and mask, with disjoint "
+                  "samples (k_acc + k_part <= m)");
+    return GS_EINVAL;
+  }
+  acc->k += part->k;
+  for (int i = 0; i < 8; ++i) {
+    const u128 s = ((u128)acc->sum[i][1] << 64 | acc->sum[i][0]) +
+                   ((u128)part->sum[i][1] << 64 | part->sum[i][0]);
+    const u128 q = ((u128)acc->sumsq[i][1] << 64 | acc->sumsq[i][0]) +
+                   ((u128)part->sumsq[i][1] << 64 | part->sumsq[i][0]);
+    acc->sum[i][0] = (uint64_t)s;
+    acc->sum[i][1] = (uint64_t)(s >> 64);
+    acc->sumsq[i][0] = (uint64_t)q;
+    acc->sumsq[i][1] = (uint64_t)(q >> 64);
+  }
+  return GS_OK;
+}
+
 extern "C" gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, double fraction,
                                        uint64_t seed, uint32_t mask, double z, gs_result* out,
                                        int64_t* k_out, void* stream_) {
