@@ -118,9 +118,12 @@ const char* gs_version(void);
  * self-loops. The arrays are borrowed (not copied) and must outlive the
  * handle. With GS_VALIDATE the structure is checked on the device and
  * GS_ENOTSORTED / GS_ESELFLOOP / GS_EDUP / GS_EASYM / GS_EINVAL returned.
- * Builds the per-graph index (upper-edge offsets for the sampler, hub
- * adjacency bitmaps and the hub co-degree table) in library-owned device
- * memory; hub_budget_bytes bounds that memory (0 = default 1 GiB).
+ * Builds the per-graph index (upper-edge offsets for the sampler, adjacency
+ * bitmaps of the highest-degree vertices, an adjacency bit matrix among the
+ * top 16384 of them, and a co-degree table |N(a) cap N(b)| among the top
+ * vertices) in library-owned device memory; hub_budget_bytes bounds that
+ * index (0 = default 8 GiB: bitmaps and matrix up to 1/8 each, the table the
+ * rest, at most 65535 vertices).
  * Synchronises `stream`. */
 gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n, int64_t nnz,
                           uint32_t flags, uint64_t hub_budget_bytes, void* stream,

@@ -55,10 +55,12 @@ struct DevGraph {
   const int32_t* tb_slot;   // [n] table slot of v, -1 if none (NULL if no table)
   const uint32_t* tb_codeg; // [tb_count][tb_count]
   int64_t tb_count;
-  // adjacency among table vertices as a bit matrix over table slots
-  // (tb_count^2 bits, small enough to stay in L2)
-  const uint32_t* hm_bits;  // [tb_count][hm_words]
-  int64_t hm_words;         // ceil(tb_count / 32)
+  // adjacency among the top hm_count vertices as a bit matrix over their
+  // own slots (hm_count^2 bits, small enough to stay in L2)
+  const int32_t* hm_slot;   // [n] matrix slot of v, -1 if none
+  const uint32_t* hm_bits;  // [hm_count][hm_words]
+  int64_t hm_words;         // ceil(hm_count / 32)
+  int64_t hm_count;
 };
 
 // Membership of x in the sorted list a[0..len): branch-free halving search.
@@ -75,19 +77,19 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* __restrict__ a, i
   return __ldg(base) == x;
 }
 
-// Table slot of v, or -1 (also when there is no table).
+// Hub-pair matrix slot of v, or -1 (also when there is no matrix).
 __device__ __forceinline__ int32_t table_slot(const DevGraph& g, int32_t v) {
-  return (g.hm_bits != nullptr && v >= 0) ? __ldg(g.tb_slot + v) : -1;
+  return (g.hm_bits != nullptr && v >= 0) ? __ldg(g.hm_slot + v) : -1;
 }
 
-// Membership of x in N(y): hub-pair bit matrix when both are table hubs,
+// Membership of x in N(y): hub-pair bit matrix when both have matrix slots,
 // bitmap test for bitmap hubs, halving search otherwise.
 __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64_t base_y,
                                              int64_t deg_y, int32_t x) {
   if (g.hm_bits != nullptr) {
-    int32_t ys = __ldg(g.tb_slot + y);
+    int32_t ys = __ldg(g.hm_slot + y);
     if (ys >= 0) {
-      int32_t xs = __ldg(g.tb_slot + x);
+      int32_t xs = __ldg(g.hm_slot + x);
       if (xs >= 0) {
         uint32_t w = __ldg(g.hm_bits + (int64_t)ys * g.hm_words + (xs >> 5));
         return (w >> (xs & 31)) & 1u;
@@ -105,13 +107,13 @@ __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64
 }
 
 // Membership of x in a set given either as a vertex's adjacency (vtx >= 0,
-// list = N(vtx)) or as a plain sorted list (vtx < 0). vslot is vtx's table
+// list = N(vtx)) or as a plain sorted list (vtx < 0). vslot is vtx's matrix
 // slot (-1 if none): when x also has one, the hub-pair bit matrix answers.
 __device__ __forceinline__ bool set_contains(const DevGraph& g, int32_t vtx, int32_t vslot,
                                              const int32_t* __restrict__ list, int64_t len,
                                              int32_t x) {
   if (vslot >= 0) {
-    int32_t xs = __ldg(g.tb_slot + x);
+    int32_t xs = __ldg(g.hm_slot + x);
     if (xs >= 0) {
       uint32_t w = __ldg(g.hm_bits + (int64_t)vslot * g.hm_words + (xs >> 5));
       return (w >> (xs & 31)) & 1u;
@@ -154,6 +156,7 @@ struct gs_graph {
   uint32_t* bm_bits;
   int32_t* tb_slot;
   uint32_t* tb_codeg;
+  int32_t* hm_slot;
   uint32_t* hm_bits;
 };
 

@@ -754,6 +754,7 @@ DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
     g.tb_slot = nullptr;
     g.tb_codeg = nullptr;
     g.tb_count = 0;
+    g.hm_slot = nullptr;
     g.hm_bits = nullptr;
   }
   return g;

@@ -10,8 +10,11 @@
 
 namespace gs {
 
-// Vertices below this degree never get bitmaps or table rows.
+// Vertices below this degree never get bitmaps, matrix or table rows.
 constexpr int64_t kHubMinDegree = 64;
+// The hub-pair bit matrix covers at most this many vertices (2^14 squared
+// bits = 32 MiB, which stays resident in the 129 MB L2).
+constexpr int64_t kHubMatrixMax = 16384;
 
 // ------------------------------------------------------------- validation
 // One warp per row (grid-stride). Checks the simple-graph conditions of
@@ -267,14 +270,21 @@ static gs_status hub_threshold(const gs_graph* g, int64_t cap, int64_t min_deg,
   return GS_OK;
 }
 
-// Builds bitmaps and the co-degree table within budget bytes (half each).
+// Builds bitmaps (up to 1/8 of the budget), the hub-pair matrix (up to 1/8,
+// at most kHubMatrixMax vertices) and the co-degree table (the rest) within
+// `budget` bytes (0 = 8 GiB).
 static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stream) {
   const int64_t n = g->dev.n;
-  if (budget == 0) budget = (uint64_t)1 << 31;
+  if (budget == 0) budget = (uint64_t)8 << 30;
   if (n == 0 || g->max_degree < kHubMinDegree) return GS_OK;
   const int64_t words = (n + 31) / 32;
-  const int64_t bm_cap = (int64_t)((budget / 2) / ((uint64_t)words * 4));
-  int64_t tb_cap = (int64_t)sqrt((double)(budget / 2) / 4.0);
+  // bitmaps and the matrix get up to 1/8 of the budget each, the table the rest
+  const double share = (double)budget / 8.0;
+  const int64_t bm_cap = (int64_t)(share / ((double)words * 4.0));
+  int64_t hm_cap = (int64_t)sqrt(share * 8.0);
+  if (hm_cap > kHubMatrixMax) hm_cap = kHubMatrixMax;
+  const double tb_bytes = (double)budget - share - (double)hm_cap * (double)hm_cap / 8.0;
+  int64_t tb_cap = tb_bytes > 0 ? (int64_t)sqrt(tb_bytes / 4.0) : 0;
   if (tb_cap > 65535) tb_cap = 65535;
   unsigned long long* d_cnt = nullptr;
   int64_t* flag = nullptr;
@@ -326,6 +336,29 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       g->dev.bm_count = n_bm;
     }
   }
+  // ---- hub-pair bit matrix over the top vertices (kept small: it must stay
+  // in L2 to pay off)
+  int64_t d_hm = 0, n_hm = 0;
+  if (hm_cap > 1) GS_TRY(hub_threshold(g, hm_cap, kHubMinDegree, d_cnt, stream, &d_hm, &n_hm));
+  if (n_hm > 1) {
+    int32_t* hubs = nullptr;
+    GS_TRY(assign(d_hm, &g->hm_slot, &hubs, n_hm));
+    const int64_t hm_words = (n_hm + 31) / 32;
+    cudaError_t he = cudaMalloc(&g->hm_bits, sizeof(uint32_t) * (size_t)(hm_words * n_hm));
+    if (he != cudaSuccess) {
+      cudaFree(hubs);
+      return cuda_fail(he, "hub matrix", __FILE__, __LINE__);
+    }
+    GS_CUDA(cudaMemsetAsync(g->hm_bits, 0, sizeof(uint32_t) * (size_t)(hm_words * n_hm), stream));
+    k_hub_matrix<<<grid_for(n_hm * 256, 256, 8), 256, 0, stream>>>(
+        g->dev.row_ptr, g->dev.col, g->hm_slot, hubs, n_hm, hm_words, g->hm_bits);
+    GS_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(hubs);
+    g->dev.hm_slot = g->hm_slot;
+    g->dev.hm_bits = g->hm_bits;
+    g->dev.hm_words = hm_words;
+    g->dev.hm_count = n_hm;
+  }
   // ---- co-degree table
   int64_t d_tb = 0, n_tb = 0;
   if (tb_cap > 1) {
@@ -333,16 +366,6 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     if (n_tb > 1) {
       int32_t* hubs = nullptr;
       GS_TRY(assign(d_tb, &g->tb_slot, &hubs, n_tb));
-      const int64_t hm_words = (n_tb + 31) / 32;
-      cudaError_t he = cudaMalloc(&g->hm_bits, sizeof(uint32_t) * (size_t)(hm_words * n_tb));
-      if (he != cudaSuccess) {
-        cudaFree(hubs);
-        return cuda_fail(he, "hub matrix", __FILE__, __LINE__);
-      }
-      GS_CUDA(cudaMemsetAsync(g->hm_bits, 0, sizeof(uint32_t) * (size_t)(hm_words * n_tb), stream));
-      k_hub_matrix<<<grid_for(n_tb * 256, 256, 8), 256, 0, stream>>>(
-          g->dev.row_ptr, g->dev.col, g->tb_slot, hubs, n_tb, hm_words, g->hm_bits);
-      GS_CUDA(cudaStreamSynchronize(stream));
       cudaFree(hubs);
       GS_CUDA(cudaMalloc(&g->tb_codeg, sizeof(uint32_t) * (size_t)(n_tb * n_tb)));
       GS_CUDA(cudaMemsetAsync(g->tb_codeg, 0, sizeof(uint32_t) * (size_t)(n_tb * n_tb), stream));
@@ -372,8 +395,6 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       g->dev.tb_slot = g->tb_slot;
       g->dev.tb_codeg = g->tb_codeg;
       g->dev.tb_count = n_tb;
-      g->dev.hm_bits = g->hm_bits;
-      g->dev.hm_words = hm_words;
     }
   }
   return GS_OK;
@@ -475,6 +496,7 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->bm_bits);
   cudaFree(g->tb_slot);
   cudaFree(g->tb_codeg);
+  cudaFree(g->hm_slot);
   cudaFree(g->hm_bits);
   delete g;
   return GS_OK;
