@@ -58,6 +58,7 @@ struct DevGraph {
   // adjacency among the top hm_count vertices as a bit matrix over their
   // own slots (hm_count^2 bits, small enough to stay in L2)
   const int32_t* hm_slot;   // [n] matrix slot of v, -1 if none
+  const int16_t* col_hm;    // [nnz] matrix slot of col[p], -1 if none (NULL if no matrix)
   const uint32_t* hm_bits;  // [hm_count][hm_words]
   int64_t hm_words;         // ceil(hm_count / 32)
   int64_t hm_count;
@@ -85,11 +86,11 @@ __device__ __forceinline__ int32_t table_slot(const DevGraph& g, int32_t v) {
 // Membership of x in N(y): hub-pair bit matrix when both have matrix slots,
 // bitmap test for bitmap hubs, halving search otherwise.
 __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64_t base_y,
-                                             int64_t deg_y, int32_t x) {
+                                             int64_t deg_y, int32_t x, int32_t xs_known = -2) {
   if (g.hm_bits != nullptr) {
     int32_t ys = __ldg(g.hm_slot + y);
     if (ys >= 0) {
-      int32_t xs = __ldg(g.hm_slot + x);
+      int32_t xs = xs_known != -2 ? xs_known : __ldg(g.hm_slot + x);
       if (xs >= 0) {
         uint32_t w = __ldg(g.hm_bits + (int64_t)ys * g.hm_words + (xs >> 5));
         return (w >> (xs & 31)) & 1u;
@@ -109,11 +110,14 @@ __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64
 // Membership of x in a set given either as a vertex's adjacency (vtx >= 0,
 // list = N(vtx)) or as a plain sorted list (vtx < 0). vslot is vtx's matrix
 // slot (-1 if none): when x also has one, the hub-pair bit matrix answers.
+// xs is x's matrix slot when the caller has it (stored beside the list it
+// iterates), or kNoSlotInfo to look it up.
+constexpr int32_t kNoSlotInfo = -2;
 __device__ __forceinline__ bool set_contains(const DevGraph& g, int32_t vtx, int32_t vslot,
                                              const int32_t* __restrict__ list, int64_t len,
-                                             int32_t x) {
+                                             int32_t x, int32_t xs = kNoSlotInfo) {
   if (vslot >= 0) {
-    int32_t xs = __ldg(g.hm_slot + x);
+    if (xs == kNoSlotInfo) xs = __ldg(g.hm_slot + x);
     if (xs >= 0) {
       uint32_t w = __ldg(g.hm_bits + (int64_t)vslot * g.hm_words + (xs >> 5));
       return (w >> (xs & 31)) & 1u;
@@ -158,6 +162,7 @@ struct gs_graph {
   uint32_t* tb_codeg;
   int32_t* hm_slot;
   uint32_t* hm_bits;
+  int16_t* col_hm;
 };
 
 namespace gs {
@@ -221,6 +226,7 @@ struct CountBufs {
   int64_t* task_off = nullptr;
   int64_t* tmp1 = nullptr;
   int32_t* T = nullptr;
+  int16_t* T_hm = nullptr;  // matrix slots of T's entries (NULL without a matrix)
 };
 
 Tuning default_tuning();

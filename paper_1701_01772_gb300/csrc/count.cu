@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(kThreads) k_tri(DevGraph g, const int2* __rest
       int64_t i = p - __ldg(off + le);
       if (i < du) {
         int32_t x = __ldg(g.col + bu + i);
-        hit = x != pr.y && adj_contains(g, pr.y, bv, dv, x);
+        const int32_t xs = g.col_hm != nullptr ? (int32_t)__ldg(g.col_hm + bu + i) : -2;
+        hit = x != pr.y && adj_contains(g, pr.y, bv, dv, x, xs);
       }
     }
     const unsigned ball = __ballot_sync(kFull, hit);
@@ -187,7 +188,7 @@ void launch_tri_unpadded(const DevGraph& g, const int2* uv, const int64_t* off, 
 __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off,
                             const int64_t* __restrict__ toff, int64_t K,
                             const uint32_t* __restrict__ tbits, int32_t* __restrict__ T,
-                            int64_t* __restrict__ tdeg) {
+                            int16_t* __restrict__ T_hm, int64_t* __restrict__ tdeg) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < K; e += warps) {
@@ -200,7 +201,9 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
       uint32_t word = __ldg(tbits + w0 + w);
       if ((word >> lane) & 1u) {
         int32_t x = __ldg(g.col + bu + w * 32 + lane);
-        T[pos + __popc(word & ((1u << lane) - 1u))] = x;
+        const int64_t at = pos + __popc(word & ((1u << lane) - 1u));
+        T[at] = x;
+        if (T_hm != nullptr) T_hm[at] = __ldg(g.col_hm + bu + w * 32 + lane);
         dsum += __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
       }
       pos += __popc(word);
@@ -227,6 +230,7 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
 //                holds c(w, o).
 struct Seg {
   const int32_t* it;    // iterated list
+  const int16_t* its;   // matrix slots of the iterated list's entries, or NULL
   const int32_t* sl;    // searched list
   int32_t svtx;         // vertex whose adjacency sl is (bitmap-capable), or -1
   int32_t sslot;        // table slot of svtx, or -1
@@ -288,12 +292,14 @@ __device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int6
                                               int32_t o, int64_t bo, int64_t dob, Seg& s) {
   if (dw <= dob) {
     s.it = g.col + bw;
+    s.its = g.col_hm != nullptr ? g.col_hm + bw : nullptr;
     s.sl = g.col + bo;
     s.svtx = o;
     s.slen = (int32_t)dob;
     s.cnt = (int32_t)dw;
   } else {
     s.it = g.col + bo;
+    s.its = g.col_hm != nullptr ? g.col_hm + bo : nullptr;
     s.sl = g.col + bw;
     s.svtx = w;
     s.slen = (int32_t)dw;
@@ -303,11 +309,13 @@ __device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int6
 }
 
 __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
-                                          const int32_t* __restrict__ T, int64_t i,
+                                          const int32_t* __restrict__ T,
+                                          const int16_t* __restrict__ T_hm, int64_t i,
                                           uint32_t tword, int lane, bool need_k, bool need_q,
                                           Item& it) {
   it.a.cnt = it.b.cnt = 0;
   it.a.it = it.a.sl = it.b.it = it.b.sl = g.col;
+  it.a.its = it.b.its = nullptr;
   it.a.svtx = it.b.svtx = -1;
   it.a.sslot = it.b.sslot = -1;
   it.a.slen = it.b.slen = 0;
@@ -327,12 +335,14 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
     const int64_t dup = bw + dw - upw;
     if (dup <= tg) {
       it.a.it = g.col + upw;
+      it.a.its = g.col_hm != nullptr ? g.col_hm + upw : nullptr;
       it.a.sl = T + c.toff + iw + 1;
       it.a.svtx = -1;
       it.a.slen = (int32_t)tg;
       it.a.cnt = (int32_t)dup;
     } else {
       it.a.it = T + c.toff + iw + 1;
+      it.a.its = T_hm != nullptr ? T_hm + c.toff + iw + 1 : nullptr;
       it.a.sl = g.col + bw;
       it.a.svtx = w;
       it.a.sslot = table_slot(g, w);
@@ -367,10 +377,11 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
 // Out-of-line copy for k_quad: the item set-up runs once per chunk and its
 // temporaries would otherwise raise the register count of the test loop.
 __device__ __noinline__ void load_item_outlined(const DevGraph& g, const EdgeCtx& c,
-                                                const int32_t* __restrict__ T, int64_t i,
+                                                const int32_t* __restrict__ T,
+                                                const int16_t* __restrict__ T_hm, int64_t i,
                                                 uint32_t tword, int lane, bool need_k,
                                                 bool need_q, Item& it) {
-  load_item(g, c, T, i, tword, lane, need_k, need_q, it);
+  load_item(g, c, T, T_hm, i, tword, lane, need_k, need_q, it);
 }
 
 template <class T>
@@ -385,7 +396,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 __global__ void __launch_bounds__(kThreads)
     k_chunk_cost(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
                  const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
-                 const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T, int need_k,
+                 const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
+                 const int16_t* __restrict__ T_hm, int need_k,
                  int need_q, int64_t task_probes, int64_t* __restrict__ chunk_cost,
                  int64_t* __restrict__ task_cnt, unsigned long long* __restrict__ q,
                  unsigned long long* __restrict__ stats) {
@@ -405,8 +417,8 @@ __global__ void __launch_bounds__(kThreads)
     while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
     if (e != c.e) load_edge(g, uv, t, toff, e, c);
     Item it;
-    load_item(g, c, T, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k, need_q,
-              it);
+    load_item(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k,
+              need_q, it);
     int64_t cost = warp_sum<int64_t>((int64_t)it.a.cnt + it.b.cnt);
     int64_t qc = warp_sum<int64_t>(it.qconst);
     if (lane == 0) {
@@ -425,6 +437,7 @@ __global__ void __launch_bounds__(kThreads)
 // lane can read the item its test belongs to.
 struct SharedItem {
   const int32_t* it[2];
+  const int16_t* its[2];
   const int32_t* sl[2];
   int32_t svtx[2];
   int32_t sslot[2];
@@ -437,8 +450,9 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
            const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
            const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
-           const int64_t* __restrict__ task_off, int64_t groups, int need_k, int need_q,
-           int64_t task_probes, unsigned long long* __restrict__ k_out,
+           const int16_t* __restrict__ T_hm, const int64_t* __restrict__ task_off,
+           int64_t groups, int need_k, int need_q, int64_t task_probes,
+           unsigned long long* __restrict__ k_out,
            unsigned long long* __restrict__ q) {
   __shared__ SharedItem items[kThreads / 32][32];
   const int lane = threadIdx.x & 31;
@@ -473,12 +487,14 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         EdgeCtx c;
         load_edge(g, uv, t, toff, e, c);
         Item it;
-        load_item_outlined(g, c, T, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane,
-                           need_k, need_q, it);
+        load_item_outlined(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi),
+                           lane, need_k, need_q, it);
         __syncwarp();
         SharedItem& si = my[lane];
         si.it[0] = it.a.it;
         si.it[1] = it.b.it;
+        si.its[0] = it.a.its;
+        si.its[1] = it.b.its;
         si.sl[0] = it.a.sl;
         si.sl[1] = it.b.sl;
         si.svtx[0] = it.a.svtx;
@@ -522,8 +538,10 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         int32_t o = (int32_t)(rr - sj);
         const int seg = o < si.ca ? 0 : 1;
         if (seg) o -= si.ca;
+        const int16_t* its = si.its[seg];
+        const int32_t xs = its != nullptr ? (int32_t)__ldg(its + o) : kNoSlotInfo;
         const bool hit = set_contains(g, si.svtx[seg], si.sslot[seg], si.sl[seg], si.slen[seg],
-                                      __ldg(si.it[seg] + o));
+                                      __ldg(si.it[seg] + o), xs);
         if (hit) {
           if (seg == 0) {
             ++acc_k;
@@ -756,6 +774,7 @@ DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
     g.tb_count = 0;
     g.hm_slot = nullptr;
     g.hm_bits = nullptr;
+    g.col_hm = nullptr;
   }
   return g;
 }
@@ -864,11 +883,12 @@ int64_t launch_scan_t(CountBufs& b, cudaStream_t stream) {
 // sync.
 int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
                     cudaStream_t stream) {
+  int16_t* T_hm = g.col_hm != nullptr ? b.T_hm : nullptr;
   k_compact_T<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(g, b.uv, b.off, b.toff,
-                                                                          b.K, b.tbits, b.T,
+                                                                          b.K, b.tbits, b.T, T_hm,
                                                                           b.tdeg);
   k_chunk_cost<<<sm_count() * kBlocksPerSm, kThreads, 0, stream>>>(
-      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T, need_k, need_q, tu.task_probes,
+      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T, T_hm, need_k, need_q, tu.task_probes,
       b.chunk_cost, b.task_off, b.q, b.stats);
   exclusive_scan_i64(b.task_off, b.task_off, b.groups, b.tmp1, stream);
   return 5;
@@ -882,6 +902,7 @@ int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& t
                  : tu.quad_blocks_per_sm > kQuadBlocksPerSm ? kQuadBlocksPerSm
                                                             : tu.quad_blocks_per_sm;
   k_quad<<<sms * qb, kThreads, 0, stream>>>(g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T,
+                                            g.col_hm != nullptr ? b.T_hm : nullptr,
                                             b.task_off, b.groups, need_k, need_q,
                                             tu.task_probes, b.k2, b.q);
   return 1;
@@ -991,8 +1012,12 @@ gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs
     GS_CUDA(cudaMemcpyAsync(&b.tsum, b.toff + K, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
     GS_CUDA(cudaStreamSynchronize(stream));
     void* base2 = nullptr;
-    GS_TRY(ws_reserve(ws, 2, Carve::bytes_for<int32_t>(b.tsum), stream, &base2));
-    b.T = (int32_t*)base2;
+    GS_TRY(ws_reserve(ws, 2,
+                      Carve::bytes_for<int32_t>(b.tsum) + Carve::bytes_for<int16_t>(b.tsum),
+                      stream, &base2));
+    Carve c2{(char*)base2, 0};
+    b.T = c2.take<int32_t>(b.tsum);
+    b.T_hm = c2.take<int16_t>(b.tsum);
     timer.stop(2);
     timer.start(3);
     more += launch_cost(g, need_k, need_q, tu, b, stream);

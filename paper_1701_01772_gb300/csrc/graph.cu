@@ -158,6 +158,15 @@ __global__ void k_hub_matrix(const int64_t* __restrict__ row_ptr, const int32_t*
   }
 }
 
+// col_hm[p] = matrix slot of col[p] (-1 if none): stored beside the
+// adjacency so a membership test gets the slot with the element.
+__global__ void k_col_slots(const int32_t* __restrict__ col, int64_t nnz,
+                            const int32_t* __restrict__ slot, int16_t* __restrict__ col_hm) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x)
+    col_hm[p] = (int16_t)__ldg(slot + col[p]);
+}
+
 // Number of table hubs among the neighbours of each vertex.
 __global__ void k_hub_nbr_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const int32_t* __restrict__ slot, int64_t n,
@@ -352,8 +361,13 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     GS_CUDA(cudaMemsetAsync(g->hm_bits, 0, sizeof(uint32_t) * (size_t)(hm_words * n_hm), stream));
     k_hub_matrix<<<grid_for(n_hm * 256, 256, 8), 256, 0, stream>>>(
         g->dev.row_ptr, g->dev.col, g->hm_slot, hubs, n_hm, hm_words, g->hm_bits);
-    GS_CUDA(cudaStreamSynchronize(stream));
     cudaFree(hubs);
+    GS_CUDA(cudaMalloc(&g->col_hm, sizeof(int16_t) * (size_t)(g->dev.nnz > 0 ? g->dev.nnz : 1)));
+    if (g->dev.nnz > 0)
+      k_col_slots<<<grid_for(g->dev.nnz, 256, 8), 256, 0, stream>>>(g->dev.col, g->dev.nnz,
+                                                                    g->hm_slot, g->col_hm);
+    GS_CUDA(cudaStreamSynchronize(stream));
+    g->dev.col_hm = g->col_hm;
     g->dev.hm_slot = g->hm_slot;
     g->dev.hm_bits = g->hm_bits;
     g->dev.hm_words = hm_words;
@@ -498,6 +512,7 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->tb_codeg);
   cudaFree(g->hm_slot);
   cudaFree(g->hm_bits);
+  cudaFree(g->col_hm);
   delete g;
   return GS_OK;
 }
