@@ -78,6 +78,11 @@ __device__ __forceinline__ bool sorted_contains(const int32_t* __restrict__ a, i
   return __ldg(base) == x;
 }
 
+// Bitmap slot of v, or -1 (also when there are no bitmaps).
+__device__ __forceinline__ int32_t bitmap_slot(const DevGraph& g, int32_t v) {
+  return (g.bm_slot != nullptr && v >= 0) ? __ldg(g.bm_slot + v) : -1;
+}
+
 // Hub-pair matrix slot of v, or -1 (also when there is no matrix).
 __device__ __forceinline__ int32_t table_slot(const DevGraph& g, int32_t v) {
   return (g.hm_bits != nullptr && v >= 0) ? __ldg(g.hm_slot + v) : -1;

@@ -233,7 +233,8 @@ struct Seg {
   const int16_t* its;   // matrix slots of the iterated list's entries, or NULL
   const int32_t* sl;    // searched list
   int32_t svtx;         // vertex whose adjacency sl is (bitmap-capable), or -1
-  int32_t sslot;        // table slot of svtx, or -1
+  int32_t sslot;        // matrix slot of svtx, or -1
+  int32_t sbm;          // bitmap slot of svtx, or -1
   int32_t slen;         // length of sl
   int32_t cnt;          // number of tests
 };
@@ -306,6 +307,7 @@ __device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int6
     s.cnt = (int32_t)dob;
   }
   s.sslot = table_slot(g, s.svtx);
+  s.sbm = bitmap_slot(g, s.svtx);
 }
 
 __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
@@ -318,6 +320,7 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   it.a.its = it.b.its = nullptr;
   it.a.svtx = it.b.svtx = -1;
   it.a.sslot = it.b.sslot = -1;
+  it.a.sbm = it.b.sbm = -1;
   it.a.slen = it.b.slen = 0;
   it.qconst = 0;
   it.bsign = 0;
@@ -346,6 +349,7 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
       it.a.sl = g.col + bw;
       it.a.svtx = w;
       it.a.sslot = table_slot(g, w);
+      it.a.sbm = bitmap_slot(g, w);
       it.a.slen = (int32_t)dw;
       it.a.cnt = (int32_t)tg;
     }
@@ -441,6 +445,7 @@ struct SharedItem {
   const int32_t* sl[2];
   int32_t svtx[2];
   int32_t sslot[2];
+  int32_t sbm[2];
   int32_t slen[2];
   int32_t ca;
   int32_t bsign;
@@ -501,6 +506,8 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         si.svtx[1] = it.b.svtx;
         si.sslot[0] = it.a.sslot;
         si.sslot[1] = it.b.sslot;
+        si.sbm[0] = it.a.sbm;
+        si.sbm[1] = it.b.sbm;
         si.slen[0] = it.a.slen;
         si.slen[1] = it.b.slen;
         si.ca = it.a.cnt;
@@ -523,31 +530,72 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     }
     const int64_t lo = (task - __ldg(task_off + gi)) * task_probes;
     const int32_t len = (int32_t)min(ctotal - lo, task_probes);
-    for (int32_t r = lane; r - lane < len; r += 32) {
-      const int64_t rr = lo + r;
-      // item j = last lane whose start <= rr
-      int j = 0;
+    // Two independent tests per lane per iteration (r and r + 32): their
+    // loads are issued together so each warp keeps more requests in flight.
+    for (int32_t r = lane; r - lane < len; r += 64) {
+      int32_t x[2], xs[2], seg[2];
+      const SharedItem* it[2];
+      bool act[2];
 #pragma unroll
-      for (int step = 16; step > 0; step >>= 1) {
-        int64_t s = __shfl_sync(kFull, start, j + step);
-        if (s <= rr) j += step;
-      }
-      const int64_t sj = __shfl_sync(kFull, start, j);
-      if (r < len) {
-        const SharedItem& si = my[j];
+      for (int h = 0; h < 2; ++h) {
+        const int64_t rr = lo + r + 32 * h;
+        int j = 0;  // item = last lane whose start <= rr
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+          int64_t sv = __shfl_sync(kFull, start, j + step);
+          if (sv <= rr) j += step;
+        }
+        const int64_t sj = __shfl_sync(kFull, start, j);
+        act[h] = r + 32 * h < len;
+        it[h] = &my[j];
         int32_t o = (int32_t)(rr - sj);
-        const int seg = o < si.ca ? 0 : 1;
-        if (seg) o -= si.ca;
-        const int16_t* its = si.its[seg];
-        const int32_t xs = its != nullptr ? (int32_t)__ldg(its + o) : kNoSlotInfo;
-        const bool hit = set_contains(g, si.svtx[seg], si.sslot[seg], si.sl[seg], si.slen[seg],
-                                      __ldg(si.it[seg] + o), xs);
+        seg[h] = o < it[h]->ca ? 0 : 1;
+        if (seg[h]) o -= it[h]->ca;
+        x[h] = 0;
+        xs[h] = -1;
+        if (act[h]) {
+          x[h] = __ldg(it[h]->it[seg[h]] + o);
+          const int16_t* its = it[h]->its[seg[h]];
+          xs[h] = its != nullptr ? (int32_t)__ldg(its + o) : kNoSlotInfo;
+        }
+      }
+      // constant-time word for matrix / bitmap answers, issued for both
+      uint32_t word[2], bitpos[2];
+      bool direct[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        direct[h] = false;
+        word[h] = 0;
+        bitpos[h] = 0;
+        if (!act[h]) continue;
+        const int sslot = it[h]->sslot[seg[h]];
+        if (sslot >= 0) {
+          if (xs[h] == kNoSlotInfo) xs[h] = __ldg(g.hm_slot + x[h]);
+          if (xs[h] >= 0) {
+            word[h] = __ldg(g.hm_bits + (int64_t)sslot * g.hm_words + (xs[h] >> 5));
+            bitpos[h] = xs[h] & 31;
+            direct[h] = true;
+            continue;
+          }
+        }
+        const int sbm = it[h]->sbm[seg[h]];
+        if (sbm >= 0) {
+          word[h] = __ldg(g.bm_bits + (int64_t)sbm * g.bm_words + (x[h] >> 5));
+          bitpos[h] = x[h] & 31;
+          direct[h] = true;
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!act[h]) continue;
+        const bool hit = direct[h] ? ((word[h] >> bitpos[h]) & 1u) != 0
+                                   : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
         if (hit) {
-          if (seg == 0) {
+          if (seg[h] == 0) {
             ++acc_k;
             acc_q += need_q ? 2 : 0;
           } else {
-            acc_q += si.bsign;
+            acc_q += it[h]->bsign;
           }
         }
       }
