@@ -88,6 +88,8 @@ int64_t enqueue_batch(gs_batch* b, const Tuning& tu, cudaStream_t stream) {
   n += launch_tri(g, four, tu, c, stream);
   if (four) {
     n += launch_scan_t(c, stream);
+    n += launch_compact(g, c, stream);
+    n += launch_tmask(g, c, stream);
     n += launch_cost(g, need_k, need_q, tu, c, stream);
     n += launch_quad(g, need_k, need_q, tu, c, stream);
   }

@@ -183,8 +183,8 @@ struct Tuning {
 struct gs_workspace {
   int has_tuning;
   gs::Tuning tuning;
-  void* buf[4];
-  size_t cap[4];
+  void* buf[5];
+  size_t cap[5];
   cudaStream_t last_stream;
   int device;
   int timing;
@@ -232,6 +232,11 @@ struct CountBufs {
   int64_t* tmp1 = nullptr;
   int32_t* T = nullptr;
   int16_t* T_hm = nullptr;  // matrix slots of T's entries (NULL without a matrix)
+  // dense clique mode: per-edge mask index (-1 = sparse edge) and the
+  // masks of T's matrix members ([ndense][hm_words])
+  int32_t* mask_idx = nullptr;
+  uint32_t* tmask = nullptr;
+  int64_t ndense = 0;
 };
 
 Tuning default_tuning();
@@ -247,6 +252,8 @@ int64_t launch_front(const gs_graph* gr, const DevGraph& g, const int32_t* pairs
 int64_t launch_tri(const DevGraph& g, bool four, const Tuning& tu, CountBufs& b,
                    cudaStream_t stream);
 int64_t launch_scan_t(CountBufs& b, cudaStream_t stream);
+int64_t launch_compact(const DevGraph& g, CountBufs& b, cudaStream_t stream);
+int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream);
 int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
                     cudaStream_t stream);
 int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,

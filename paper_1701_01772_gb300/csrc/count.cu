@@ -48,6 +48,9 @@ constexpr int kBlocksPerSm = 4;
 #endif
 constexpr int kQuadBlocksPerSm = GS_QUAD_BLOCKS_PER_SM;
 constexpr unsigned kFull = 0xffffffffu;
+// An edge whose T has at least this many hub-matrix members counts the pairs
+// among them with word-parallel AND + popcount over hub-matrix rows.
+constexpr int kDenseMin = 256;
 constexpr unsigned long long kEmpty = ~0ull;
 
 __device__ __forceinline__ int64_t deg_of(const int64_t* __restrict__ row_ptr, int32_t v,
@@ -188,7 +191,9 @@ void launch_tri_unpadded(const DevGraph& g, const int2* uv, const int64_t* off, 
 __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off,
                             const int64_t* __restrict__ toff, int64_t K,
                             const uint32_t* __restrict__ tbits, int32_t* __restrict__ T,
-                            int16_t* __restrict__ T_hm, int64_t* __restrict__ tdeg) {
+                            int16_t* __restrict__ T_hm, int64_t* __restrict__ tdeg,
+                            int32_t* __restrict__ mask_idx,
+                            unsigned long long* __restrict__ dense_counter) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < K; e += warps) {
@@ -197,19 +202,53 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
     int64_t du = deg_of(g.row_ptr, pr.x, &bu);
     int64_t words = (du + 31) >> 5, w0 = off[e] >> 5, pos = toff[e];
     long long dsum = 0;
+    int thm = 0;
     for (int64_t w = 0; w < words; ++w) {
       uint32_t word = __ldg(tbits + w0 + w);
+      bool hm_member = false;
       if ((word >> lane) & 1u) {
         int32_t x = __ldg(g.col + bu + w * 32 + lane);
         const int64_t at = pos + __popc(word & ((1u << lane) - 1u));
         T[at] = x;
-        if (T_hm != nullptr) T_hm[at] = __ldg(g.col_hm + bu + w * 32 + lane);
+        if (T_hm != nullptr) {
+          const int16_t xs = __ldg(g.col_hm + bu + w * 32 + lane);
+          T_hm[at] = xs;
+          hm_member = xs >= 0;
+        }
         dsum += __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
       }
+      thm += __popc(__ballot_sync(kFull, hm_member));
       pos += __popc(word);
     }
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
-    if (lane == 0) tdeg[e] = dsum;
+    if (lane == 0) {
+      tdeg[e] = dsum;
+      if (mask_idx != nullptr)
+        mask_idx[e] = (T_hm != nullptr && thm >= kDenseMin)
+                          ? (int32_t)atomicAdd(dense_counter, 1ull)
+                          : -1;
+    }
+  }
+}
+
+// Masks of T's hub-matrix members for dense edges: bit s of the edge's
+// mask is set iff the member with matrix slot s is in T. One warp per edge.
+__global__ void k_build_tmask(const int64_t* __restrict__ toff, const unsigned long long* __restrict__ t,
+                              const int16_t* __restrict__ T_hm, const int32_t* __restrict__ mask_idx,
+                              int64_t K, int64_t words, uint32_t* __restrict__ tmask) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < K; e += warps) {
+    const int32_t idx = mask_idx[e];
+    if (idx < 0) continue;
+    uint32_t* m = tmask + (int64_t)idx * words;
+    for (int64_t w = lane; w < words; w += 32) m[w] = 0u;
+    __syncwarp();
+    const int64_t b = toff[e], len = (int64_t)t[e];
+    for (int64_t i = lane; i < len; i += 32) {
+      const int32_t s = T_hm[b + i];
+      if (s >= 0) atomicOr(m + (s >> 5), 1u << (s & 31));
+    }
   }
 }
 
@@ -239,8 +278,15 @@ struct Seg {
   int32_t cnt;          // number of tests
 };
 
+// Segment-A modes of an item w in T: 0 = tests (pairs above w), 1 = dense
+// words (w has a matrix slot and the edge is dense: AND of w's matrix row
+// with the edge's T mask, slots above w's), 2 = rest (w has no matrix slot
+// and the edge is dense: x over N(w), counted when x is in T and either
+// has a matrix slot or is above w).
 struct Item {
   Seg a, b;
+  int32_t amode;
+  int32_t rest_w;
   int32_t bsign;        // +1 (w in S_u) or -1 (w in T) per segment-B hit
   int64_t qconst;       // constant q contribution of this item
 };
@@ -250,12 +296,17 @@ struct EdgeCtx {
   int32_t u, v;
   int64_t bu, du, bv, dv;
   int64_t te, toff;
+  const uint32_t* tmask;  // this edge's T mask (dense edges), else NULL
 };
 
 __device__ __forceinline__ void load_edge(const DevGraph& g, const int2* __restrict__ uv,
                                           const unsigned long long* __restrict__ t,
-                                          const int64_t* __restrict__ toff, int64_t e,
+                                          const int64_t* __restrict__ toff,
+                                          const int32_t* __restrict__ mask_idx,
+                                          const uint32_t* __restrict__ tmask, int64_t e,
                                           EdgeCtx& c) {
+  const int32_t mi = mask_idx != nullptr ? mask_idx[e] : -1;
+  c.tmask = mi >= 0 ? tmask + (int64_t)mi * g.hm_words : nullptr;
   int2 pr = uv[e];
   c.e = e;
   c.u = pr.x;
@@ -324,13 +375,36 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   it.a.slen = it.b.slen = 0;
   it.qconst = 0;
   it.bsign = 0;
+  it.amode = 0;
+  it.rest_w = -1;
   if (i >= c.du) return;
   const int32_t w = __ldg(g.col + c.bu + i);
   if (w == c.v) return;
   const bool in_t = (tword >> lane) & 1u;
   int64_t bw;
   const int64_t dw = deg_of(g.row_ptr, w, &bw);
-  if (in_t) {
+  if (in_t && c.tmask != nullptr) {
+    const int32_t sw = table_slot(g, w);
+    if (sw >= 0) {
+      // dense: words of w's matrix row from word sw/32 on, ANDed with the mask
+      const int64_t w0 = sw >> 5;
+      it.amode = 1;
+      it.a.it = reinterpret_cast<const int32_t*>(g.hm_bits + (int64_t)sw * g.hm_words + w0);
+      it.a.sl = reinterpret_cast<const int32_t*>(c.tmask + w0);
+      it.a.sslot = sw & 31;  // bit of w in the first word: only higher bits count
+      it.a.cnt = (int32_t)(g.hm_words - w0);
+    } else {
+      // rest: x over N(w), x in T, and (x has a matrix slot or x > w)
+      it.amode = 2;
+      it.rest_w = w;
+      it.a.it = g.col + bw;
+      it.a.its = g.col_hm + bw;
+      it.a.sl = T + c.toff;
+      it.a.slen = (int32_t)c.te;
+      it.a.cnt = (int32_t)dw;
+    }
+  }
+  if (in_t && c.tmask == nullptr) {
     // segment A: |N(w) above w  cap  T above w|
     const int64_t iw = sorted_index(T + c.toff, c.te, w);
     const int64_t tg = c.te - iw - 1;
@@ -353,6 +427,8 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
       it.a.slen = (int32_t)dw;
       it.a.cnt = (int32_t)tg;
     }
+  }
+  if (in_t) {
     if (need_q) {
       // segment B: -(c(w, u) - 1)
       it.bsign = -1;
@@ -401,7 +477,8 @@ __global__ void __launch_bounds__(kThreads)
     k_chunk_cost(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
                  const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
                  const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
-                 const int16_t* __restrict__ T_hm, int need_k,
+                 const int16_t* __restrict__ T_hm, const int32_t* __restrict__ mask_idx,
+                 const uint32_t* __restrict__ tmask, int need_k,
                  int need_q, int64_t task_probes, int64_t* __restrict__ chunk_cost,
                  int64_t* __restrict__ task_cnt, unsigned long long* __restrict__ q,
                  unsigned long long* __restrict__ stats) {
@@ -416,10 +493,10 @@ __global__ void __launch_bounds__(kThreads)
   if (g0 >= g1) return;
   int64_t e = last_le(off, K, g0 * 32);
   EdgeCtx c;
-  load_edge(g, uv, t, toff, e, c);
+  load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
   for (int64_t gi = g0; gi < g1; ++gi) {
     while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
-    if (e != c.e) load_edge(g, uv, t, toff, e, c);
+    if (e != c.e) load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
     Item it;
     load_item(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k,
               need_q, it);
@@ -443,19 +520,21 @@ struct SharedItem {
   const int32_t* it[2];
   const int16_t* its[2];
   const int32_t* sl[2];
-  int32_t svtx[2];
   int32_t sslot[2];
   int32_t sbm[2];
   int32_t slen[2];
   int32_t ca;
   int32_t bsign;
+  int32_t amode;
+  int32_t rest_w;
 };
 
 __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
            const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
            const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
-           const int16_t* __restrict__ T_hm, const int64_t* __restrict__ task_off,
+           const int16_t* __restrict__ T_hm, const int32_t* __restrict__ mask_idx,
+           const uint32_t* __restrict__ tmask, const int64_t* __restrict__ task_off,
            int64_t groups, int need_k, int need_q, int64_t task_probes,
            unsigned long long* __restrict__ k_out,
            unsigned long long* __restrict__ q) {
@@ -490,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
       int64_t mine;
       {
         EdgeCtx c;
-        load_edge(g, uv, t, toff, e, c);
+        load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
         Item it;
         load_item_outlined(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi),
                            lane, need_k, need_q, it);
@@ -502,8 +581,6 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         si.its[1] = it.b.its;
         si.sl[0] = it.a.sl;
         si.sl[1] = it.b.sl;
-        si.svtx[0] = it.a.svtx;
-        si.svtx[1] = it.b.svtx;
         si.sslot[0] = it.a.sslot;
         si.sslot[1] = it.b.sslot;
         si.sbm[0] = it.a.sbm;
@@ -511,6 +588,8 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         si.slen[0] = it.a.slen;
         si.slen[1] = it.b.slen;
         si.ca = it.a.cnt;
+        si.amode = it.amode;
+        si.rest_w = it.rest_w;
         // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2
         // when q is wanted); segment B adds +-1 to q
         si.bsign = it.bsign;
@@ -533,9 +612,9 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     // Two independent tests per lane per iteration (r and r + 32): their
     // loads are issued together so each warp keeps more requests in flight.
     for (int32_t r = lane; r - lane < len; r += 64) {
-      int32_t x[2], xs[2], seg[2];
+      int32_t x[2], xs[2], seg[2], o[2];
       const SharedItem* it[2];
-      bool act[2];
+      bool act[2], words[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int64_t rr = lo + r + 32 * h;
@@ -548,15 +627,21 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         const int64_t sj = __shfl_sync(kFull, start, j);
         act[h] = r + 32 * h < len;
         it[h] = &my[j];
-        int32_t o = (int32_t)(rr - sj);
-        seg[h] = o < it[h]->ca ? 0 : 1;
-        if (seg[h]) o -= it[h]->ca;
+        o[h] = (int32_t)(rr - sj);
+        seg[h] = o[h] < it[h]->ca ? 0 : 1;
+        if (seg[h]) o[h] -= it[h]->ca;
+        words[h] = act[h] && seg[h] == 0 && it[h]->amode == 1;
         x[h] = 0;
         xs[h] = -1;
         if (act[h]) {
-          x[h] = __ldg(it[h]->it[seg[h]] + o);
-          const int16_t* its = it[h]->its[seg[h]];
-          xs[h] = its != nullptr ? (int32_t)__ldg(its + o) : kNoSlotInfo;
+          // dense items load (row word, mask word); others (element, slot)
+          x[h] = __ldg(it[h]->it[seg[h]] + o[h]);
+          if (words[h]) {
+            xs[h] = __ldg(it[h]->sl[0] + o[h]);
+          } else {
+            const int16_t* its = it[h]->its[seg[h]];
+            xs[h] = its != nullptr ? (int32_t)__ldg(its + o[h]) : kNoSlotInfo;
+          }
         }
       }
       // constant-time word for matrix / bitmap answers, issued for both
@@ -567,7 +652,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         direct[h] = false;
         word[h] = 0;
         bitpos[h] = 0;
-        if (!act[h]) continue;
+        if (!act[h] || words[h]) continue;
         const int sslot = it[h]->sslot[seg[h]];
         if (sslot >= 0) {
           if (xs[h] == kNoSlotInfo) xs[h] = __ldg(g.hm_slot + x[h]);
@@ -588,8 +673,22 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (!act[h]) continue;
-        const bool hit = direct[h] ? ((word[h] >> bitpos[h]) & 1u) != 0
-                                   : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
+        if (words[h]) {
+          // pairs of matrix members in T above w: AND of the row and the mask
+          uint32_t both = (uint32_t)x[h] & (uint32_t)xs[h];
+          if (o[h] == 0) {
+            const int b0 = it[h]->sslot[0];
+            both &= b0 == 31 ? 0u : (~0u << (b0 + 1));
+          }
+          const int cnt = __popc(both);
+          acc_k += cnt;
+          acc_q += need_q ? 2 * cnt : 0;
+          continue;
+        }
+        bool hit = direct[h] ? ((word[h] >> bitpos[h]) & 1u) != 0
+                             : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
+        if (hit && seg[h] == 0 && it[h]->amode == 2)
+          hit = xs[h] >= 0 || x[h] > it[h]->rest_w;
         if (hit) {
           if (seg[h] == 0) {
             ++acc_k;
@@ -835,7 +934,8 @@ size_t count_front_bytes(int64_t K, bool all_edges, bool check_dup, int64_t nseg
          Carve::bytes_for<unsigned long long>(8) +
          (all_edges ? Carve::bytes_for<int32_t>(2 * K) : 0) + Carve::bytes_for<int2>(K) +
          Carve::bytes_for<int64_t>(K + 1) * 2 + Carve::bytes_for<unsigned long long>(K) * 3 +
-         Carve::bytes_for<int64_t>(K) + Carve::bytes_for<int64_t>(scan_tmp_elems(K + 1)) +
+         Carve::bytes_for<int64_t>(K) + Carve::bytes_for<int32_t>(K) +
+         Carve::bytes_for<int64_t>(scan_tmp_elems(K + 1)) +
          (check_dup ? Carve::bytes_for<unsigned long long>(dup_cap) : 0) +
          Carve::bytes_for<u128>((int64_t)fold_blocks * 16) +
          (nseg > 0 ? Carve::bytes_for<unsigned long long>(nseg * 64) +
@@ -862,6 +962,7 @@ void carve_front(void* base, int64_t K, bool all_edges, bool check_dup, int64_t 
   b.k2 = c.take<unsigned long long>(K);
   b.q = c.take<unsigned long long>(K);
   b.tdeg = c.take<int64_t>(K);
+  b.mask_idx = c.take<int32_t>(K);
   b.tmp0 = c.take<int64_t>(scan_tmp_elems(K + 1));
   b.dup = check_dup ? c.take<unsigned long long>(dup_cap) : nullptr;
   b.part = c.take<u128>((int64_t)b.fold_blocks * 16);
@@ -927,19 +1028,33 @@ int64_t launch_scan_t(CountBufs& b, cudaStream_t stream) {
   return 3;
 }
 
-// compact T, chunk costs, task scan. T must hold b.toff[K] entries. No host
-// sync.
+// T lists (and their matrix slots) in order; marks dense edges (mask index
+// from the counter stats[6]). T must hold b.toff[K] entries. No host sync.
+int64_t launch_compact(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
+  int16_t* T_hm = g.col_hm != nullptr ? b.T_hm : nullptr;
+  k_compact_T<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(
+      g, b.uv, b.off, b.toff, b.K, b.tbits, b.T, T_hm, b.tdeg, b.mask_idx, b.stats + 6);
+  return 1;
+}
+
+// T masks of the dense edges (b.ndense of them). No host sync.
+int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
+  if (b.ndense <= 0 || g.col_hm == nullptr) return 0;
+  k_build_tmask<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(
+      b.toff, b.t, b.T_hm, b.mask_idx, b.K, g.hm_words, b.tmask);
+  return 1;
+}
+
+// Chunk costs and the task scan. No host sync.
 int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
                     cudaStream_t stream) {
   int16_t* T_hm = g.col_hm != nullptr ? b.T_hm : nullptr;
-  k_compact_T<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(g, b.uv, b.off, b.toff,
-                                                                          b.K, b.tbits, b.T, T_hm,
-                                                                          b.tdeg);
+  const int32_t* mi = g.col_hm != nullptr ? b.mask_idx : nullptr;
   k_chunk_cost<<<sm_count() * kBlocksPerSm, kThreads, 0, stream>>>(
-      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T, T_hm, need_k, need_q, tu.task_probes,
-      b.chunk_cost, b.task_off, b.q, b.stats);
+      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T, T_hm, mi, b.tmask, need_k, need_q,
+      tu.task_probes, b.chunk_cost, b.task_off, b.q, b.stats);
   exclusive_scan_i64(b.task_off, b.task_off, b.groups, b.tmp1, stream);
-  return 5;
+  return 4;
 }
 
 // The 4-node membership tests (k_quad). No host sync.
@@ -951,6 +1066,7 @@ int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& t
                                                             : tu.quad_blocks_per_sm;
   k_quad<<<sms * qb, kThreads, 0, stream>>>(g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T,
                                             g.col_hm != nullptr ? b.T_hm : nullptr,
+                                            g.col_hm != nullptr ? b.mask_idx : nullptr, b.tmask,
                                             b.task_off, b.groups, need_k, need_q,
                                             tu.task_probes, b.k2, b.q);
   return 1;
@@ -1066,8 +1182,20 @@ gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs
     Carve c2{(char*)base2, 0};
     b.T = c2.take<int32_t>(b.tsum);
     b.T_hm = c2.take<int16_t>(b.tsum);
+    more += launch_compact(g, b, stream);
+    unsigned long long nd = 0;
+    GS_CUDA(cudaMemcpyAsync(&nd, b.stats + 6, sizeof(nd), cudaMemcpyDeviceToHost, stream));
+    GS_CUDA(cudaStreamSynchronize(stream));
+    b.ndense = (int64_t)nd;
+    b.tmask = nullptr;
+    if (b.ndense > 0) {
+      void* base4 = nullptr;
+      GS_TRY(ws_reserve(ws, 4, sizeof(uint32_t) * (size_t)(b.ndense * g.hm_words), stream, &base4));
+      b.tmask = (uint32_t*)base4;
+    }
     timer.stop(2);
     timer.start(3);
+    more += launch_tmask(g, b, stream);
     more += launch_cost(g, need_k, need_q, tu, b, stream);
     timer.stop(3);
     timer.start(4);

@@ -189,7 +189,7 @@ gs_status gs_workspace_create(gs_workspace** out) {
 
 gs_status gs_workspace_destroy(gs_workspace* ws) {
   if (ws == nullptr) return GS_OK;
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 5; ++i)
     if (ws->buf[i]) {
       cudaStreamSynchronize(ws->last_stream);
       cudaFree(ws->buf[i]);
@@ -226,7 +226,7 @@ gs_status gs_workspace_bytes(const gs_workspace* ws, uint64_t* bytes) {
     gs::set_error("gs_workspace_bytes: null argument");
     return GS_EINVAL;
   }
-  *bytes = ws->cap[0] + ws->cap[1] + ws->cap[2] + ws->cap[3];
+  *bytes = ws->cap[0] + ws->cap[1] + ws->cap[2] + ws->cap[3] + ws->cap[4];
   return GS_OK;
 }
 

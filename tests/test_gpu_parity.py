@@ -279,3 +279,39 @@ def test_invalid_csr_is_rejected(defect):
     with pytest.raises(gs.GraphletError) as ei:
         gs.Graph.from_numpy(rp, col)
     assert ei.value.status == code
+
+
+# ------------------------------------------------------------------ dense clique mode
+
+def _core_periphery(n_core=420, p_core=0.9, n_per=4000, per_deg=8, seed=3):
+    """A dense core (every core edge has T with hundreds of hub members) and
+    a sparse periphery of low-degree vertices attached to the core, so T mixes
+    vertices with and without hub-matrix slots."""
+    rng = np.random.default_rng(seed)
+    iu = np.triu_indices(n_core, 1)
+    keep = rng.random(len(iu[0])) < p_core
+    a = list(iu[0][keep])
+    b = list(iu[1][keep])
+    for i in range(n_per):
+        for c in rng.choice(n_core, size=per_deg, replace=False):
+            a.append(n_core + i)
+            b.append(int(c))
+    return synth.from_pairs(n_core + n_per, np.array(a), np.array(b))
+
+
+def test_dense_clique_mode_closed_form():
+    n, edges = brute.family_edges("complete", 300)
+    rp, col = synth.from_pairs(n, np.array([e[0] for e in edges]), np.array([e[1] for e in edges]))
+    g = _graph(rp, col)
+    res = gs.gs_estimate(g.count(None)).as_dict()
+    want = brute.closed_form("complete", 300)
+    for i in ALL:
+        assert res[i]["exact"] == want[i], i
+    g.close()
+
+
+def test_dense_clique_mode_mixed_t_against_oracle():
+    rp, col = _core_periphery()
+    sample = synth.explicit_sample(rp, col, 0.03, seed=9)
+    _full_check(rp, col, sample)
+    _full_check(rp, col, sample, hub_budget=NO_HUBS)
