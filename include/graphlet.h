@@ -122,8 +122,8 @@ const char* gs_version(void);
  * bitmaps of the highest-degree vertices, an adjacency bit matrix among the
  * top 16384 of them, and a co-degree table |N(a) cap N(b)| among the top
  * vertices) in library-owned device memory; hub_budget_bytes bounds that
- * index (0 = default 8 GiB: bitmaps and matrix up to 1/8 each, the table the
- * rest, at most 65535 vertices).
+ * index (0 = default 20 GiB: bitmaps and matrix up to 1/8 each, the table
+ * the rest, at most 65535 vertices).
  * Synchronises `stream`. */
 gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n, int64_t nnz,
                           uint32_t flags, uint64_t hub_budget_bytes, void* stream,

@@ -281,10 +281,10 @@ static gs_status hub_threshold(const gs_graph* g, int64_t cap, int64_t min_deg,
 
 // Builds bitmaps (up to 1/8 of the budget), the hub-pair matrix (up to 1/8,
 // at most kHubMatrixMax vertices) and the co-degree table (the rest) within
-// `budget` bytes (0 = 8 GiB).
+// `budget` bytes (0 = 20 GiB).
 static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stream) {
   const int64_t n = g->dev.n;
-  if (budget == 0) budget = (uint64_t)8 << 30;
+  if (budget == 0) budget = (uint64_t)20 << 30;
   if (n == 0 || g->max_degree < kHubMinDegree) return GS_OK;
   const int64_t words = (n + 31) / 32;
   // bitmaps and the matrix get up to 1/8 of the budget each, the table the rest

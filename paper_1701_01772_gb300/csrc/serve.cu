@@ -106,71 +106,113 @@ struct gs_server {
 
 namespace {
 
+double now_s();
+
+// Marks a finished group's requests done (results are final) and wakes the
+// waiters, so a group does not wait for the rest of its batch.
+void release(gs_server* s, std::vector<Req*>& grp, gs_status st) {
+  const double t = now_s();
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (Req* q : grp) {
+      if (st != GS_OK) q->status = st;
+      q->t_done = t;
+      q->done = 1;
+      s->completed += 1;
+    }
+  }
+  s->cv_done.notify_all();
+}
+
+// Samples and counts one graph's requests of a batch in one pass.
+gs_status process_group(gs_server* s, gs_workspace* ws, cudaStream_t stream, size_t gi,
+                        std::vector<Req*>& grp, int32_t** pair_buf, int64_t* pair_cap,
+                        int64_t** seg_dev, int64_t* seg_cap) {
+  gs_graph* gr = s->graphs[gi];
+  const int64_t nb = (int64_t)grp.size();
+  std::vector<int64_t> seg(nb + 1, 0);
+  uint32_t mask = 0;
+  for (int64_t i = 0; i < nb; ++i) {
+    Req* q = grp[i];
+    mask |= q->r.mask;
+    int64_t k = 0;
+    int32_t* dst = nullptr;  // sample into workspace slot 3, then append
+    GS_TRY(sample_range(gr, ws, q->r.fraction, q->r.seed, 0, gr->m, nullptr, 0, &k, &dst,
+                        stream));
+    if (seg[i] + k > *pair_cap) {
+      int64_t cap = std::max<int64_t>(2 * *pair_cap, seg[i] + k + 1024);
+      int32_t* nbuf = nullptr;
+      GS_CUDA(cudaMalloc(&nbuf, sizeof(int32_t) * 2 * cap));
+      if (*pair_buf != nullptr) {
+        GS_CUDA(cudaMemcpyAsync(nbuf, *pair_buf, sizeof(int32_t) * 2 * seg[i],
+                                cudaMemcpyDeviceToDevice, stream));
+        GS_CUDA(cudaStreamSynchronize(stream));
+        cudaFree(*pair_buf);
+      }
+      *pair_buf = nbuf;
+      *pair_cap = cap;
+    }
+    if (k > 0)
+      GS_CUDA(cudaMemcpyAsync(*pair_buf + 2 * seg[i], dst, sizeof(int32_t) * 2 * k,
+                              cudaMemcpyDeviceToDevice, stream));
+    q->k = k;
+    seg[i + 1] = seg[i] + k;
+  }
+  const int64_t K = seg[nb];
+  if (nb + 1 > *seg_cap) {
+    cudaFree(*seg_dev);
+    GS_CUDA(cudaMalloc(seg_dev, sizeof(int64_t) * (nb + 1)));
+    *seg_cap = nb + 1;
+  }
+  GS_CUDA(cudaMemcpyAsync(*seg_dev, seg.data(), sizeof(int64_t) * (nb + 1),
+                          cudaMemcpyHostToDevice, stream));
+  std::vector<unsigned long long> h((size_t)nb * 32, 0);
+  if (K > 0) {
+    CountBufs b;
+    GS_TRY(count_run(gr, ws, *pair_buf, K, mask, false, nullptr, *seg_dev, nb,
+                     ws->has_tuning ? ws->tuning : default_tuning(), b, stream, "gs_server"));
+    GS_CUDA(cudaMemcpyAsync(h.data(), b.seg_sums, sizeof(unsigned long long) * nb * 32,
+                            cudaMemcpyDeviceToHost, stream));
+  }
+  GS_CUDA(cudaStreamSynchronize(stream));
+  for (int64_t i = 0; i < nb; ++i) {
+    Req* q = grp[i];
+    gs_sums sums;
+    memset(&sums, 0, sizeof(sums));
+    sums.k = q->k;
+    sums.m = gr->m;
+    sums.mask = q->r.mask;
+    store_sums(h.data() + 32 * i, q->r.mask, &sums);
+    q->status = gs_estimate(&sums, q->r.z, &q->res);
+  }
+  return GS_OK;
+}
+
+// Runs a batch graph group by graph group (smallest estimated groups first)
+// and releases each group's results as soon as it is counted. On return
+// `batch` holds the requests that were not released (after an error).
 gs_status run_batch(gs_server* s, gs_workspace* ws, cudaStream_t stream, std::vector<Req*>& batch,
                     int32_t** pair_buf, int64_t* pair_cap, int64_t** seg_dev, int64_t* seg_cap) {
-  // group the batch by graph, keeping arrival order inside a group
   std::vector<std::vector<Req*>> groups(s->graphs.size());
-  for (Req* q : batch) groups[q->r.graph].push_back(q);
-  for (size_t gi = 0; gi < groups.size(); ++gi) {
-    std::vector<Req*>& grp = groups[gi];
-    if (grp.empty()) continue;
-    gs_graph* gr = s->graphs[gi];
-    const int64_t nb = (int64_t)grp.size();
-    std::vector<int64_t> seg(nb + 1, 0);
-    uint32_t mask = 0;
-    for (int64_t i = 0; i < nb; ++i) {
-      Req* q = grp[i];
-      mask |= q->r.mask;
-      int64_t k = 0;
-      int32_t* dst = nullptr;  // sample into workspace slot 3, then append
-      GS_TRY(sample_range(gr, ws, q->r.fraction, q->r.seed, 0, gr->m, nullptr, 0, &k, &dst,
-                          stream));
-      if (seg[i] + k > *pair_cap) {
-        int64_t cap = std::max<int64_t>(2 * *pair_cap, seg[i] + k + 1024);
-        int32_t* nbuf = nullptr;
-        GS_CUDA(cudaMalloc(&nbuf, sizeof(int32_t) * 2 * cap));
-        if (*pair_buf != nullptr) {
-          GS_CUDA(cudaMemcpyAsync(nbuf, *pair_buf, sizeof(int32_t) * 2 * seg[i],
-                                  cudaMemcpyDeviceToDevice, stream));
-          GS_CUDA(cudaStreamSynchronize(stream));
-          cudaFree(*pair_buf);
-        }
-        *pair_buf = nbuf;
-        *pair_cap = cap;
-      }
-      if (k > 0)
-        GS_CUDA(cudaMemcpyAsync(*pair_buf + 2 * seg[i], dst, sizeof(int32_t) * 2 * k,
-                                cudaMemcpyDeviceToDevice, stream));
-      q->k = k;
-      seg[i + 1] = seg[i] + k;
+  std::vector<double> est(s->graphs.size(), 0.0);
+  for (Req* q : batch) {
+    groups[q->r.graph].push_back(q);
+    est[q->r.graph] += (double)q->est_bytes;
+  }
+  batch.clear();
+  std::vector<size_t> order;
+  for (size_t gi = 0; gi < groups.size(); ++gi)
+    if (!groups[gi].empty()) order.push_back(gi);
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return est[a] < est[b]; });
+  for (size_t k = 0; k < order.size(); ++k) {
+    gs_status st = process_group(s, ws, stream, order[k], groups[order[k]], pair_buf, pair_cap,
+                                 seg_dev, seg_cap);
+    if (st != GS_OK) {
+      for (size_t r = k; r < order.size(); ++r)
+        batch.insert(batch.end(), groups[order[r]].begin(), groups[order[r]].end());
+      return st;
     }
-    const int64_t K = seg[nb];
-    if (nb + 1 > *seg_cap) {
-      cudaFree(*seg_dev);
-      GS_CUDA(cudaMalloc(seg_dev, sizeof(int64_t) * (nb + 1)));
-      *seg_cap = nb + 1;
-    }
-    GS_CUDA(cudaMemcpyAsync(*seg_dev, seg.data(), sizeof(int64_t) * (nb + 1),
-                            cudaMemcpyHostToDevice, stream));
-    std::vector<unsigned long long> h((size_t)nb * 32, 0);
-    if (K > 0) {
-      CountBufs b;
-      GS_TRY(count_run(gr, ws, *pair_buf, K, mask, false, nullptr, *seg_dev, nb,
-                       ws->has_tuning ? ws->tuning : default_tuning(), b, stream, "gs_server"));
-      GS_CUDA(cudaMemcpyAsync(h.data(), b.seg_sums, sizeof(unsigned long long) * nb * 32,
-                              cudaMemcpyDeviceToHost, stream));
-    }
-    GS_CUDA(cudaStreamSynchronize(stream));
-    for (int64_t i = 0; i < nb; ++i) {
-      Req* q = grp[i];
-      gs_sums sums;
-      memset(&sums, 0, sizeof(sums));
-      sums.k = q->k;
-      sums.m = gr->m;
-      sums.mask = q->r.mask;
-      store_sums(h.data() + 32 * i, q->r.mask, &sums);
-      q->status = gs_estimate(&sums, q->r.z, &q->res);
-    }
+    release(s, groups[order[k]], GS_OK);
   }
   return GS_OK;
 }
@@ -219,15 +261,11 @@ void lane_main(gs_server* s) {
       q->batch_size = (int64_t)batch.size();
     }
     gs_status st = run_batch(s, ws, stream, batch, &pair_buf, &pair_cap, &seg_dev, &seg_cap);
-    const double t1 = now_s();
+    // requests of groups that did not finish (an error) are completed here;
+    // released requests may already be gone, so only `batch` is touched
+    if (!batch.empty()) release(s, batch, st != GS_OK ? st : GS_ECUDA);
     {
       std::lock_guard<std::mutex> lock(s->mu);
-      for (Req* q : batch) {
-        if (st != GS_OK) q->status = st;
-        q->t_done = t1;
-        q->done = 1;
-        s->completed += 1;
-      }
       if (st != GS_OK && s->first_error == GS_OK) s->first_error = st;
       s->reserved -= est;
       s->in_flight -= 1;
