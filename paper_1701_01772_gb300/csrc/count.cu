@@ -24,17 +24,21 @@
 //            tests one x in N(u) for membership in N(v). Ballots give t and,
 //            for 4-node work, one 32-bit word of "x in T" flags per chunk of
 //            32 positions.
-//   compact  T lists written in order (one warp per edge).
+//   compact  T lists written in order with their hub-matrix slots (one warp
+//            per edge); edges with at least kDenseMin matrix members in T are
+//            marked dense and get a T mask over matrix slots.
 //   cost     per chunk of 32 positions (items w = N(u)[i]): membership-test
 //            count of each item (iterate the shorter list, test in the
 //            longer); constant terms (the -1s, table co-degrees) added
 //            directly.
 //   quad     chunks are cut into tasks of task_probes tests; tasks are split
 //            evenly over all warps; inside a task lanes take consecutive
-//            tests and find their item by a search over the warp's scanned
-//            costs (load-balanced search).
+//            tests (two per lane per iteration) and find their item by a
+//            search over the warp's scanned costs (load-balanced search). In
+//            a dense edge a "test" of a hub member of T is one 32-bit word of
+//            its matrix row ANDed with the T mask.
 //   fold     per edge numerators N_i in 128-bit, block partial sums, one
-//            final fixed-order pass.
+//            final fixed-order pass (or per-segment limb sums, k_fold_seg).
 #include <string.h>
 
 #include "common.cuh"
