@@ -165,6 +165,10 @@ extern "C" gs_status gs_batch_create(const int64_t* d_vtx_off, const int64_t* d_
     b->graph = nullptr;
     return fail(s);
   }
+  // adjacency bit matrices for the member graphs (all of them are small in
+  // the intended use): every membership test becomes one word load
+  s = build_dense_blocks(b->graph, hv.data(), num_graphs, (uint64_t)24 << 30, stream);
+  if (s != GS_OK) return fail(s);
   k_batch_segments<<<grid_for(num_graphs + 1, 256, 4), 256, 0, stream>>>(
       d_vtx_off, b->graph->edge_off, num_graphs, b->seg_off);
   b->edges.resize(num_graphs + 1);

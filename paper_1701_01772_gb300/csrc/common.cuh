@@ -59,6 +59,12 @@ struct DevGraph {
   // own slots (hm_count^2 bits, small enough to stay in L2)
   const int32_t* hm_slot;   // [n] matrix slot of v, -1 if none
   const int16_t* col_hm;    // [nnz] matrix slot of col[p], -1 if none (NULL if no matrix)
+  // adjacency bit matrices of small graphs (one block per graph of at most
+  // kDenseGraphMax vertices; a batch holds one block per member graph):
+  // row of v starts at word dm_row[v] (-1: no block), bit x - dm_first[v]
+  const uint32_t* dm_bits;
+  const int64_t* dm_row;
+  const int32_t* dm_first;
   const uint32_t* hm_bits;  // [hm_count][hm_words]
   int64_t hm_words;         // ceil(hm_count / 32)
   int64_t hm_count;
@@ -92,6 +98,13 @@ __device__ __forceinline__ int32_t table_slot(const DevGraph& g, int32_t v) {
 // bitmap test for bitmap hubs, halving search otherwise.
 __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64_t base_y,
                                              int64_t deg_y, int32_t x, int32_t xs_known = -2) {
+  if (g.dm_row != nullptr) {
+    const int64_t r = __ldg(g.dm_row + y);
+    if (r >= 0) {
+      const int32_t lx = x - __ldg(g.dm_first + y);
+      return (__ldg(g.dm_bits + r + (lx >> 5)) >> (lx & 31)) & 1u;
+    }
+  }
   if (g.hm_bits != nullptr) {
     int32_t ys = __ldg(g.hm_slot + y);
     if (ys >= 0) {
@@ -168,6 +181,9 @@ struct gs_graph {
   int32_t* hm_slot;
   uint32_t* hm_bits;
   int16_t* col_hm;
+  uint32_t* dm_bits;
+  int64_t* dm_row;
+  int32_t* dm_first;
 };
 
 namespace gs {
@@ -194,6 +210,15 @@ struct gs_workspace {
 };
 
 namespace gs {
+// Graphs (or batch members) of at most this many vertices get an adjacency
+// bit matrix (at most 32 MiB each).
+constexpr int64_t kDenseGraphMax = 16384;
+// Builds adjacency bit-matrix blocks for the vertex ranges [first[i],
+// first[i+1]) of at most kDenseGraphMax vertices (ranges = member graphs of a
+// disjoint union; a single range [0, n) for one graph). Skipped silently when
+// the blocks would exceed max_bytes or cannot be allocated.
+gs_status build_dense_blocks(gs_graph* g, const int64_t* h_first, int64_t ranges,
+                             uint64_t max_bytes, cudaStream_t stream);
 // Returns a device buffer of at least `bytes` in slot `slot` of the
 // workspace, growing it (after synchronising the stream it was last used
 // on) when needed. Previously held contents of that slot are lost on growth.

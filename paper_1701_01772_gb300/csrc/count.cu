@@ -343,26 +343,44 @@ __device__ __forceinline__ int64_t sorted_index(const int32_t* __restrict__ a, i
   return lo;
 }
 
+// sslot value marking a searched vertex whose adjacency is a dense bit-matrix
+// row: sl then points at the row and sbm holds the first vertex of the block.
+constexpr int32_t kDenseRow = -3;
+
+// The searched side of a segment: vertex y's adjacency, answered by its
+// dense row, the hub-pair matrix, its bitmap, or a halving search.
+__device__ __forceinline__ void set_search(const DevGraph& g, int32_t y, int64_t by, int64_t dy,
+                                           Seg& s) {
+  s.svtx = y;
+  s.sl = g.col + by;
+  s.slen = (int32_t)dy;
+  if (g.dm_row != nullptr) {
+    const int64_t r = __ldg(g.dm_row + y);
+    if (r >= 0) {
+      s.sslot = kDenseRow;
+      s.sl = reinterpret_cast<const int32_t*>(g.dm_bits + r);
+      s.sbm = __ldg(g.dm_first + y);
+      return;
+    }
+  }
+  s.sslot = table_slot(g, y);
+  s.sbm = bitmap_slot(g, y);
+}
+
 // Segment for c(w, o): iterate the shorter adjacency, test in the longer.
 __device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int64_t bw, int64_t dw,
                                               int32_t o, int64_t bo, int64_t dob, Seg& s) {
   if (dw <= dob) {
     s.it = g.col + bw;
     s.its = g.col_hm != nullptr ? g.col_hm + bw : nullptr;
-    s.sl = g.col + bo;
-    s.svtx = o;
-    s.slen = (int32_t)dob;
     s.cnt = (int32_t)dw;
+    set_search(g, o, bo, dob, s);
   } else {
     s.it = g.col + bo;
     s.its = g.col_hm != nullptr ? g.col_hm + bo : nullptr;
-    s.sl = g.col + bw;
-    s.svtx = w;
-    s.slen = (int32_t)dw;
     s.cnt = (int32_t)dob;
+    set_search(g, w, bw, dw, s);
   }
-  s.sslot = table_slot(g, s.svtx);
-  s.sbm = bitmap_slot(g, s.svtx);
 }
 
 __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
@@ -424,12 +442,8 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
     } else {
       it.a.it = T + c.toff + iw + 1;
       it.a.its = T_hm != nullptr ? T_hm + c.toff + iw + 1 : nullptr;
-      it.a.sl = g.col + bw;
-      it.a.svtx = w;
-      it.a.sslot = table_slot(g, w);
-      it.a.sbm = bitmap_slot(g, w);
-      it.a.slen = (int32_t)dw;
       it.a.cnt = (int32_t)tg;
+      set_search(g, w, bw, dw, it.a);
     }
   }
   if (in_t) {
@@ -658,6 +672,13 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         bitpos[h] = 0;
         if (!act[h] || words[h]) continue;
         const int sslot = it[h]->sslot[seg[h]];
+        if (sslot == kDenseRow) {
+          const int32_t lx = x[h] - it[h]->sbm[seg[h]];
+          word[h] = __ldg(reinterpret_cast<const uint32_t*>(it[h]->sl[seg[h]]) + (lx >> 5));
+          bitpos[h] = lx & 31;
+          direct[h] = true;
+          continue;
+        }
         if (sslot >= 0) {
           if (xs[h] == kNoSlotInfo) xs[h] = __ldg(g.hm_slot + x[h]);
           if (xs[h] >= 0) {

@@ -167,6 +167,23 @@ __global__ void k_col_slots(const int32_t* __restrict__ col, int64_t nnz,
     col_hm[p] = (int16_t)__ldg(slot + col[p]);
 }
 
+// Sets the adjacency bits of rows that have a dense block. One warp per row.
+__global__ void k_dense_rows(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                             int64_t n, const int64_t* __restrict__ dm_row,
+                             const int32_t* __restrict__ dm_first, uint32_t* __restrict__ bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t r = dm_row[v];
+    if (r < 0) continue;
+    const int32_t f = dm_first[v];
+    for (int64_t p = row_ptr[v] + lane; p < row_ptr[v + 1]; p += 32) {
+      const int32_t lx = col[p] - f;
+      atomicOr(bits + r + (lx >> 5), 1u << (lx & 31));
+    }
+  }
+}
+
 // Number of table hubs among the neighbours of each vertex.
 __global__ void k_hub_nbr_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const int32_t* __restrict__ slot, int64_t n,
@@ -414,6 +431,52 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   return GS_OK;
 }
 
+namespace gs {
+gs_status build_dense_blocks(gs_graph* g, const int64_t* h_first, int64_t ranges,
+                             uint64_t max_bytes, cudaStream_t stream) {
+  const int64_t n = g->dev.n;
+  if (n == 0 || ranges <= 0) return GS_OK;
+  std::vector<int64_t> row(n, -1);
+  std::vector<int32_t> first(n, 0);
+  int64_t words_total = 0;
+  for (int64_t i = 0; i < ranges; ++i) {
+    const int64_t f = h_first[i], len = h_first[i + 1] - h_first[i];
+    if (len <= 0 || len > kDenseGraphMax) continue;
+    const int64_t w = (len + 31) / 32;
+    for (int64_t v = 0; v < len; ++v) {
+      row[f + v] = words_total + v * w;
+      first[f + v] = (int32_t)f;
+    }
+    words_total += len * w;
+  }
+  if (words_total == 0 || (uint64_t)words_total * 4 > max_bytes) return GS_OK;
+  if (cudaMalloc(&g->dm_bits, sizeof(uint32_t) * (size_t)words_total) != cudaSuccess ||
+      cudaMalloc(&g->dm_row, sizeof(int64_t) * (size_t)n) != cudaSuccess ||
+      cudaMalloc(&g->dm_first, sizeof(int32_t) * (size_t)n) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(g->dm_bits);
+    cudaFree(g->dm_row);
+    cudaFree(g->dm_first);
+    g->dm_bits = nullptr;
+    g->dm_row = nullptr;
+    g->dm_first = nullptr;
+    return GS_OK;  // the matrices are an accelerator, not a requirement
+  }
+  GS_CUDA(cudaMemsetAsync(g->dm_bits, 0, sizeof(uint32_t) * (size_t)words_total, stream));
+  GS_CUDA(cudaMemcpyAsync(g->dm_row, row.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice,
+                          stream));
+  GS_CUDA(cudaMemcpyAsync(g->dm_first, first.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice,
+                          stream));
+  k_dense_rows<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.col, n,
+                                                             g->dm_row, g->dm_first, g->dm_bits);
+  GS_CUDA(cudaStreamSynchronize(stream));
+  g->dev.dm_bits = g->dm_bits;
+  g->dev.dm_row = g->dm_row;
+  g->dev.dm_first = g->dm_first;
+  return GS_OK;
+}
+}  // namespace gs
+
 extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n,
                                      int64_t nnz, uint32_t flags, uint64_t hub_budget_bytes,
                                      void* stream_, gs_graph** out) {
@@ -497,6 +560,14 @@ extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_
   }
   gs_status hs = build_hub_index(g, hub_budget_bytes, stream);
   if (hs != GS_OK) return fail(hs);
+  if (n <= kDenseGraphMax && hub_budget_bytes != 1) {
+    // a small graph gets its whole adjacency as a bit matrix (Sec. 2.6 notes
+    // adjacency matrices for small graphs); a 1-byte budget turns every
+    // index structure off
+    const int64_t range[2] = {0, n};
+    hs = build_dense_blocks(g, range, 1, (uint64_t)64 << 20, stream);
+    if (hs != GS_OK) return fail(hs);
+  }
   *out = g;
   return GS_OK;
 }
@@ -513,6 +584,9 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->hm_slot);
   cudaFree(g->hm_bits);
   cudaFree(g->col_hm);
+  cudaFree(g->dm_bits);
+  cudaFree(g->dm_row);
+  cudaFree(g->dm_first);
   delete g;
   return GS_OK;
 }
