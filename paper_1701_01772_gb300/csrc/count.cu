@@ -408,13 +408,14 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   if (in_t && c.tmask != nullptr) {
     const int32_t sw = table_slot(g, w);
     if (sw >= 0) {
-      // dense: words of w's matrix row from word sw/32 on, ANDed with the mask
-      const int64_t w0 = sw >> 5;
+      // dense: 128-bit groups of w's matrix row from the group holding bit
+      // sw on, ANDed with the mask; a unit of work is one group
+      const int64_t g0 = sw >> 7;
       it.amode = 1;
-      it.a.it = reinterpret_cast<const int32_t*>(g.hm_bits + (int64_t)sw * g.hm_words + w0);
-      it.a.sl = reinterpret_cast<const int32_t*>(c.tmask + w0);
-      it.a.sslot = sw & 31;  // bit of w in the first word: only higher bits count
-      it.a.cnt = (int32_t)(g.hm_words - w0);
+      it.a.it = reinterpret_cast<const int32_t*>(g.hm_bits + (int64_t)sw * g.hm_words + 4 * g0);
+      it.a.sl = reinterpret_cast<const int32_t*>(c.tmask + 4 * g0);
+      it.a.sslot = sw & 127;  // bit of w in the first group: only higher bits count
+      it.a.cnt = (int32_t)(g.hm_words / 4 - g0);
     } else {
       // rest: x over N(w), x in T, and (x has a matrix slot or x > w)
       it.amode = 2;
@@ -651,15 +652,26 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         words[h] = act[h] && seg[h] == 0 && it[h]->amode == 1;
         x[h] = 0;
         xs[h] = -1;
-        if (act[h]) {
-          // dense items load (row word, mask word); others (element, slot)
-          x[h] = __ldg(it[h]->it[seg[h]] + o[h]);
-          if (words[h]) {
-            xs[h] = __ldg(it[h]->sl[0] + o[h]);
-          } else {
-            const int16_t* its = it[h]->its[seg[h]];
-            xs[h] = its != nullptr ? (int32_t)__ldg(its + o[h]) : kNoSlotInfo;
+        if (words[h]) {
+          // dense: one 128-bit group of the row ANDed with the T mask; the
+          // group holding w's bit keeps only the bits above it
+          const uint4 rw = __ldg(reinterpret_cast<const uint4*>(it[h]->it[0]) + o[h]);
+          const uint4 mk = __ldg(reinterpret_cast<const uint4*>(it[h]->sl[0]) + o[h]);
+          uint32_t wd[4] = {rw.x & mk.x, rw.y & mk.y, rw.z & mk.z, rw.w & mk.w};
+          if (o[h] == 0) {
+            const int b0 = it[h]->sslot[0];
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+              const int lo_bit = 32 * q4;
+              if (b0 >= lo_bit + 31) wd[q4] = 0u;
+              else if (b0 >= lo_bit) wd[q4] &= ~0u << (b0 - lo_bit + 1);
+            }
           }
+          x[h] = __popc(wd[0]) + __popc(wd[1]) + __popc(wd[2]) + __popc(wd[3]);
+        } else if (act[h]) {
+          x[h] = __ldg(it[h]->it[seg[h]] + o[h]);
+          const int16_t* its = it[h]->its[seg[h]];
+          xs[h] = its != nullptr ? (int32_t)__ldg(its + o[h]) : kNoSlotInfo;
         }
       }
       // constant-time word for matrix / bitmap answers, issued for both
@@ -699,15 +711,9 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
       for (int h = 0; h < 2; ++h) {
         if (!act[h]) continue;
         if (words[h]) {
-          // pairs of matrix members in T above w: AND of the row and the mask
-          uint32_t both = (uint32_t)x[h] & (uint32_t)xs[h];
-          if (o[h] == 0) {
-            const int b0 = it[h]->sslot[0];
-            both &= b0 == 31 ? 0u : (~0u << (b0 + 1));
-          }
-          const int cnt = __popc(both);
-          acc_k += cnt;
-          acc_q += need_q ? 2 * cnt : 0;
+          // pairs of matrix members in T above w, counted in the load stage
+          acc_k += x[h];
+          acc_q += need_q ? 2 * x[h] : 0;
           continue;
         }
         bool hit = direct[h] ? ((word[h] >> bitpos[h]) & 1u) != 0

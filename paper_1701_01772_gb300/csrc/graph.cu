@@ -369,7 +369,9 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   if (n_hm > 1) {
     int32_t* hubs = nullptr;
     GS_TRY(assign(d_hm, &g->hm_slot, &hubs, n_hm));
-    const int64_t hm_words = (n_hm + 31) / 32;
+    // rows padded to a multiple of 4 words (128 bits) so that dense clique
+    // counting can read a row and a T mask with aligned 16-byte loads
+    const int64_t hm_words = (n_hm + 127) / 128 * 4;
     cudaError_t he = cudaMalloc(&g->hm_bits, sizeof(uint32_t) * (size_t)(hm_words * n_hm));
     if (he != cudaSuccess) {
       cudaFree(hubs);
