@@ -52,9 +52,15 @@ struct DevGraph {
   int64_t bm_words;         // ceil(n / 32)
   int64_t bm_count;
   // co-degree table |N(x) cap N(y)| for the highest-degree vertices
-  const int32_t* tb_slot;   // [n] table slot of v, -1 if none (NULL if no table)
+  const int32_t* tb_slot;   // [n] table slot of v, -1 if none, <= -2 mid row (NULL if no table)
   const uint32_t* tb_codeg; // [tb_count][tb_count]
   int64_t tb_count;
+  // co-degrees between "mid" vertices (degree below the table's threshold,
+  // tb_slot[a] = -2 - row) and the bg_count "big" table vertices
+  // (bg_slot[b] >= 0): md_codeg[row][bg_slot[b]], 16-bit entries
+  const int32_t* bg_slot;    // [n] column of v, -1 if none (NULL if absent)
+  const uint16_t* md_codeg;  // [md_count][bg_count]
+  int64_t md_count, bg_count;
   // adjacency among the top hm_count vertices as a bit matrix over their
   // own slots (hm_count^2 bits, small enough to stay in L2)
   const int32_t* hm_slot;   // [n] matrix slot of v, -1 if none
@@ -184,6 +190,8 @@ struct gs_graph {
   uint32_t* dm_bits;
   int64_t* dm_row;
   int32_t* dm_first;
+  int32_t* bg_slot;
+  uint16_t* md_codeg;
 };
 
 namespace gs {

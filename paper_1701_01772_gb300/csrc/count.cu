@@ -321,14 +321,23 @@ __device__ __forceinline__ void load_edge(const DevGraph& g, const int2* __restr
   c.toff = toff[e];
 }
 
-// c(a, b) + 1 from the co-degree table when both are table hubs, 0 when the
-// table cannot answer (the +1 marks a present entry).
+// c(a, b) + 1 from the co-degree table when both are table hubs or from the
+// mid x big table when one is a mid vertex and the other a big hub; 0 when
+// neither can answer (the +1 marks a present entry).
 __device__ __forceinline__ uint32_t table_codeg(const DevGraph& g, int32_t a, int32_t b) {
   if (g.tb_slot == nullptr) return 0;
   int32_t sa = __ldg(g.tb_slot + a), sb = __ldg(g.tb_slot + b);
-  if (sa < 0 || sb < 0) return 0;
-  int32_t lo = min(sa, sb), hi = max(sa, sb);
-  return __ldg(g.tb_codeg + (int64_t)lo * g.tb_count + hi) + 1u;
+  if (sa >= 0 && sb >= 0) {
+    int32_t lo = min(sa, sb), hi = max(sa, sb);
+    return __ldg(g.tb_codeg + (int64_t)lo * g.tb_count + hi) + 1u;
+  }
+  if (g.md_codeg != nullptr && (sa < -1 || sb < -1) && (sa >= 0 || sb >= 0)) {
+    // one mid vertex (slot -2 - row), one table vertex that may be big
+    const int32_t row = -2 - min(sa, sb);
+    const int32_t col = __ldg(g.bg_slot + (sa >= 0 ? a : b));
+    if (col >= 0) return (uint32_t)__ldg(g.md_codeg + (int64_t)row * g.bg_count + col) + 1u;
+  }
+  return 0;
 }
 
 // Index of x in the sorted list a[0..len) (x is present).
@@ -953,6 +962,8 @@ DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
     g.hm_slot = nullptr;
     g.hm_bits = nullptr;
     g.col_hm = nullptr;
+    g.bg_slot = nullptr;
+    g.md_codeg = nullptr;
   }
   return g;
 }

@@ -12,6 +12,8 @@ namespace gs {
 
 // Vertices below this degree never get bitmaps, matrix or table rows.
 constexpr int64_t kHubMinDegree = 64;
+// Mid rows of the mid x big co-degree table start at this degree.
+constexpr int64_t kMidMinDegree = 8;
 // The hub-pair bit matrix covers at most this many vertices (2^14 squared
 // bits = 32 MiB, which stays resident in the 129 MB L2).
 constexpr int64_t kHubMatrixMax = 16384;
@@ -95,7 +97,11 @@ __global__ void k_nbr_degsum(const int64_t* __restrict__ row_ptr, const int32_t*
 //   bitmaps  for the top bm_count vertices, a bit per vertex id marking the
 //            neighbours, so "x in N(h)" is one load instead of a search;
 //   table    for the top tb_count vertices, c(a, b) = |N(a) cap N(b)| for
-//            every pair of table hubs (upper triangle a < b by slot).
+//            every pair of table hubs (upper triangle a < b by slot);
+//   mid x big  c(a, b) for the next md_count vertices a by degree (down to
+//            kMidMinDegree) against the top bg_count table vertices b, which
+//            answers most co-degree queries between a sampled edge's
+//            high-degree end and a low-degree neighbour.
 // Slots are assigned in increasing vertex id among vertices whose degree is
 // at least a threshold, so the index is deterministic.
 
@@ -181,6 +187,70 @@ __global__ void k_dense_rows(const int64_t* __restrict__ row_ptr, const int32_t*
       const int32_t lx = col[p] - f;
       atomicOr(bits + r + (lx >> 5), 1u << (lx & 31));
     }
+  }
+}
+
+// Mid x big co-degrees: every vertex x adds 1 to c(w, h) for each mid
+// neighbour w (tb_slot[w] = -2 - row) and big neighbour h (x is a common
+// neighbour of w and h). Entries are 16 bits wide, updated through the 32-bit
+// word that holds them; a co-degree is below the mid vertex's degree
+// (< 65536), so no carry reaches the neighbouring entry. One warp per vertex;
+// x's big neighbours (at most kBigMax) are gathered in shared memory.
+constexpr int kBigMax = 1024;
+__global__ void __launch_bounds__(256) k_mid_big_pairs(const int64_t* __restrict__ row_ptr,
+                                                       const int32_t* __restrict__ col, int64_t n,
+                                                       const int32_t* __restrict__ tb_slot,
+                                                       const int32_t* __restrict__ bg_slot,
+                                                       int64_t bg_count,
+                                                       uint32_t* __restrict__ words) {
+  __shared__ int32_t bigs[8][kBigMax];
+  const int lane = threadIdx.x & 31;
+  int32_t* mine = bigs[threadIdx.x >> 5];
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    const int64_t s = row_ptr[x], e = row_ptr[x + 1];
+    int nb = 0;
+    for (int64_t p0 = s; p0 < e; p0 += 32) {
+      const int64_t p = p0 + lane;
+      const int32_t c = p < e ? __ldg(bg_slot + col[p]) : -1;
+      const unsigned ball = __ballot_sync(0xffffffffu, c >= 0);
+      if (c >= 0) mine[nb + __popc(ball & ((1u << lane) - 1u))] = c;
+      nb += __popc(ball);
+    }
+    __syncwarp();
+    if (nb > 0) {
+      for (int64_t p = s + lane; p < e; p += 32) {
+        const int32_t r = __ldg(tb_slot + col[p]);
+        if (r > -2) continue;
+        const int64_t base = (int64_t)(-2 - r) * bg_count;
+        for (int i = 0; i < nb; ++i) {
+          const int64_t at = base + mine[i];
+          atomicAdd(words + (at >> 1), 1u << (16 * (int)(at & 1)));
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Marks mid vertices (lo <= degree < hi, no table slot) and big vertices
+// (table vertices of degree >= big).
+__global__ void k_flag_mid(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ tb_slot,
+                           int64_t n, int64_t lo, int64_t hi, int64_t* __restrict__ flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = row_ptr[v + 1] - row_ptr[v];
+    flag[v] = d >= lo && d < hi && tb_slot[v] < 0;
+  }
+}
+
+__global__ void k_set_mid_rows(const int64_t* __restrict__ flag_scan,
+                               const int64_t* __restrict__ row_ptr, int64_t n, int64_t lo,
+                               int64_t hi, int32_t* __restrict__ tb_slot) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = row_ptr[v + 1] - row_ptr[v];
+    if (d >= lo && d < hi && tb_slot[v] < 0) tb_slot[v] = (int32_t)(-2 - flag_scan[v]);
   }
 }
 
@@ -430,6 +500,51 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       g->dev.tb_count = n_tb;
     }
   }
+  // ---- mid x big co-degrees: rows for the highest-degree vertices below
+  // the table (degree >= kMidMinDegree), columns for the top kBigMax table
+  // vertices; whatever the budget has left
+  const double used = (double)n_bm * (double)words * 4.0 +
+                      (double)n_hm * (double)g->dev.hm_words * 4.0 +
+                      (double)g->dev.tb_count * (double)g->dev.tb_count * 4.0;
+  const int64_t d_hi = d_tb < 65536 ? d_tb : 65536;
+  if (g->dev.tb_count > 1 && d_hi > kMidMinDegree && (double)budget > used) {
+    int64_t d_bg = 0, n_bg = 0;
+    const int64_t bg_cap = g->dev.tb_count < kBigMax ? g->dev.tb_count : kBigMax;
+    GS_TRY(hub_threshold(g, bg_cap, d_tb, d_cnt, stream, &d_bg, &n_bg));
+    const int64_t md_cap = n_bg > 0 ? (int64_t)(((double)budget - used) / (2.0 * (double)n_bg)) : 0;
+    // lowest degree d_md >= kMidMinDegree with at most md_cap mid vertices
+    int64_t d_md = 0, n_ge = 0;
+    if (md_cap > 0)
+      GS_TRY(hub_threshold(g, md_cap + g->dev.tb_count, kMidMinDegree, d_cnt, stream, &d_md, &n_ge));
+    if (md_cap > 0 && d_md < d_hi) {
+      int32_t* hubs = nullptr;
+      GS_TRY(assign(d_bg, &g->bg_slot, &hubs, n_bg));
+      cudaFree(hubs);
+      k_flag_mid<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->tb_slot, n, d_md,
+                                                          d_hi, flag);
+      GS_TRY(exclusive_scan_i64(flag, flag, n, tmp, stream));
+      int64_t rows = 0;
+      GS_CUDA(cudaMemcpyAsync(&rows, flag + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+      GS_CUDA(cudaStreamSynchronize(stream));
+      if (rows > 0) {
+        const int64_t nwords = (rows * n_bg + 1) / 2;
+        cudaError_t me = cudaMalloc(&g->md_codeg, sizeof(uint32_t) * (size_t)nwords);
+        if (me != cudaSuccess) return cuda_fail(me, "mid x big table", __FILE__, __LINE__);
+        GS_CUDA(cudaMemsetAsync(g->md_codeg, 0, sizeof(uint32_t) * (size_t)nwords, stream));
+        k_set_mid_rows<<<grid_for(n, 256, 8), 256, 0, stream>>>(flag, g->dev.row_ptr, n, d_md,
+                                                                d_hi, g->tb_slot);
+        k_mid_big_pairs<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(
+            g->dev.row_ptr, g->dev.col, n, g->tb_slot, g->bg_slot, n_bg,
+            reinterpret_cast<uint32_t*>(g->md_codeg));
+        cudaError_t e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(e, "mid x big table", __FILE__, __LINE__);
+        g->dev.bg_slot = g->bg_slot;
+        g->dev.md_codeg = g->md_codeg;
+        g->dev.md_count = rows;
+        g->dev.bg_count = n_bg;
+      }
+    }
+  }
   return GS_OK;
 }
 
@@ -589,6 +704,8 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->dm_bits);
   cudaFree(g->dm_row);
   cudaFree(g->dm_first);
+  cudaFree(g->bg_slot);
+  cudaFree(g->md_codeg);
   delete g;
   return GS_OK;
 }
@@ -604,6 +721,18 @@ extern "C" gs_status gs_graph_info(const gs_graph* g, int64_t* n, int64_t* m, in
   if (max_degree) *max_degree = g->max_degree;
   if (bitmap_hubs) *bitmap_hubs = g->dev.bm_count;
   if (table_hubs) *table_hubs = g->dev.tb_count;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_graph_index_info(const gs_graph* g, int64_t* matrix_hubs,
+                                         int64_t* mid_rows, int64_t* big_hubs) {
+  if (g == nullptr) {
+    set_error("gs_graph_index_info: null graph");
+    return GS_EINVAL;
+  }
+  if (matrix_hubs) *matrix_hubs = g->dev.hm_count;
+  if (mid_rows) *mid_rows = g->dev.md_count;
+  if (big_hubs) *big_hubs = g->dev.bg_count;
   return GS_OK;
 }
 

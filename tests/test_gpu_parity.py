@@ -140,7 +140,30 @@ def test_hub_index_is_used_on_power_law_graphs():
     rp, col = synth.chung_lu(20000, 150000, 2.1, 1500.0, seed=77)
     g = _graph(rp, col)
     assert g.info["bitmap_hubs"] > 0 and g.info["table_hubs"] > 1
+    assert g.info["matrix_hubs"] > 1
+    assert g.info["mid_rows"] > 0 and 0 < g.info["big_hubs"] <= g.info["table_hubs"]
     g.close()
+
+
+def test_mid_big_table_cut_by_budget():
+    # a budget that leaves room for only part of the mid x big table: the
+    # rows kept are the highest-degree mid vertices, the rest fall back to
+    # searches, and the counts do not change
+    rp, col = synth.chung_lu(20000, 150000, 2.1, 1500.0, seed=77)
+    g = _graph(rp, col)
+    full = g.info
+    g.close()
+    assert full["mid_rows"] > 0
+    for budget in (1 << 20, 2 << 20, 3 << 20, 4 << 20, 6 << 20, 8 << 20, 12 << 20):
+        g = _graph(rp, col, hub_budget_bytes=budget)
+        info = g.info
+        g.close()
+        if 0 < info["mid_rows"] < full["mid_rows"]:
+            break
+    else:
+        pytest.fail("no budget cut the mid x big table")
+    _full_check(rp, col, synth.upper_pairs(rp, col), hub_budget=budget)
+    _full_check(rp, col, synth.explicit_sample(rp, col, 0.1, seed=4), hub_budget=budget)
 
 
 @pytest.mark.parametrize("mask", [gs.GS_G3, gs.GS_THREE_NODE, gs.GS_G7, gs.GS_G10,
