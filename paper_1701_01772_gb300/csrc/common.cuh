@@ -260,7 +260,7 @@ struct CountBufs {
   unsigned long long* limbs = nullptr;     // [nseg][16][4]
   unsigned long long* seg_sums = nullptr;  // [nseg][16][2]
   uint32_t* tbits = nullptr;
-  int64_t* chunk_cost = nullptr;
+  int32_t* tpre = nullptr;  // per chunk: T entries of its edge in earlier chunks
   int64_t* task_off = nullptr;
   int64_t* tmp1 = nullptr;
   int32_t* T = nullptr;

@@ -47,6 +47,9 @@ namespace gs {
 
 constexpr int kThreads = 256;
 constexpr int kBlocksPerSm = 4;
+// k_chunk_cost: 6 CTAs per SM (at most 40 registers) hide more of its
+// dependent loads than 4 do.
+constexpr int kCostBlocksPerSm = 6;
 #ifndef GS_QUAD_BLOCKS_PER_SM
 #define GS_QUAD_BLOCKS_PER_SM 8
 #endif
@@ -195,7 +198,8 @@ void launch_tri_unpadded(const DevGraph& g, const int2* uv, const int64_t* off, 
 __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off,
                             const int64_t* __restrict__ toff, int64_t K,
                             const uint32_t* __restrict__ tbits, int32_t* __restrict__ T,
-                            int16_t* __restrict__ T_hm, int64_t* __restrict__ tdeg,
+                            int32_t* __restrict__ tpre, int16_t* __restrict__ T_hm,
+                            int64_t* __restrict__ tdeg,
                             int32_t* __restrict__ mask_idx,
                             unsigned long long* __restrict__ dense_counter) {
   const int lane = threadIdx.x & 31;
@@ -209,6 +213,7 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
     int thm = 0;
     for (int64_t w = 0; w < words; ++w) {
       uint32_t word = __ldg(tbits + w0 + w);
+      if (lane == 0) tpre[w0 + w] = (int32_t)(pos - toff[e]);
       bool hm_member = false;
       if ((word >> lane) & 1u) {
         int32_t x = __ldg(g.col + bu + w * 32 + lane);
@@ -340,18 +345,6 @@ __device__ __forceinline__ uint32_t table_codeg(const DevGraph& g, int32_t a, in
   return 0;
 }
 
-// Index of x in the sorted list a[0..len) (x is present).
-__device__ __forceinline__ int64_t sorted_index(const int32_t* __restrict__ a, int64_t len,
-                                                int32_t x) {
-  int64_t lo = 0;
-  while (len > 1) {
-    int64_t half = len >> 1;
-    lo = (__ldg(a + lo + half) <= x) ? lo + half : lo;
-    len -= half;
-  }
-  return lo;
-}
-
 // sslot value marking a searched vertex whose adjacency is a dense bit-matrix
 // row: sl then points at the row and sbm holds the first vertex of the block.
 constexpr int32_t kDenseRow = -3;
@@ -395,8 +388,8 @@ __device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int6
 __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
                                           const int32_t* __restrict__ T,
                                           const int16_t* __restrict__ T_hm, int64_t i,
-                                          uint32_t tword, int lane, bool need_k, bool need_q,
-                                          Item& it) {
+                                          uint32_t tword, int32_t tbase, int lane, bool need_k,
+                                          bool need_q, Item& it) {
   it.a.cnt = it.b.cnt = 0;
   it.a.it = it.a.sl = it.b.it = it.b.sl = g.col;
   it.a.its = it.b.its = nullptr;
@@ -438,7 +431,8 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   }
   if (in_t && c.tmask == nullptr) {
     // segment A: |N(w) above w  cap  T above w|
-    const int64_t iw = sorted_index(T + c.toff, c.te, w);
+    // index of w in T: T entries in earlier chunks plus earlier lanes of this one
+    const int64_t iw = tbase + __popc(tword & ((1u << lane) - 1u));
     const int64_t tg = c.te - iw - 1;
     const int64_t upw = __ldg(g.up_ptr + w);
     const int64_t dup = bw + dw - upw;
@@ -487,9 +481,10 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
 __device__ __noinline__ void load_item_outlined(const DevGraph& g, const EdgeCtx& c,
                                                 const int32_t* __restrict__ T,
                                                 const int16_t* __restrict__ T_hm, int64_t i,
-                                                uint32_t tword, int lane, bool need_k,
+                                                uint32_t tword, int32_t tbase, int lane,
+                                                bool need_k,
                                                 bool need_q, Item& it) {
-  load_item(g, c, T, T_hm, i, tword, lane, need_k, need_q, it);
+  load_item(g, c, T, T_hm, i, tword, tbase, lane, need_k, need_q, it);
 }
 
 template <class T>
@@ -501,14 +496,13 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // Chunk costs: membership tests per chunk and the number of tasks it needs.
 // Also adds the constant part of q. Same warp partition as k_tri.
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
     k_chunk_cost(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
                  const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
-                 const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
-                 const int16_t* __restrict__ T_hm, const int32_t* __restrict__ mask_idx,
-                 const uint32_t* __restrict__ tmask, int need_k,
-                 int need_q, int64_t task_probes, int64_t* __restrict__ chunk_cost,
-                 int64_t* __restrict__ task_cnt, unsigned long long* __restrict__ q,
+                 const uint32_t* __restrict__ tbits, const int32_t* __restrict__ tpre,
+                 const int32_t* __restrict__ T, const int16_t* __restrict__ T_hm,
+                 const int32_t* __restrict__ mask_idx, const uint32_t* __restrict__ tmask,
+                 int need_k, int need_q, int64_t task_probes, int64_t* __restrict__ task_cnt, unsigned long long* __restrict__ q,
                  unsigned long long* __restrict__ stats) {
   unsigned long long tests = 0;
   const int lane = threadIdx.x & 31;
@@ -526,12 +520,11 @@ __global__ void __launch_bounds__(kThreads)
     while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
     if (e != c.e) load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
     Item it;
-    load_item(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), lane, need_k,
-              need_q, it);
+    load_item(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), __ldg(tpre + gi),
+              lane, need_k, need_q, it);
     int64_t cost = warp_sum<int64_t>((int64_t)it.a.cnt + it.b.cnt);
     int64_t qc = warp_sum<int64_t>(it.qconst);
     if (lane == 0) {
-      chunk_cost[gi] = cost;
       task_cnt[gi] = (cost + task_probes - 1) / task_probes;
       if (qc != 0) atomicAdd(q + e, (unsigned long long)qc);
       tests += cost;
@@ -560,9 +553,10 @@ struct SharedItem {
 __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
            const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
-           const uint32_t* __restrict__ tbits, const int32_t* __restrict__ T,
-           const int16_t* __restrict__ T_hm, const int32_t* __restrict__ mask_idx,
-           const uint32_t* __restrict__ tmask, const int64_t* __restrict__ task_off,
+           const uint32_t* __restrict__ tbits, const int32_t* __restrict__ tpre,
+           const int32_t* __restrict__ T, const int16_t* __restrict__ T_hm,
+           const int32_t* __restrict__ mask_idx, const uint32_t* __restrict__ tmask,
+           const int64_t* __restrict__ task_off,
            int64_t groups, int need_k, int need_q, int64_t task_probes,
            unsigned long long* __restrict__ k_out,
            unsigned long long* __restrict__ q) {
@@ -600,7 +594,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
         Item it;
         load_item_outlined(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi),
-                           lane, need_k, need_q, it);
+                           __ldg(tpre + gi), lane, need_k, need_q, it);
         __syncwarp();
         SharedItem& si = my[lane];
         si.it[0] = it.a.it;
@@ -1015,7 +1009,7 @@ void carve_front(void* base, int64_t K, bool all_edges, bool check_dup, int64_t 
 
 size_t count_mid_bytes(int64_t P) {
   const int64_t groups = (P + 31) / 32;
-  return Carve::bytes_for<uint32_t>(groups) + Carve::bytes_for<int64_t>(groups) +
+  return Carve::bytes_for<uint32_t>(groups) + Carve::bytes_for<int32_t>(groups) +
          Carve::bytes_for<int64_t>(groups + 1) +
          Carve::bytes_for<int64_t>(scan_tmp_elems(groups + 1));
 }
@@ -1025,7 +1019,7 @@ void carve_mid(void* base, int64_t P, CountBufs& b) {
   b.P = P;
   b.groups = (P + 31) / 32;
   b.tbits = c.take<uint32_t>(b.groups);
-  b.chunk_cost = c.take<int64_t>(b.groups);
+  b.tpre = c.take<int32_t>(b.groups);
   b.task_off = c.take<int64_t>(b.groups + 1);
   b.tmp1 = c.take<int64_t>(scan_tmp_elems(b.groups + 1));
 }
@@ -1075,7 +1069,7 @@ int64_t launch_scan_t(CountBufs& b, cudaStream_t stream) {
 int64_t launch_compact(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
   int16_t* T_hm = g.col_hm != nullptr ? b.T_hm : nullptr;
   k_compact_T<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(
-      g, b.uv, b.off, b.toff, b.K, b.tbits, b.T, T_hm, b.tdeg, b.mask_idx, b.stats + 6);
+      g, b.uv, b.off, b.toff, b.K, b.tbits, b.T, b.tpre, T_hm, b.tdeg, b.mask_idx, b.stats + 6);
   return 1;
 }
 
@@ -1092,9 +1086,9 @@ int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& t
                     cudaStream_t stream) {
   int16_t* T_hm = g.col_hm != nullptr ? b.T_hm : nullptr;
   const int32_t* mi = g.col_hm != nullptr ? b.mask_idx : nullptr;
-  k_chunk_cost<<<sm_count() * kBlocksPerSm, kThreads, 0, stream>>>(
-      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T, T_hm, mi, b.tmask, need_k, need_q,
-      tu.task_probes, b.chunk_cost, b.task_off, b.q, b.stats);
+  k_chunk_cost<<<sm_count() * kCostBlocksPerSm, kThreads, 0, stream>>>(
+      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.tpre, b.T, T_hm, mi, b.tmask, need_k, need_q,
+      tu.task_probes, b.task_off, b.q, b.stats);
   exclusive_scan_i64(b.task_off, b.task_off, b.groups, b.tmp1, stream);
   return 4;
 }
@@ -1106,7 +1100,8 @@ int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& t
   const int qb = tu.quad_blocks_per_sm < 1 ? 1
                  : tu.quad_blocks_per_sm > kQuadBlocksPerSm ? kQuadBlocksPerSm
                                                             : tu.quad_blocks_per_sm;
-  k_quad<<<sms * qb, kThreads, 0, stream>>>(g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.T,
+  k_quad<<<sms * qb, kThreads, 0, stream>>>(g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.tpre,
+                                            b.T,
                                             g.col_hm != nullptr ? b.T_hm : nullptr,
                                             g.col_hm != nullptr ? b.mask_idx : nullptr, b.tmask,
                                             b.task_off, b.groups, need_k, need_q,
