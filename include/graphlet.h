@@ -121,9 +121,10 @@ const char* gs_version(void);
  * Builds the per-graph index (upper-edge offsets for the sampler, adjacency
  * bitmaps of the highest-degree vertices, an adjacency bit matrix among the
  * top 16384 of them, and a co-degree table |N(a) cap N(b)| among the top
- * vertices, plus a mid x big co-degree table, see gs_graph_index_info) in
- * library-owned device memory; hub_budget_bytes bounds that index (0 =
- * default 20 GiB: bitmaps and matrix up to 1/8 each, the table the rest, at
+ * vertices, plus a mid x big co-degree table and adjacency bucket
+ * directories, see gs_graph_index_info) in library-owned device memory;
+ * hub_budget_bytes bounds that index (0 = default 20 GiB: bitmaps and
+ * matrix up to 1/8 each, directories up to 1/16, the table the rest, at
  * most 65535 vertices, the mid x big table whatever remains).
  * Synchronises `stream`. */
 gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n, int64_t nnz,
@@ -140,13 +141,16 @@ gs_status gs_graph_info(const gs_graph* g, int64_t* n, int64_t* m, int64_t* max_
                         int64_t* bitmap_hubs, int64_t* table_hubs);
 
 /* Host outputs describing the rest of the per-graph index: the number of
- * vertices in the hub-pair bit matrix, and the shape of the mid x big
+ * vertices in the hub-pair bit matrix, the shape of the mid x big
  * co-degree table (16-bit |N(a) cap N(b)| for "mid" vertices a, the
  * highest-degree vertices below the co-degree table's threshold, against
- * "big" vertices b, the top table vertices; 0 rows when it was not built).
- * Any output pointer may be NULL. */
+ * "big" vertices b, the top table vertices; 0 rows when it was not built),
+ * and the number of vertices whose adjacency list has a bucket directory
+ * (offsets of the neighbours by the high bits of their ids, so that a
+ * membership test reads one directory entry and a few neighbours instead of
+ * halving the whole list). Any output pointer may be NULL. */
 gs_status gs_graph_index_info(const gs_graph* g, int64_t* matrix_hubs, int64_t* mid_rows,
-                              int64_t* big_hubs);
+                              int64_t* big_hubs, int64_t* dir_vertices);
 
 /* Library-owned scratch for gs_sample / gs_count. One workspace serves one
  * stream at a time; it grows on demand (cudaMalloc, after synchronising the

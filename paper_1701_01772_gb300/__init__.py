@@ -148,7 +148,7 @@ def lib() -> ctypes.CDLL:
         "gs_graph_create": ([P, P, I64, I64, U32, U64, P, PP], ctypes.c_int32),
         "gs_graph_destroy": ([P], ctypes.c_int32),
         "gs_graph_info": ([P, PI64, PI64, PI64, PI64, PI64], ctypes.c_int32),
-        "gs_graph_index_info": ([P, PI64, PI64, PI64], ctypes.c_int32),
+        "gs_graph_index_info": ([P, PI64, PI64, PI64, PI64], ctypes.c_int32),
         "gs_workspace_create": ([PP], ctypes.c_int32),
         "gs_workspace_destroy": ([P], ctypes.c_int32),
         "gs_workspace_bytes": ([P, ctypes.POINTER(U64)], ctypes.c_int32),
@@ -237,9 +237,10 @@ def gs_graph_info(handle: int) -> dict:
 
 
 def gs_graph_index_info(handle: int) -> dict:
-    vals = [ctypes.c_int64() for _ in range(3)]
+    vals = [ctypes.c_int64() for _ in range(4)]
     _check(lib().gs_graph_index_info(handle, *(ctypes.byref(v) for v in vals)))
-    return dict(zip(("matrix_hubs", "mid_rows", "big_hubs"), (v.value for v in vals)))
+    return dict(zip(("matrix_hubs", "mid_rows", "big_hubs", "dir_vertices"),
+                    (v.value for v in vals)))
 
 
 def gs_workspace_create() -> int:

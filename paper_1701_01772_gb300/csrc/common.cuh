@@ -74,7 +74,28 @@ struct DevGraph {
   const uint32_t* hm_bits;  // [hm_count][hm_words]
   int64_t hm_words;         // ceil(hm_count / 32)
   int64_t hm_count;
+  // bucket directories of the adjacency lists of vertices that have no
+  // bitmap (degree at least a threshold): the neighbours x of v with
+  // x >> s_v == b sit at offsets [D[b], D[b + 1]) of N(v), D = dir +
+  // dir_at[v], s_v = id_bits - dir_log2(deg v)
+  const int64_t* dir_at;    // [n] first directory entry of v, -1 if none (NULL if absent)
+  const uint32_t* dir;
+  int32_t id_bits;          // vertex ids are below 2^id_bits
+  int64_t dir_count;        // vertices with a directory
 };
+
+// log2 of the number of directory buckets of a vertex of degree d >= 2:
+// floor(log2 d) - 1, so a bucket holds 2 to 4 neighbours on average when
+// ids are spread evenly; at most id_bits (one bucket per id).
+__host__ __device__ __forceinline__ int dir_log2(int64_t d, int id_bits) {
+#ifdef __CUDA_ARCH__
+  const int f = 63 - __clzll((long long)d);
+#else
+  const int f = 63 - __builtin_clzll((unsigned long long)d);
+#endif
+  const int kb = f - 1;
+  return kb < 0 ? 0 : (kb > id_bits ? id_bits : kb);
+}
 
 // Membership of x in the sorted list a[0..len): branch-free halving search.
 // Invariant: if x is present it lies in [base, base + len).
@@ -128,34 +149,19 @@ __device__ __forceinline__ bool adj_contains(const DevGraph& g, int32_t y, int64
       return (w >> (x & 31)) & 1u;
     }
   }
+  if (g.dir_at != nullptr) {
+    const int64_t at = __ldg(g.dir_at + y);
+    if (at >= 0) {
+      const uint32_t* d = g.dir + at + (x >> (g.id_bits - dir_log2(deg_y, g.id_bits)));
+      const uint32_t lo = __ldg(d), hi = __ldg(d + 1);
+      return sorted_contains(g.col + base_y + lo, (int64_t)(hi - lo), x);
+    }
+  }
   return sorted_contains(g.col + base_y, deg_y, x);
 }
 
-// Membership of x in a set given either as a vertex's adjacency (vtx >= 0,
-// list = N(vtx)) or as a plain sorted list (vtx < 0). vslot is vtx's matrix
-// slot (-1 if none): when x also has one, the hub-pair bit matrix answers.
-// xs is x's matrix slot when the caller has it (stored beside the list it
-// iterates), or kNoSlotInfo to look it up.
+// Matrix slot value meaning "not known: look it up".
 constexpr int32_t kNoSlotInfo = -2;
-__device__ __forceinline__ bool set_contains(const DevGraph& g, int32_t vtx, int32_t vslot,
-                                             const int32_t* __restrict__ list, int64_t len,
-                                             int32_t x, int32_t xs = kNoSlotInfo) {
-  if (vslot >= 0) {
-    if (xs == kNoSlotInfo) xs = __ldg(g.hm_slot + x);
-    if (xs >= 0) {
-      uint32_t w = __ldg(g.hm_bits + (int64_t)vslot * g.hm_words + (xs >> 5));
-      return (w >> (xs & 31)) & 1u;
-    }
-  }
-  if (vtx >= 0 && g.bm_slot != nullptr) {
-    int32_t s = __ldg(g.bm_slot + vtx);
-    if (s >= 0) {
-      uint32_t w = __ldg(g.bm_bits + (int64_t)s * g.bm_words + (x >> 5));
-      return (w >> (x & 31)) & 1u;
-    }
-  }
-  return sorted_contains(list, len, x);
-}
 
 // ---------------------------------------------------------------- scan
 
@@ -192,6 +198,8 @@ struct gs_graph {
   int32_t* dm_first;
   int32_t* bg_slot;
   uint16_t* md_codeg;
+  int64_t* dir_at;
+  uint32_t* dir;
 };
 
 namespace gs {

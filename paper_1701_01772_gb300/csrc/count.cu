@@ -46,7 +46,6 @@
 namespace gs {
 
 constexpr int kThreads = 256;
-constexpr int kBlocksPerSm = 4;
 // k_chunk_cost: 6 CTAs per SM (at most 40 registers) hide more of its
 // dependent loads than 4 do.
 constexpr int kCostBlocksPerSm = 6;
@@ -282,8 +281,10 @@ struct Seg {
   const int32_t* sl;    // searched list
   int32_t svtx;         // vertex whose adjacency sl is (bitmap-capable), or -1
   int32_t sslot;        // matrix slot of svtx, or -1
-  int32_t sbm;          // bitmap slot of svtx, or -1
-  int32_t slen;         // length of sl
+  int32_t sbm;          // bitmap slot of svtx (>= 0), -2 - s when svtx has a
+                        // bucket directory with shift s, else -1
+  int32_t slen;         // length of sl, or (sbm < -1) the first entry of
+                        // svtx's directory in g.dir
   int32_t cnt;          // number of tests
 };
 
@@ -367,6 +368,13 @@ __device__ __forceinline__ void set_search(const DevGraph& g, int32_t y, int64_t
   }
   s.sslot = table_slot(g, y);
   s.sbm = bitmap_slot(g, y);
+  if (s.sbm < 0 && g.dir_at != nullptr) {
+    const int64_t at = __ldg(g.dir_at + y);
+    if (at >= 0) {
+      s.slen = (int32_t)at;
+      s.sbm = -2 - (g.id_bits - dir_log2(dy, g.id_bits));
+    }
+  }
 }
 
 // Segment for c(w, o): iterate the shorter adjacency, test in the longer.
@@ -677,12 +685,14 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
           xs[h] = its != nullptr ? (int32_t)__ldg(its + o[h]) : kNoSlotInfo;
         }
       }
-      // constant-time word for matrix / bitmap answers, issued for both
+      // constant-time word for matrix / bitmap answers, or the bucket bounds
+      // of a directory, issued for both
       uint32_t word[2], bitpos[2];
-      bool direct[2];
+      bool direct[2], bucket[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         direct[h] = false;
+        bucket[h] = false;
         word[h] = 0;
         bitpos[h] = 0;
         if (!act[h] || words[h]) continue;
@@ -708,6 +718,12 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
           word[h] = __ldg(g.bm_bits + (int64_t)sbm * g.bm_words + (x[h] >> 5));
           bitpos[h] = x[h] & 31;
           direct[h] = true;
+        } else if (sbm < -1) {
+          const uint32_t* d =
+              g.dir + (uint32_t)it[h]->slen[seg[h]] + (uint32_t)(x[h] >> (-2 - sbm));
+          word[h] = __ldg(d);
+          bitpos[h] = __ldg(d + 1);
+          bucket[h] = true;
         }
       }
 #pragma unroll
@@ -719,8 +735,10 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
           acc_q += need_q ? 2 * x[h] : 0;
           continue;
         }
-        bool hit = direct[h] ? ((word[h] >> bitpos[h]) & 1u) != 0
-                             : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
+        bool hit = direct[h]   ? ((word[h] >> bitpos[h]) & 1u) != 0
+                   : bucket[h] ? sorted_contains(it[h]->sl[seg[h]] + word[h],
+                                                 (int64_t)(bitpos[h] - word[h]), x[h])
+                               : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
         if (hit && seg[h] == 0 && it[h]->amode == 2)
           hit = xs[h] >= 0 || x[h] > it[h]->rest_w;
         if (hit) {
@@ -958,6 +976,8 @@ DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
     g.col_hm = nullptr;
     g.bg_slot = nullptr;
     g.md_codeg = nullptr;
+    g.dir_at = nullptr;
+    g.dir = nullptr;
   }
   return g;
 }

@@ -12,6 +12,8 @@ namespace gs {
 
 // Vertices below this degree never get bitmaps, matrix or table rows.
 constexpr int64_t kHubMinDegree = 64;
+// Vertices of at least this degree (and no bitmap) get a bucket directory.
+constexpr int64_t kDirMinDegree = 16;
 // Mid rows of the mid x big co-degree table start at this degree.
 constexpr int64_t kMidMinDegree = 8;
 // The hub-pair bit matrix covers at most this many vertices (2^14 squared
@@ -254,6 +256,80 @@ __global__ void k_set_mid_rows(const int64_t* __restrict__ flag_scan,
   }
 }
 
+// Directory entries of v: 2^dir_log2(d) + 1 when v has degree >= d_min and no
+// bitmap, else 0.
+__device__ __forceinline__ int64_t dir_entries(const int64_t* __restrict__ row_ptr,
+                                               const int32_t* __restrict__ bm_slot, int64_t v,
+                                               int64_t d_min, int id_bits) {
+  const int64_t d = row_ptr[v + 1] - row_ptr[v];
+  if (d < d_min || d < 2) return 0;
+  if (bm_slot != nullptr && bm_slot[v] >= 0) return 0;
+  return ((int64_t)1 << dir_log2(d, id_bits)) + 1;
+}
+
+__global__ void k_dir_entries_total(const int64_t* __restrict__ row_ptr,
+                                    const int32_t* __restrict__ bm_slot, int64_t n, int64_t d_min,
+                                    int id_bits, unsigned long long* total) {
+  unsigned long long c = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    c += (unsigned long long)dir_entries(row_ptr, bm_slot, v, d_min, id_bits);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(total, c);
+}
+
+__global__ void k_dir_sizes(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ bm_slot,
+                            int64_t n, int64_t d_min, int id_bits, int64_t* __restrict__ size) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    size[v] = dir_entries(row_ptr, bm_slot, v, d_min, id_bits);
+}
+
+__global__ void k_dir_at(const int64_t* __restrict__ size_scan, const int64_t* __restrict__ row_ptr,
+                         const int32_t* __restrict__ bm_slot, int64_t n, int64_t d_min, int id_bits,
+                         int64_t* __restrict__ dir_at) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    dir_at[v] = dir_entries(row_ptr, bm_slot, v, d_min, id_bits) > 0 ? size_scan[v] : -1;
+}
+
+// One warp per vertex with a directory: entry b is the offset in N(v) of the
+// first neighbour whose bucket x >> s is at least b (entry 2^k is deg v).
+// Entries b with bucket(N(v)[i-1]) < b <= bucket(N(v)[i]) are written by
+// the lane holding i, so every entry is written exactly once.
+__global__ void k_dir_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           const int64_t* __restrict__ dir_at, int64_t n, int id_bits,
+                           uint32_t* __restrict__ dir) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    const int64_t at = dir_at[v];
+    if (at < 0) continue;
+    const int64_t s = row_ptr[v], d = row_ptr[v + 1] - s;
+    const int kb = dir_log2(d, id_bits);
+    const int sh = id_bits - kb;
+    const int64_t nb = (int64_t)1 << kb;
+    uint32_t* D = dir + at;
+    for (int64_t i = lane; i < d; i += 32) {
+      const int64_t b = col[s + i] >> sh;
+      const int64_t bp = i > 0 ? (int64_t)(col[s + i - 1] >> sh) : -1;
+      for (int64_t bb = bp + 1; bb <= b; ++bb) D[bb] = (uint32_t)i;
+    }
+    const int64_t last = col[s + d - 1] >> sh;
+    for (int64_t bb = last + 1 + lane; bb <= nb; bb += 32) D[bb] = (uint32_t)d;
+  }
+}
+
+__global__ void k_count_dirs(const int64_t* __restrict__ dir_at, int64_t n,
+                             unsigned long long* cnt) {
+  unsigned c = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    c += dir_at[v] >= 0;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, (unsigned long long)c);
+}
+
 // Number of table hubs among the neighbours of each vertex.
 __global__ void k_hub_nbr_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                 const int32_t* __restrict__ slot, int64_t n,
@@ -379,9 +455,6 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   const int64_t bm_cap = (int64_t)(share / ((double)words * 4.0));
   int64_t hm_cap = (int64_t)sqrt(share * 8.0);
   if (hm_cap > kHubMatrixMax) hm_cap = kHubMatrixMax;
-  const double tb_bytes = (double)budget - share - (double)hm_cap * (double)hm_cap / 8.0;
-  int64_t tb_cap = tb_bytes > 0 ? (int64_t)sqrt(tb_bytes / 4.0) : 0;
-  if (tb_cap > 65535) tb_cap = 65535;
   unsigned long long* d_cnt = nullptr;
   int64_t* flag = nullptr;
   int64_t* tmp = nullptr;
@@ -432,6 +505,61 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       g->dev.bm_count = n_bm;
     }
   }
+  // ---- bucket directories for the vertices without bitmaps, highest degree
+  // first, in up to 1/16 of the budget
+  int id_bits = 0;
+  while (((int64_t)1 << id_bits) < n) ++id_bits;
+  g->dev.id_bits = id_bits;
+  double dir_bytes = 0.0;
+  {
+    // entry offsets must fit 31 bits (a membership test carries them as int32)
+    double dir_cap = (double)budget / 16.0;
+    if (dir_cap > 4.0 * (double)INT32_MAX) dir_cap = 4.0 * (double)INT32_MAX;
+    auto entries_ge = [&](int64_t d, int64_t* c) -> gs_status {
+      GS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream));
+      k_dir_entries_total<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->bm_slot, n,
+                                                                   d, id_bits, d_cnt);
+      unsigned long long h = 0;
+      GS_CUDA(cudaMemcpyAsync(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, stream));
+      GS_CUDA(cudaStreamSynchronize(stream));
+      *c = (int64_t)h;
+      return GS_OK;
+    };
+    // lowest threshold >= kDirMinDegree whose directories fit
+    int64_t lo = kDirMinDegree, hi = g->max_degree + 1, c = 0;
+    GS_TRY(entries_ge(lo, &c));
+    if ((double)c * 4.0 > dir_cap) {
+      while (hi - lo > 1) {  // entries(lo) too many, entries(hi) = 0 fits
+        const int64_t mid = lo + (hi - lo) / 2;
+        GS_TRY(entries_ge(mid, &c));
+        if ((double)c * 4.0 <= dir_cap) hi = mid; else lo = mid;
+      }
+      lo = hi;
+      GS_TRY(entries_ge(lo, &c));
+    }
+    if (c > 0) {
+      GS_CUDA(cudaMalloc(&g->dir_at, sizeof(int64_t) * (size_t)n));
+      k_dir_sizes<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->bm_slot, n, lo,
+                                                           id_bits, flag);
+      GS_TRY(exclusive_scan_i64(flag, flag, n, tmp, stream));
+      k_dir_at<<<grid_for(n, 256, 8), 256, 0, stream>>>(flag, g->dev.row_ptr, g->bm_slot, n, lo,
+                                                        id_bits, g->dir_at);
+      cudaError_t de = cudaMalloc(&g->dir, sizeof(uint32_t) * (size_t)c);
+      if (de != cudaSuccess) return cuda_fail(de, "adjacency directories", __FILE__, __LINE__);
+      k_dir_fill<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.col,
+                                                               g->dir_at, n, id_bits, g->dir);
+      GS_CUDA(cudaStreamSynchronize(stream));
+      g->dev.dir_at = g->dir_at;
+      g->dev.dir = g->dir;
+      GS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream));
+      k_count_dirs<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->dir_at, n, d_cnt);
+      unsigned long long cnt = 0;
+      GS_CUDA(cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, stream));
+      GS_CUDA(cudaStreamSynchronize(stream));
+      g->dev.dir_count = (int64_t)cnt;
+      dir_bytes = (double)c * 4.0;
+    }
+  }
   // ---- hub-pair bit matrix over the top vertices (kept small: it must stay
   // in L2 to pay off)
   int64_t d_hm = 0, n_hm = 0;
@@ -463,6 +591,10 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     g->dev.hm_count = n_hm;
   }
   // ---- co-degree table
+  const double tb_bytes =
+      (double)budget - share - (double)hm_cap * (double)hm_cap / 8.0 - dir_bytes;
+  int64_t tb_cap = tb_bytes > 0 ? (int64_t)sqrt(tb_bytes / 4.0) : 0;
+  if (tb_cap > 65535) tb_cap = 65535;
   int64_t d_tb = 0, n_tb = 0;
   if (tb_cap > 1) {
     GS_TRY(hub_threshold(g, tb_cap, kHubMinDegree, d_cnt, stream, &d_tb, &n_tb));
@@ -505,7 +637,7 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   // vertices; whatever the budget has left
   const double used = (double)n_bm * (double)words * 4.0 +
                       (double)n_hm * (double)g->dev.hm_words * 4.0 +
-                      (double)g->dev.tb_count * (double)g->dev.tb_count * 4.0;
+                      (double)g->dev.tb_count * (double)g->dev.tb_count * 4.0 + dir_bytes;
   const int64_t d_hi = d_tb < 65536 ? d_tb : 65536;
   if (g->dev.tb_count > 1 && d_hi > kMidMinDegree && (double)budget > used) {
     int64_t d_bg = 0, n_bg = 0;
@@ -706,6 +838,8 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->dm_first);
   cudaFree(g->bg_slot);
   cudaFree(g->md_codeg);
+  cudaFree(g->dir_at);
+  cudaFree(g->dir);
   delete g;
   return GS_OK;
 }
@@ -725,7 +859,8 @@ extern "C" gs_status gs_graph_info(const gs_graph* g, int64_t* n, int64_t* m, in
 }
 
 extern "C" gs_status gs_graph_index_info(const gs_graph* g, int64_t* matrix_hubs,
-                                         int64_t* mid_rows, int64_t* big_hubs) {
+                                         int64_t* mid_rows, int64_t* big_hubs,
+                                         int64_t* dir_vertices) {
   if (g == nullptr) {
     set_error("gs_graph_index_info: null graph");
     return GS_EINVAL;
@@ -733,6 +868,7 @@ extern "C" gs_status gs_graph_index_info(const gs_graph* g, int64_t* matrix_hubs
   if (matrix_hubs) *matrix_hubs = g->dev.hm_count;
   if (mid_rows) *mid_rows = g->dev.md_count;
   if (big_hubs) *big_hubs = g->dev.bg_count;
+  if (dir_vertices) *dir_vertices = g->dev.dir_count;
   return GS_OK;
 }
 

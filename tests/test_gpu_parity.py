@@ -142,7 +142,15 @@ def test_hub_index_is_used_on_power_law_graphs():
     assert g.info["bitmap_hubs"] > 0 and g.info["table_hubs"] > 1
     assert g.info["matrix_hubs"] > 1
     assert g.info["mid_rows"] > 0 and 0 < g.info["big_hubs"] <= g.info["table_hubs"]
+    assert g.info["dir_vertices"] > 0
     g.close()
+    # a small budget still has directories (the highest degrees first); none at 1 byte
+    few = _graph(rp, col, hub_budget_bytes=3 << 20)
+    assert few.info["dir_vertices"] > 0
+    few.close()
+    none = _graph(rp, col, hub_budget_bytes=NO_HUBS)
+    assert none.info["dir_vertices"] == 0
+    none.close()
 
 
 def test_mid_big_table_cut_by_budget():
