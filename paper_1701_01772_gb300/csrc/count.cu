@@ -545,18 +545,23 @@ __global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
 
 // Item descriptors of the chunk a warp is working on, in shared memory so a
 // lane can read the item its test belongs to.
+// Kept to 60 bytes: eight CTAs of 256 items then take 120 KB of shared
+// memory, which leaves the rest of the SM's 256 KB to the L1 cache that the
+// membership tests depend on. The matrix slots of an iterated list are found
+// beside it (col_hm for adjacency lists, T_hm for T), the rest-mode vertex
+// w sits in sbm[0] (a T search has no bitmap) and amode and the segment-B
+// sign share one word.
 struct SharedItem {
   const int32_t* it[2];
-  const int16_t* its[2];
   const int32_t* sl[2];
-  int32_t sslot[2];
   int32_t sbm[2];
   int32_t slen[2];
+  int16_t sslot[2];
   int32_t ca;
-  int32_t bsign;
-  int32_t amode;
-  int32_t rest_w;
+  int32_t mode;  // amode | (bsign + 1) << 8
 };
+static_assert(sizeof(SharedItem) == 56 || sizeof(SharedItem) == 60 || sizeof(SharedItem) == 64,
+              "SharedItem size");
 
 __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
@@ -607,22 +612,18 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         SharedItem& si = my[lane];
         si.it[0] = it.a.it;
         si.it[1] = it.b.it;
-        si.its[0] = it.a.its;
-        si.its[1] = it.b.its;
         si.sl[0] = it.a.sl;
         si.sl[1] = it.b.sl;
-        si.sslot[0] = it.a.sslot;
-        si.sslot[1] = it.b.sslot;
-        si.sbm[0] = it.a.sbm;
+        si.sslot[0] = (int16_t)it.a.sslot;
+        si.sslot[1] = (int16_t)it.b.sslot;
+        si.sbm[0] = it.amode == 2 ? it.rest_w : it.a.sbm;
         si.sbm[1] = it.b.sbm;
         si.slen[0] = it.a.slen;
         si.slen[1] = it.b.slen;
         si.ca = it.a.cnt;
-        si.amode = it.amode;
-        si.rest_w = it.rest_w;
         // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2
         // when q is wanted); segment B adds +-1 to q
-        si.bsign = it.bsign;
+        si.mode = it.amode | ((it.bsign + 1) << 8);
         mine = (int64_t)it.a.cnt + it.b.cnt;
         __syncwarp();
       }
@@ -660,7 +661,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         o[h] = (int32_t)(rr - sj);
         seg[h] = o[h] < it[h]->ca ? 0 : 1;
         if (seg[h]) o[h] -= it[h]->ca;
-        words[h] = act[h] && seg[h] == 0 && it[h]->amode == 1;
+        words[h] = act[h] && seg[h] == 0 && (it[h]->mode & 0xff) == 1;
         x[h] = 0;
         xs[h] = -1;
         if (words[h]) {
@@ -680,9 +681,14 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
           }
           x[h] = __popc(wd[0]) + __popc(wd[1]) + __popc(wd[2]) + __popc(wd[3]);
         } else if (act[h]) {
-          x[h] = __ldg(it[h]->it[seg[h]] + o[h]);
-          const int16_t* its = it[h]->its[seg[h]];
-          xs[h] = its != nullptr ? (int32_t)__ldg(its + o[h]) : kNoSlotInfo;
+          const int32_t* ip = it[h]->it[seg[h]] + o[h];
+          x[h] = __ldg(ip);
+          xs[h] = kNoSlotInfo;
+          if (T_hm != nullptr) {  // matrix slots stored beside the list
+            const size_t pc = (size_t)(ip - g.col);
+            xs[h] = pc < (size_t)g.nnz ? (int32_t)__ldg(g.col_hm + pc)
+                                       : (int32_t)__ldg(T_hm + (ip - T));
+          }
         }
       }
       // constant-time word for matrix / bitmap answers, or the bucket bounds
@@ -696,6 +702,8 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         word[h] = 0;
         bitpos[h] = 0;
         if (!act[h] || words[h]) continue;
+        // a rest-mode T search (sbm[0] holds w) has no constant-time answer
+        if (seg[h] == 0 && (it[h]->mode & 0xff) == 2) continue;
         const int sslot = it[h]->sslot[seg[h]];
         if (sslot == kDenseRow) {
           const int32_t lx = x[h] - it[h]->sbm[seg[h]];
@@ -739,14 +747,14 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
                    : bucket[h] ? sorted_contains(it[h]->sl[seg[h]] + word[h],
                                                  (int64_t)(bitpos[h] - word[h]), x[h])
                                : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
-        if (hit && seg[h] == 0 && it[h]->amode == 2)
-          hit = xs[h] >= 0 || x[h] > it[h]->rest_w;
+        if (hit && seg[h] == 0 && (it[h]->mode & 0xff) == 2)
+          hit = xs[h] >= 0 || x[h] > it[h]->sbm[0];
         if (hit) {
           if (seg[h] == 0) {
             ++acc_k;
             acc_q += need_q ? 2 : 0;
           } else {
-            acc_q += it[h]->bsign;
+            acc_q += (it[h]->mode >> 8) - 1;
           }
         }
       }
