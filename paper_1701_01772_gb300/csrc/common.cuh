@@ -97,6 +97,41 @@ __host__ __device__ __forceinline__ int dir_log2(int64_t d, int id_bits) {
   return kb < 0 ? 0 : (kb > id_bits ? id_bits : kb);
 }
 
+// Loads with an L2 eviction priority: keep (evict_last) for small, heavily
+// reused structures, once (evict_first) for large randomly read tables.
+__device__ __forceinline__ uint64_t l2_policy_keep() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_once() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_keep(const uint32_t* a) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(l2_policy_keep()));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_keep4(const uint4* a) {
+  uint4 v;
+  asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(a), "l"(l2_policy_keep()));
+  return v;
+}
+__device__ __forceinline__ uint32_t ld_once(const uint32_t* a) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(l2_policy_once()));
+  return v;
+}
+__device__ __forceinline__ uint16_t ld_once16(const uint16_t* a) {
+  uint16_t v;
+  asm("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(l2_policy_once()));
+  return v;
+}
+
 // Membership of x in the sorted list a[0..len): branch-free halving search.
 // Invariant: if x is present it lies in [base, base + len).
 __device__ __forceinline__ bool sorted_contains(const int32_t* __restrict__ a, int64_t len,

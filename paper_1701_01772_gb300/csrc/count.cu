@@ -25,8 +25,10 @@
 //            for 4-node work, one 32-bit word of "x in T" flags per chunk of
 //            32 positions.
 //   compact  T lists written in order with their hub-matrix slots (one warp
-//            per edge); edges with at least kDenseMin matrix members in T are
-//            marked dense and get a T mask over matrix slots.
+//            per edge); edges with at least kDenseMin matrix members in T
+//            whose dense-mode work (row groups plus rest adjacency) is below
+//            their sparse-mode tests are marked dense and get a T mask over
+//            matrix slots.
 //   cost     per chunk of 32 positions (items w = N(u)[i]): membership-test
 //            count of each item (iterate the shorter list, test in the
 //            longer); constant terms (the -1s, table co-degrees) added
@@ -54,9 +56,10 @@ constexpr int kCostBlocksPerSm = 6;
 #endif
 constexpr int kQuadBlocksPerSm = GS_QUAD_BLOCKS_PER_SM;
 constexpr unsigned kFull = 0xffffffffu;
-// An edge whose T has at least this many hub-matrix members counts the pairs
-// among them with word-parallel AND + popcount over hub-matrix rows.
-constexpr int kDenseMin = 256;
+// An edge whose T has at least this many hub-matrix members, and whose
+// dense-mode work is the smaller, counts the pairs among them with
+// word-parallel AND + popcount over hub-matrix rows.
+constexpr int kDenseMin = 64;
 constexpr unsigned long long kEmpty = ~0ull;
 
 __device__ __forceinline__ int64_t deg_of(const int64_t* __restrict__ row_ptr, int32_t v,
@@ -208,7 +211,12 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
     int64_t bu;
     int64_t du = deg_of(g.row_ptr, pr.x, &bu);
     int64_t words = (du + 31) >> 5, w0 = off[e] >> 5, pos = toff[e];
+    const int64_t te = toff[e + 1] - toff[e];
     long long dsum = 0;
+    // segment-A work of this edge in either mode (estimates): sparse = tests
+    // over the shorter of N(w) above w / T above w; dense = row groups of the
+    // matrix members plus the adjacency of the others
+    long long sparse = 0, dense = 0;
     int thm = 0;
     for (int64_t w = 0; w < words; ++w) {
       uint32_t word = __ldg(tbits + w0 + w);
@@ -218,21 +226,30 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
         int32_t x = __ldg(g.col + bu + w * 32 + lane);
         const int64_t at = pos + __popc(word & ((1u << lane) - 1u));
         T[at] = x;
+        const int64_t x_end = __ldg(g.row_ptr + x + 1);
+        const int64_t dx = x_end - __ldg(g.row_ptr + x);
         if (T_hm != nullptr) {
           const int16_t xs = __ldg(g.col_hm + bu + w * 32 + lane);
           T_hm[at] = xs;
           hm_member = xs >= 0;
+          const int64_t tg = te - (at - toff[e]) - 1;
+          sparse += min(dx / 2, tg);  // about half of N(x) lies above x
+          dense += hm_member ? (g.hm_words / 4 - (xs >> 7)) : dx;
         }
-        dsum += __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
+        dsum += dx;
       }
       thm += __popc(__ballot_sync(kFull, hm_member));
       pos += __popc(word);
     }
-    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      dsum += __shfl_xor_sync(kFull, dsum, o);
+      sparse += __shfl_xor_sync(kFull, sparse, o);
+      dense += __shfl_xor_sync(kFull, dense, o);
+    }
     if (lane == 0) {
       tdeg[e] = dsum;
       if (mask_idx != nullptr)
-        mask_idx[e] = (T_hm != nullptr && thm >= kDenseMin)
+        mask_idx[e] = (T_hm != nullptr && thm >= kDenseMin && dense < sparse)
                           ? (int32_t)atomicAdd(dense_counter, 1ull)
                           : -1;
     }
@@ -335,13 +352,13 @@ __device__ __forceinline__ uint32_t table_codeg(const DevGraph& g, int32_t a, in
   int32_t sa = __ldg(g.tb_slot + a), sb = __ldg(g.tb_slot + b);
   if (sa >= 0 && sb >= 0) {
     int32_t lo = min(sa, sb), hi = max(sa, sb);
-    return __ldg(g.tb_codeg + (int64_t)lo * g.tb_count + hi) + 1u;
+    return ld_once(g.tb_codeg + (int64_t)lo * g.tb_count + hi) + 1u;
   }
   if (g.md_codeg != nullptr && (sa < -1 || sb < -1) && (sa >= 0 || sb >= 0)) {
     // one mid vertex (slot -2 - row), one table vertex that may be big
     const int32_t row = -2 - min(sa, sb);
     const int32_t col = __ldg(g.bg_slot + (sa >= 0 ? a : b));
-    if (col >= 0) return (uint32_t)__ldg(g.md_codeg + (int64_t)row * g.bg_count + col) + 1u;
+    if (col >= 0) return (uint32_t)ld_once16(g.md_codeg + (int64_t)row * g.bg_count + col) + 1u;
   }
   return 0;
 }
@@ -545,7 +562,21 @@ __global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
 
 // Item descriptors of the chunk a warp is working on, in shared memory so a
 // lane can read the item its test belongs to.
-// Kept to 60 bytes: eight CTAs of 256 items then take 120 KB of shared
+// Membership of x in a directory bucket p[0..len): short buckets (the usual
+// case: 2 to 4 entries) are compared entry by entry with independent loads.
+__device__ __forceinline__ bool bucket_contains(const int32_t* __restrict__ p, int32_t len,
+                                                int32_t x) {
+  if (len <= 4) {
+    bool f = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < len) f |= __ldg(p + k) == x;
+    return f;
+  }
+  return sorted_contains(p, len, x);
+}
+
+// Kept to 64 bytes: eight CTAs of 256 items then take 128 KB of shared
 // memory, which leaves the rest of the SM's 256 KB to the L1 cache that the
 // membership tests depend on. The matrix slots of an iterated list are found
 // beside it (col_hm for adjacency lists, T_hm for T), the rest-mode vertex
@@ -560,8 +591,7 @@ struct SharedItem {
   int32_t ca;
   int32_t mode;  // amode | (bsign + 1) << 8
 };
-static_assert(sizeof(SharedItem) == 56 || sizeof(SharedItem) == 60 || sizeof(SharedItem) == 64,
-              "SharedItem size");
+static_assert(sizeof(SharedItem) == 64, "SharedItem size");
 
 __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
@@ -574,8 +604,10 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
            unsigned long long* __restrict__ k_out,
            unsigned long long* __restrict__ q) {
   __shared__ SharedItem items[kThreads / 32][32];
+  __shared__ const uint32_t* chunk_mask[kThreads / 32];  // T mask of the chunk's edge
   const int lane = threadIdx.x & 31;
   SharedItem* my = items[threadIdx.x >> 5];
+  const uint32_t** my_mask = chunk_mask + (threadIdx.x >> 5);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t NT = __ldg(task_off + groups);
@@ -624,6 +656,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2
         // when q is wanted); segment B adds +-1 to q
         si.mode = it.amode | ((it.bsign + 1) << 8);
+        if (lane == 0) *my_mask = c.tmask;
         mine = (int64_t)it.a.cnt + it.b.cnt;
         __syncwarp();
       }
@@ -667,7 +700,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         if (words[h]) {
           // dense: one 128-bit group of the row ANDed with the T mask; the
           // group holding w's bit keeps only the bits above it
-          const uint4 rw = __ldg(reinterpret_cast<const uint4*>(it[h]->it[0]) + o[h]);
+          const uint4 rw = ld_keep4(reinterpret_cast<const uint4*>(it[h]->it[0]) + o[h]);
           const uint4 mk = __ldg(reinterpret_cast<const uint4*>(it[h]->sl[0]) + o[h]);
           uint32_t wd[4] = {rw.x & mk.x, rw.y & mk.y, rw.z & mk.z, rw.w & mk.w};
           if (o[h] == 0) {
@@ -702,8 +735,19 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         word[h] = 0;
         bitpos[h] = 0;
         if (!act[h] || words[h]) continue;
-        // a rest-mode T search (sbm[0] holds w) has no constant-time answer
-        if (seg[h] == 0 && (it[h]->mode & 0xff) == 2) continue;
+        if (seg[h] == 0 && (it[h]->mode & 0xff) == 2) {
+          // rest mode (sbm[0] holds w): a matrix member x is in T iff its
+          // bit is set in the edge's T mask; other x count only above w and
+          // are searched in T
+          if (xs[h] >= 0) {
+            word[h] = (*my_mask)[xs[h] >> 5];
+            bitpos[h] = xs[h] & 31;
+            direct[h] = true;
+          } else if (x[h] <= it[h]->sbm[0]) {
+            direct[h] = true;  // word 0: no hit
+          }
+          continue;
+        }
         const int sslot = it[h]->sslot[seg[h]];
         if (sslot == kDenseRow) {
           const int32_t lx = x[h] - it[h]->sbm[seg[h]];
@@ -715,7 +759,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         if (sslot >= 0) {
           if (xs[h] == kNoSlotInfo) xs[h] = __ldg(g.hm_slot + x[h]);
           if (xs[h] >= 0) {
-            word[h] = __ldg(g.hm_bits + (int64_t)sslot * g.hm_words + (xs[h] >> 5));
+            word[h] = ld_keep(g.hm_bits + (int64_t)sslot * g.hm_words + (xs[h] >> 5));
             bitpos[h] = xs[h] & 31;
             direct[h] = true;
             continue;
@@ -744,11 +788,9 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
           continue;
         }
         bool hit = direct[h]   ? ((word[h] >> bitpos[h]) & 1u) != 0
-                   : bucket[h] ? sorted_contains(it[h]->sl[seg[h]] + word[h],
-                                                 (int64_t)(bitpos[h] - word[h]), x[h])
+                   : bucket[h] ? bucket_contains(it[h]->sl[seg[h]] + word[h],
+                                                 (int32_t)(bitpos[h] - word[h]), x[h])
                                : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
-        if (hit && seg[h] == 0 && (it[h]->mode & 0xff) == 2)
-          hit = xs[h] >= 0 || x[h] > it[h]->sbm[0];
         if (hit) {
           if (seg[h] == 0) {
             ++acc_k;
