@@ -501,17 +501,6 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   (void)need_k;
 }
 
-// Out-of-line copy for k_quad: the item set-up runs once per chunk and its
-// temporaries would otherwise raise the register count of the test loop.
-__device__ __noinline__ void load_item_outlined(const DevGraph& g, const EdgeCtx& c,
-                                                const int32_t* __restrict__ T,
-                                                const int16_t* __restrict__ T_hm, int64_t i,
-                                                uint32_t tword, int32_t tbase, int lane,
-                                                bool need_k,
-                                                bool need_q, Item& it) {
-  load_item(g, c, T, T_hm, i, tword, tbase, lane, need_k, need_q, it);
-}
-
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -593,8 +582,44 @@ struct SharedItem {
 };
 static_assert(sizeof(SharedItem) == 64, "SharedItem size");
 
+// Item set-up of k_quad, out of line: it runs once per chunk and its
+// temporaries would otherwise raise the register count of the test loop.
+// Writes the lane's descriptor straight to shared memory (no Item or edge
+// context passes through local memory) and returns the item's test count.
+__device__ __noinline__ int64_t setup_item(const DevGraph& g, const int2* __restrict__ uv,
+                                           const unsigned long long* __restrict__ t,
+                                           const int64_t* __restrict__ toff,
+                                           const int32_t* __restrict__ mask_idx,
+                                           const uint32_t* __restrict__ tmask, int64_t e,
+                                           const int32_t* __restrict__ T,
+                                           const int16_t* __restrict__ T_hm, int64_t i,
+                                           uint32_t tword, int32_t tbase, int lane, bool need_k,
+                                           bool need_q, SharedItem* si,
+                                           const uint32_t** chunk_mask) {
+  EdgeCtx c;
+  load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
+  Item it;
+  load_item(g, c, T, T_hm, i, tword, tbase, lane, need_k, need_q, it);
+  si->it[0] = it.a.it;
+  si->it[1] = it.b.it;
+  si->sl[0] = it.a.sl;
+  si->sl[1] = it.b.sl;
+  si->sslot[0] = (int16_t)it.a.sslot;
+  si->sslot[1] = (int16_t)it.b.sslot;
+  si->sbm[0] = it.amode == 2 ? it.rest_w : it.a.sbm;
+  si->sbm[1] = it.b.sbm;
+  si->slen[0] = it.a.slen;
+  si->slen[1] = it.b.slen;
+  si->ca = it.a.cnt;
+  // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2 when q
+  // is wanted); segment B adds +-1 to q
+  si->mode = it.amode | ((it.bsign + 1) << 8);
+  if (lane == 0) *chunk_mask = c.tmask;
+  return (int64_t)it.a.cnt + it.b.cnt;
+}
+
 __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
-    k_quad(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
+    k_quad(const __grid_constant__ DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
            const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
            const uint32_t* __restrict__ tbits, const int32_t* __restrict__ tpre,
            const int32_t* __restrict__ T, const int16_t* __restrict__ T_hm,
@@ -633,33 +658,11 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
       acc_k = 0;
       acc_q = 0;
       while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
-      int64_t mine;
-      {
-        EdgeCtx c;
-        load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
-        Item it;
-        load_item_outlined(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi),
-                           __ldg(tpre + gi), lane, need_k, need_q, it);
-        __syncwarp();
-        SharedItem& si = my[lane];
-        si.it[0] = it.a.it;
-        si.it[1] = it.b.it;
-        si.sl[0] = it.a.sl;
-        si.sl[1] = it.b.sl;
-        si.sslot[0] = (int16_t)it.a.sslot;
-        si.sslot[1] = (int16_t)it.b.sslot;
-        si.sbm[0] = it.amode == 2 ? it.rest_w : it.a.sbm;
-        si.sbm[1] = it.b.sbm;
-        si.slen[0] = it.a.slen;
-        si.slen[1] = it.b.slen;
-        si.ca = it.a.cnt;
-        // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2
-        // when q is wanted); segment B adds +-1 to q
-        si.mode = it.amode | ((it.bsign + 1) << 8);
-        if (lane == 0) *my_mask = c.tmask;
-        mine = (int64_t)it.a.cnt + it.b.cnt;
-        __syncwarp();
-      }
+      __syncwarp();
+      const int64_t mine =
+          setup_item(g, uv, t, toff, mask_idx, tmask, e, T, T_hm, gi * 32 + lane - __ldg(off + e),
+                     __ldg(tbits + gi), __ldg(tpre + gi), lane, need_k, need_q, my + lane, my_mask);
+      __syncwarp();
       int64_t incl = mine;
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
