@@ -211,12 +211,7 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
     int64_t bu;
     int64_t du = deg_of(g.row_ptr, pr.x, &bu);
     int64_t words = (du + 31) >> 5, w0 = off[e] >> 5, pos = toff[e];
-    const int64_t te = toff[e + 1] - toff[e];
     long long dsum = 0;
-    // segment-A work of this edge in either mode (estimates): sparse = tests
-    // over the shorter of N(w) above w / T above w; dense = row groups of the
-    // matrix members plus the adjacency of the others
-    long long sparse = 0, dense = 0;
     int thm = 0;
     for (int64_t w = 0; w < words; ++w) {
       uint32_t word = __ldg(tbits + w0 + w);
@@ -226,32 +221,42 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
         int32_t x = __ldg(g.col + bu + w * 32 + lane);
         const int64_t at = pos + __popc(word & ((1u << lane) - 1u));
         T[at] = x;
-        const int64_t x_end = __ldg(g.row_ptr + x + 1);
-        const int64_t dx = x_end - __ldg(g.row_ptr + x);
         if (T_hm != nullptr) {
           const int16_t xs = __ldg(g.col_hm + bu + w * 32 + lane);
           T_hm[at] = xs;
           hm_member = xs >= 0;
-          const int64_t tg = te - (at - toff[e]) - 1;
-          sparse += min(dx / 2, tg);  // about half of N(x) lies above x
-          dense += hm_member ? (g.hm_words / 4 - (xs >> 7)) : dx;
         }
-        dsum += dx;
+        dsum += __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
       }
       thm += __popc(__ballot_sync(kFull, hm_member));
       pos += __popc(word);
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      dsum += __shfl_xor_sync(kFull, dsum, o);
-      sparse += __shfl_xor_sync(kFull, sparse, o);
-      dense += __shfl_xor_sync(kFull, dense, o);
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
+    bool dense_mode = false;
+    if (T_hm != nullptr && thm >= kDenseMin) {
+      // segment-A work of this edge in either mode (estimates): sparse =
+      // tests over the shorter of N(w) above w / T above w; dense = row
+      // groups of the matrix members plus the adjacency of the others
+      __syncwarp();  // this warp's T entries are visible to all its lanes
+      const int64_t t0 = toff[e], te = pos - t0;
+      long long sparse = 0, dense = 0;
+      for (int64_t j = lane; j < te; j += 32) {
+        const int32_t x = T[t0 + j];
+        const int16_t xs = T_hm[t0 + j];
+        const int64_t dx = __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
+        sparse += min(dx / 2, te - j - 1);  // about half of N(x) lies above x
+        dense += xs >= 0 ? (g.hm_words / 4 - (xs >> 7)) : dx;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sparse += __shfl_xor_sync(kFull, sparse, o);
+        dense += __shfl_xor_sync(kFull, dense, o);
+      }
+      dense_mode = dense < sparse;
     }
     if (lane == 0) {
       tdeg[e] = dsum;
       if (mask_idx != nullptr)
-        mask_idx[e] = (T_hm != nullptr && thm >= kDenseMin && dense < sparse)
-                          ? (int32_t)atomicAdd(dense_counter, 1ull)
-                          : -1;
+        mask_idx[e] = dense_mode ? (int32_t)atomicAdd(dense_counter, 1ull) : -1;
     }
   }
 }
@@ -676,6 +681,10 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     }
     const int64_t lo = (task - __ldg(task_off + gi)) * task_probes;
     const int32_t len = (int32_t)min(ctotal - lo, task_probes);
+    // item starts relative to the task's first test, in 32 bits: clamping
+    // keeps their order and never touches the item that holds a test of
+    // this task (it starts less than one item's tests before lo)
+    const int32_t srel = (int32_t)max(min(start - lo, task_probes), (int64_t)INT32_MIN + 1);
     // Two independent tests per lane per iteration (r and r + 32): their
     // loads are issued together so each warp keeps more requests in flight.
     for (int32_t r = lane; r - lane < len; r += 64) {
@@ -684,17 +693,17 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
       bool act[2], words[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int64_t rr = lo + r + 32 * h;
+        const int32_t rr = r + 32 * h;  // test index within the task
         int j = 0;  // item = last lane whose start <= rr
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
-          int64_t sv = __shfl_sync(kFull, start, j + step);
+          const int32_t sv = __shfl_sync(kFull, srel, j + step);
           if (sv <= rr) j += step;
         }
-        const int64_t sj = __shfl_sync(kFull, start, j);
-        act[h] = r + 32 * h < len;
+        const int32_t sj = __shfl_sync(kFull, srel, j);
+        act[h] = rr < len;
         it[h] = &my[j];
-        o[h] = (int32_t)(rr - sj);
+        o[h] = rr - sj;
         seg[h] = o[h] < it[h]->ca ? 0 : 1;
         if (seg[h]) o[h] -= it[h]->ca;
         words[h] = act[h] && seg[h] == 0 && (it[h]->mode & 0xff) == 1;
