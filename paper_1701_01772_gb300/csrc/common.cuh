@@ -304,6 +304,7 @@ struct CountBufs {
   unsigned long long* seg_sums = nullptr;  // [nseg][16][2]
   uint32_t* tbits = nullptr;
   int32_t* tpre = nullptr;  // per chunk: T entries of its edge in earlier chunks
+  uint32_t* cbits = nullptr;  // per chunk: lanes with tests, lanes answered by a table
   int64_t* task_off = nullptr;
   int64_t* tmp1 = nullptr;
   int32_t* T = nullptr;

@@ -320,6 +320,7 @@ struct Item {
   int32_t amode;
   int32_t rest_w;
   int32_t bsign;        // +1 (w in S_u) or -1 (w in T) per segment-B hit
+  bool tabled;          // a co-degree table answered segment B
   int64_t qconst;       // constant q contribution of this item
 };
 
@@ -367,6 +368,14 @@ __device__ __forceinline__ uint32_t table_codeg(const DevGraph& g, int32_t a, in
   }
   return 0;
 }
+
+// What the cost pass learnt about an item, for the 4-node pass (hint < 0:
+// nothing; compute everything): it has tests, and a co-degree table
+// answered its segment B (so the 4-node pass needs neither the table nor
+// the item when it has no tests). The constant q terms are added by the cost
+// pass alone.
+constexpr int kHintLive = 1;
+constexpr int kHintTabled = 2;
 
 // sslot value marking a searched vertex whose adjacency is a dense bit-matrix
 // row: sl then points at the row and sbm holds the first vertex of the block.
@@ -419,8 +428,9 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
                                           const int32_t* __restrict__ T,
                                           const int16_t* __restrict__ T_hm, int64_t i,
                                           uint32_t tword, int32_t tbase, int lane, bool need_k,
-                                          bool need_q, Item& it) {
+                                          bool need_q, int hint, Item& it) {
   it.a.cnt = it.b.cnt = 0;
+  it.tabled = false;
   it.a.it = it.a.sl = it.b.it = it.b.sl = g.col;
   it.a.its = it.b.its = nullptr;
   it.a.svtx = it.b.svtx = -1;
@@ -432,6 +442,7 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   it.amode = 0;
   it.rest_w = -1;
   if (i >= c.du) return;
+  if (hint >= 0 && !(hint & kHintLive)) return;  // no tests (known from the cost pass)
   const int32_t w = __ldg(g.col + c.bu + i);
   if (w == c.v) return;
   const bool in_t = (tword >> lane) & 1u;
@@ -484,7 +495,8 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
     if (need_q) {
       // segment B: -(c(w, u) - 1)
       it.bsign = -1;
-      uint32_t tc = table_codeg(g, w, c.u);
+      const uint32_t tc = hint >= 0 ? (hint & kHintTabled ? 1u : 0u) : table_codeg(g, w, c.u);
+      it.tabled = tc != 0;
       if (tc != 0) {
         it.qconst = 1 - (int64_t)(tc - 1u);
       } else {
@@ -495,7 +507,8 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   } else if (need_q) {
     // segment B: c(w, v) - 1
     it.bsign = 1;
-    uint32_t tc = table_codeg(g, w, c.v);
+    const uint32_t tc = hint >= 0 ? (hint & kHintTabled ? 1u : 0u) : table_codeg(g, w, c.v);
+    it.tabled = tc != 0;
     if (tc != 0) {
       it.qconst = (int64_t)(tc - 1u) - 1;
     } else {
@@ -521,7 +534,8 @@ __global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
                  const uint32_t* __restrict__ tbits, const int32_t* __restrict__ tpre,
                  const int32_t* __restrict__ T, const int16_t* __restrict__ T_hm,
                  const int32_t* __restrict__ mask_idx, const uint32_t* __restrict__ tmask,
-                 int need_k, int need_q, int64_t task_probes, int64_t* __restrict__ task_cnt, unsigned long long* __restrict__ q,
+                 int need_k, int need_q, int64_t task_probes, int64_t* __restrict__ task_cnt,
+                 uint32_t* __restrict__ cbits, unsigned long long* __restrict__ q,
                  unsigned long long* __restrict__ stats) {
   unsigned long long tests = 0;
   const int lane = threadIdx.x & 31;
@@ -540,7 +554,10 @@ __global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
     if (e != c.e) load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
     Item it;
     load_item(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), __ldg(tpre + gi),
-              lane, need_k, need_q, it);
+              lane, need_k, need_q, -1, it);
+    const unsigned live = __ballot_sync(kFull, it.a.cnt + it.b.cnt > 0);
+    const unsigned tabled = __ballot_sync(kFull, it.tabled);
+    if (lane == 0) reinterpret_cast<uint2*>(cbits)[gi] = make_uint2(live, tabled);
     int64_t cost = warp_sum<int64_t>((int64_t)it.a.cnt + it.b.cnt);
     int64_t qc = warp_sum<int64_t>(it.qconst);
     if (lane == 0) {
@@ -599,12 +616,12 @@ __device__ __noinline__ int64_t setup_item(const DevGraph& g, const int2* __rest
                                            const int32_t* __restrict__ T,
                                            const int16_t* __restrict__ T_hm, int64_t i,
                                            uint32_t tword, int32_t tbase, int lane, bool need_k,
-                                           bool need_q, SharedItem* si,
+                                           bool need_q, int hint, SharedItem* si,
                                            const uint32_t** chunk_mask) {
   EdgeCtx c;
   load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
   Item it;
-  load_item(g, c, T, T_hm, i, tword, tbase, lane, need_k, need_q, it);
+  load_item(g, c, T, T_hm, i, tword, tbase, lane, need_k, need_q, hint, it);
   si->it[0] = it.a.it;
   si->it[1] = it.b.it;
   si->sl[0] = it.a.sl;
@@ -627,6 +644,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     k_quad(const __grid_constant__ DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
            const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
            const uint32_t* __restrict__ tbits, const int32_t* __restrict__ tpre,
+           const uint32_t* __restrict__ cbits,
            const int32_t* __restrict__ T, const int16_t* __restrict__ T_hm,
            const int32_t* __restrict__ mask_idx, const uint32_t* __restrict__ tmask,
            const int64_t* __restrict__ task_off,
@@ -664,9 +682,13 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
       acc_q = 0;
       while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
       __syncwarp();
+      const uint2 cb = __ldg(reinterpret_cast<const uint2*>(cbits) + gi);
+      const int hint = (int)((cb.x >> lane) & 1u) * kHintLive +
+                       (int)((cb.y >> lane) & 1u) * kHintTabled;
       const int64_t mine =
           setup_item(g, uv, t, toff, mask_idx, tmask, e, T, T_hm, gi * 32 + lane - __ldg(off + e),
-                     __ldg(tbits + gi), __ldg(tpre + gi), lane, need_k, need_q, my + lane, my_mask);
+                     __ldg(tbits + gi), __ldg(tpre + gi), lane, need_k, need_q, hint, my + lane,
+                     my_mask);
       __syncwarp();
       int64_t incl = mine;
 #pragma unroll
@@ -1092,6 +1114,7 @@ void carve_front(void* base, int64_t K, bool all_edges, bool check_dup, int64_t 
 size_t count_mid_bytes(int64_t P) {
   const int64_t groups = (P + 31) / 32;
   return Carve::bytes_for<uint32_t>(groups) + Carve::bytes_for<int32_t>(groups) +
+         Carve::bytes_for<uint32_t>(2 * groups) +
          Carve::bytes_for<int64_t>(groups + 1) +
          Carve::bytes_for<int64_t>(scan_tmp_elems(groups + 1));
 }
@@ -1102,6 +1125,7 @@ void carve_mid(void* base, int64_t P, CountBufs& b) {
   b.groups = (P + 31) / 32;
   b.tbits = c.take<uint32_t>(b.groups);
   b.tpre = c.take<int32_t>(b.groups);
+  b.cbits = c.take<uint32_t>(2 * b.groups);
   b.task_off = c.take<int64_t>(b.groups + 1);
   b.tmp1 = c.take<int64_t>(scan_tmp_elems(b.groups + 1));
 }
@@ -1170,7 +1194,7 @@ int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& t
   const int32_t* mi = g.col_hm != nullptr ? b.mask_idx : nullptr;
   k_chunk_cost<<<sm_count() * kCostBlocksPerSm, kThreads, 0, stream>>>(
       g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.tpre, b.T, T_hm, mi, b.tmask, need_k, need_q,
-      tu.task_probes, b.task_off, b.q, b.stats);
+      tu.task_probes, b.task_off, b.cbits, b.q, b.stats);
   exclusive_scan_i64(b.task_off, b.task_off, b.groups, b.tmp1, stream);
   return 4;
 }
@@ -1183,7 +1207,7 @@ int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& t
                  : tu.quad_blocks_per_sm > kQuadBlocksPerSm ? kQuadBlocksPerSm
                                                             : tu.quad_blocks_per_sm;
   k_quad<<<sms * qb, kThreads, 0, stream>>>(g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.tpre,
-                                            b.T,
+                                            b.cbits, b.T,
                                             g.col_hm != nullptr ? b.T_hm : nullptr,
                                             g.col_hm != nullptr ? b.mask_idx : nullptr, b.tmask,
                                             b.task_off, b.groups, need_k, need_q,
