@@ -92,6 +92,7 @@ int64_t enqueue_batch(gs_batch* b, const Tuning& tu, cudaStream_t stream) {
     n += launch_tmask(g, c, stream);
     n += launch_cost(g, need_k, need_q, tu, c, stream);
     n += launch_quad(g, need_k, need_q, tu, c, stream);
+    n += launch_dense(g, need_q, c, stream);
   }
   n += launch_fold_seg(g, four, b->seg_off, c, stream);
   return n;

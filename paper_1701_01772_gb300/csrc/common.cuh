@@ -39,6 +39,10 @@ __device__ __forceinline__ void raise_error(DevError* err, int32_t code, int64_t
 
 // ---------------------------------------------------------------- graph
 
+// The hub-pair bit matrix covers at most this many vertices (2^14 squared
+// bits = 32 MiB, which stays resident in the 129 MB L2).
+constexpr int64_t kHubMatrixMax = 16384;
+
 // Device view of a registered graph plus its hub index.
 struct DevGraph {
   const int64_t* row_ptr;   // [n+1]
@@ -313,6 +317,7 @@ struct CountBufs {
   // masks of T's matrix members ([ndense][hm_words])
   int32_t* mask_idx = nullptr;
   uint32_t* tmask = nullptr;
+  int64_t* dense_e = nullptr;  // edge of each mask ([ndense])
   int64_t ndense = 0;
 };
 
@@ -333,6 +338,7 @@ int64_t launch_compact(const DevGraph& g, CountBufs& b, cudaStream_t stream);
 int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream);
 int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
                     cudaStream_t stream);
+int64_t launch_dense(const DevGraph& g, bool need_q, CountBufs& b, cudaStream_t stream);
 int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
                     cudaStream_t stream);
 int64_t launch_fold(const gs_graph* gr, const DevGraph& g, bool four, bool need_k, bool need_q,

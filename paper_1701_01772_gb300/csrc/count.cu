@@ -61,6 +61,18 @@ constexpr unsigned kFull = 0xffffffffu;
 // word-parallel AND + popcount over hub-matrix rows.
 constexpr int kDenseMin = 64;
 constexpr unsigned long long kEmpty = ~0ull;
+// Resident CTAs per SM of k_dense_pairs (at most 40 registers).
+constexpr int kDenseBlocksPerSm = 6;
+// Matrix rows are at most this many 128-bit groups.
+constexpr int kHubMatrixMaxGroups = (int)(kHubMatrixMax / 128);
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
 
 __device__ __forceinline__ int64_t deg_of(const int64_t* __restrict__ row_ptr, int32_t v,
                                           int64_t* base) {
@@ -265,12 +277,14 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
 // mask is set iff the member with matrix slot s is in T. One warp per edge.
 __global__ void k_build_tmask(const int64_t* __restrict__ toff, const unsigned long long* __restrict__ t,
                               const int16_t* __restrict__ T_hm, const int32_t* __restrict__ mask_idx,
-                              int64_t K, int64_t words, uint32_t* __restrict__ tmask) {
+                              int64_t K, int64_t words, uint32_t* __restrict__ tmask,
+                              int64_t* __restrict__ dense_e) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < K; e += warps) {
     const int32_t idx = mask_idx[e];
     if (idx < 0) continue;
+    if (lane == 0) dense_e[idx] = e;
     uint32_t* m = tmask + (int64_t)idx * words;
     for (int64_t w = lane; w < words; w += 32) m[w] = 0u;
     __syncwarp();
@@ -279,6 +293,85 @@ __global__ void k_build_tmask(const int64_t* __restrict__ toff, const unsigned l
       const int32_t s = T_hm[b + i];
       if (s >= 0) atomicOr(m + (s >> 5), 1u << (s & 31));
     }
+  }
+}
+
+// Pairs of hub-matrix members of T in the dense edges: member w (slot s)
+// contributes popcount(w's matrix row AND the edge's T mask) over the bits
+// above s, so every adjacent pair of members counts once (k += 1, q += 2).
+// A CTA takes one dense edge at a time from a counter and stages its mask
+// (at most 2 KB) in shared memory; each warp takes 32 T entries at a time
+// and walks the rows of the members among them with lanes over 128-bit
+// groups (coalesced 512-byte reads of the L2-resident matrix).
+__global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
+    k_dense_pairs(const uint32_t* __restrict__ hm_bits, int64_t hm_words,
+                  const int64_t* __restrict__ toff, const unsigned long long* __restrict__ t,
+                  const int16_t* __restrict__ T_hm, const uint32_t* __restrict__ tmask,
+                  const int64_t* __restrict__ dense_e, int64_t ndense, int need_q,
+                  unsigned long long* __restrict__ k_out, unsigned long long* __restrict__ q,
+                  unsigned long long* __restrict__ counter,
+                  unsigned long long* __restrict__ tests) {
+  __shared__ uint4 smask[kHubMatrixMaxGroups];
+  __shared__ unsigned long long part[kThreads / 32][2];
+  __shared__ int64_t cur;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = (int)(hm_words / 4);
+  for (;;) {
+    if (threadIdx.x == 0) cur = (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t idx = cur;
+    if (idx >= ndense) break;
+    const int64_t e = dense_e[idx];
+    const uint4* m = reinterpret_cast<const uint4*>(tmask + idx * hm_words);
+    for (int i = threadIdx.x; i < G; i += kThreads) smask[i] = m[i];
+    __syncthreads();
+    const int64_t b = toff[e], len = (int64_t)t[e];
+    unsigned long long acc = 0, groups = 0;
+    for (int64_t c0 = (int64_t)wid * 32; c0 < len; c0 += kThreads) {
+      const int xs = c0 + lane < len ? (int)__ldg(T_hm + b + c0 + lane) : -1;
+      unsigned members = __ballot_sync(kFull, xs >= 0);
+      while (members) {
+        const int src = __ffs(members) - 1;
+        members &= members - 1;
+        const int sl = __shfl_sync(kFull, xs, src);
+        const int g0 = sl >> 7, b0 = sl & 127;
+        const uint4* row = reinterpret_cast<const uint4*>(hm_bits + (int64_t)sl * hm_words);
+        groups += G - g0;
+        for (int gg = g0 + lane; gg < G; gg += 32) {
+          const uint4 rw = ld_keep4(row + gg);
+          const uint4 mk = smask[gg];
+          uint32_t wd[4] = {rw.x & mk.x, rw.y & mk.y, rw.z & mk.z, rw.w & mk.w};
+          if (gg == g0) {  // only the bits above w's own
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+              const int lo_bit = 32 * q4;
+              if (b0 >= lo_bit + 31) wd[q4] = 0u;
+              else if (b0 >= lo_bit) wd[q4] &= ~0u << (b0 - lo_bit + 1);
+            }
+          }
+          acc += __popc(wd[0]) + __popc(wd[1]) + __popc(wd[2]) + __popc(wd[3]);
+        }
+      }
+    }
+    acc = warp_sum<unsigned long long>(acc);
+    if (lane == 0) {
+      part[wid][0] = acc;
+      part[wid][1] = groups;  // the same on every lane
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long sk = 0, sg = 0;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        sk += part[w][0];
+        sg += part[w][1];
+      }
+      if (sk) {
+        atomicAdd(k_out + e, sk);
+        if (need_q) atomicAdd(q + e, 2 * sk);
+      }
+      if (sg) atomicAdd(tests, sg);
+    }
+    __syncthreads();  // smask, part and cur are reused for the next edge
   }
 }
 
@@ -310,11 +403,11 @@ struct Seg {
   int32_t cnt;          // number of tests
 };
 
-// Segment-A modes of an item w in T: 0 = tests (pairs above w), 1 = dense
-// words (w has a matrix slot and the edge is dense: AND of w's matrix row
-// with the edge's T mask, slots above w's), 2 = rest (w has no matrix slot
-// and the edge is dense: x over N(w), counted when x is in T and either
-// has a matrix slot or is above w).
+// Segment-A modes of an item w in T: 0 = tests (pairs above w), 2 = rest
+// (w has no matrix slot and the edge is dense: x over N(w), counted when x
+// is in T and either has a matrix slot or is above w). A matrix member of
+// a dense edge has no segment A here: k_dense_pairs counts its pairs with
+// other members.
 struct Item {
   Seg a, b;
   int32_t amode;
@@ -449,17 +542,8 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   int64_t bw;
   const int64_t dw = deg_of(g.row_ptr, w, &bw);
   if (in_t && c.tmask != nullptr) {
-    const int32_t sw = table_slot(g, w);
-    if (sw >= 0) {
-      // dense: 128-bit groups of w's matrix row from the group holding bit
-      // sw on, ANDed with the mask; a unit of work is one group
-      const int64_t g0 = sw >> 7;
-      it.amode = 1;
-      it.a.it = reinterpret_cast<const int32_t*>(g.hm_bits + (int64_t)sw * g.hm_words + 4 * g0);
-      it.a.sl = reinterpret_cast<const int32_t*>(c.tmask + 4 * g0);
-      it.a.sslot = sw & 127;  // bit of w in the first group: only higher bits count
-      it.a.cnt = (int32_t)(g.hm_words / 4 - g0);
-    } else {
+    // dense edge: the pairs among matrix members come from k_dense_pairs
+    if (table_slot(g, w) < 0) {
       // rest: x over N(w), x in T, and (x has a matrix slot or x > w)
       it.amode = 2;
       it.rest_w = w;
@@ -519,12 +603,6 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   (void)need_k;
 }
 
-template <class T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
 
 // Chunk costs: membership tests per chunk and the number of tasks it needs.
 // Also adds the constant part of q. Same warp partition as k_tri.
@@ -712,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
     for (int32_t r = lane; r - lane < len; r += 64) {
       int32_t x[2], xs[2], seg[2], o[2];
       const SharedItem* it[2];
-      bool act[2], words[2];
+      bool act[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int32_t rr = r + 32 * h;  // test index within the task
@@ -728,26 +806,9 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         o[h] = rr - sj;
         seg[h] = o[h] < it[h]->ca ? 0 : 1;
         if (seg[h]) o[h] -= it[h]->ca;
-        words[h] = act[h] && seg[h] == 0 && (it[h]->mode & 0xff) == 1;
         x[h] = 0;
         xs[h] = -1;
-        if (words[h]) {
-          // dense: one 128-bit group of the row ANDed with the T mask; the
-          // group holding w's bit keeps only the bits above it
-          const uint4 rw = ld_keep4(reinterpret_cast<const uint4*>(it[h]->it[0]) + o[h]);
-          const uint4 mk = __ldg(reinterpret_cast<const uint4*>(it[h]->sl[0]) + o[h]);
-          uint32_t wd[4] = {rw.x & mk.x, rw.y & mk.y, rw.z & mk.z, rw.w & mk.w};
-          if (o[h] == 0) {
-            const int b0 = it[h]->sslot[0];
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-              const int lo_bit = 32 * q4;
-              if (b0 >= lo_bit + 31) wd[q4] = 0u;
-              else if (b0 >= lo_bit) wd[q4] &= ~0u << (b0 - lo_bit + 1);
-            }
-          }
-          x[h] = __popc(wd[0]) + __popc(wd[1]) + __popc(wd[2]) + __popc(wd[3]);
-        } else if (act[h]) {
+        if (act[h]) {
           const int32_t* ip = it[h]->it[seg[h]] + o[h];
           x[h] = __ldg(ip);
           xs[h] = kNoSlotInfo;
@@ -768,7 +829,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
         bucket[h] = false;
         word[h] = 0;
         bitpos[h] = 0;
-        if (!act[h] || words[h]) continue;
+        if (!act[h]) continue;
         if (seg[h] == 0 && (it[h]->mode & 0xff) == 2) {
           // rest mode (sbm[0] holds w): a matrix member x is in T iff its
           // bit is set in the edge's T mask; other x count only above w and
@@ -815,12 +876,6 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         if (!act[h]) continue;
-        if (words[h]) {
-          // pairs of matrix members in T above w, counted in the load stage
-          acc_k += x[h];
-          acc_q += need_q ? 2 * x[h] : 0;
-          continue;
-        }
         bool hit = direct[h]   ? ((word[h] >> bitpos[h]) & 1u) != 0
                    : bucket[h] ? bucket_contains(it[h]->sl[seg[h]] + word[h],
                                                  (int32_t)(bitpos[h] - word[h]), x[h])
@@ -1183,7 +1238,17 @@ int64_t launch_compact(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
 int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
   if (b.ndense <= 0 || g.col_hm == nullptr) return 0;
   k_build_tmask<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(
-      b.toff, b.t, b.T_hm, b.mask_idx, b.K, g.hm_words, b.tmask);
+      b.toff, b.t, b.T_hm, b.mask_idx, b.K, g.hm_words, b.tmask, b.dense_e);
+  return 1;
+}
+
+// Pairs among the matrix members of T in the dense edges (k_dense_pairs).
+// No host sync.
+int64_t launch_dense(const DevGraph& g, bool need_q, CountBufs& b, cudaStream_t stream) {
+  if (b.ndense <= 0 || g.col_hm == nullptr) return 0;
+  k_dense_pairs<<<sm_count() * kDenseBlocksPerSm, kThreads, 0, stream>>>(
+      g.hm_bits, g.hm_words, b.toff, b.t, b.T_hm, b.tmask, b.dense_e, b.ndense, need_q ? 1 : 0,
+      b.k2, b.q, b.stats + 7, b.stats + 1);
   return 1;
 }
 
@@ -1331,10 +1396,16 @@ gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs
     GS_CUDA(cudaStreamSynchronize(stream));
     b.ndense = (int64_t)nd;
     b.tmask = nullptr;
+    b.dense_e = nullptr;
     if (b.ndense > 0) {
       void* base4 = nullptr;
-      GS_TRY(ws_reserve(ws, 4, sizeof(uint32_t) * (size_t)(b.ndense * g.hm_words), stream, &base4));
-      b.tmask = (uint32_t*)base4;
+      GS_TRY(ws_reserve(ws, 4,
+                        Carve::bytes_for<uint32_t>(b.ndense * g.hm_words) +
+                            Carve::bytes_for<int64_t>(b.ndense),
+                        stream, &base4));
+      Carve c4{(char*)base4, 0};
+      b.tmask = c4.take<uint32_t>(b.ndense * g.hm_words);
+      b.dense_e = c4.take<int64_t>(b.ndense);
     }
     timer.stop(2);
     timer.start(3);
@@ -1343,6 +1414,7 @@ gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs
     timer.stop(3);
     timer.start(4);
     more += launch_quad(g, need_k, need_q, tu, b, stream);
+    more += launch_dense(g, need_q, b, stream);
     timer.stop(4);
     GS_CUDA(cudaGetLastError());
   } else {

@@ -16,9 +16,6 @@ constexpr int64_t kHubMinDegree = 64;
 constexpr int64_t kDirMinDegree = 16;
 // Mid rows of the mid x big co-degree table start at this degree.
 constexpr int64_t kMidMinDegree = 8;
-// The hub-pair bit matrix covers at most this many vertices (2^14 squared
-// bits = 32 MiB, which stays resident in the 129 MB L2).
-constexpr int64_t kHubMatrixMax = 16384;
 
 // ------------------------------------------------------------- validation
 // One warp per row (grid-stride). Checks the simple-graph conditions of
