@@ -318,6 +318,9 @@ struct CountBufs {
   int32_t* mask_idx = nullptr;
   uint32_t* tmask = nullptr;
   int64_t* dense_e = nullptr;  // edge of each mask ([ndense])
+  int64_t* unit_off = nullptr;  // k_dense_pairs work units per mask, scanned ([ndense + 1])
+  int64_t* unit_tmp = nullptr;
+  int32_t* unit_idx = nullptr;  // dense edge (mask index) of each work unit
   int64_t ndense = 0;
 };
 

@@ -63,6 +63,9 @@ constexpr int kDenseMin = 64;
 constexpr unsigned long long kEmpty = ~0ull;
 // Resident CTAs per SM of k_dense_pairs (at most 40 registers).
 constexpr int kDenseBlocksPerSm = 6;
+// T entries per k_dense_pairs work unit (a heavy dense edge is split into
+// several units so that small samples still fill the GPU).
+constexpr int64_t kDenseUnit = 4 * kThreads;
 // Matrix rows are at most this many 128-bit groups.
 constexpr int kHubMatrixMaxGroups = (int)(kHubMatrixMax / 128);
 
@@ -278,13 +281,16 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
 __global__ void k_build_tmask(const int64_t* __restrict__ toff, const unsigned long long* __restrict__ t,
                               const int16_t* __restrict__ T_hm, const int32_t* __restrict__ mask_idx,
                               int64_t K, int64_t words, uint32_t* __restrict__ tmask,
-                              int64_t* __restrict__ dense_e) {
+                              int64_t* __restrict__ dense_e, int64_t* __restrict__ units) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < K; e += warps) {
     const int32_t idx = mask_idx[e];
     if (idx < 0) continue;
-    if (lane == 0) dense_e[idx] = e;
+    if (lane == 0) {
+      dense_e[idx] = e;
+      units[idx] = ((int64_t)t[e] + kDenseUnit - 1) / kDenseUnit;
+    }
     uint32_t* m = tmask + (int64_t)idx * words;
     for (int64_t w = lane; w < words; w += 32) m[w] = 0u;
     __syncwarp();
@@ -296,18 +302,34 @@ __global__ void k_build_tmask(const int64_t* __restrict__ toff, const unsigned l
   }
 }
 
+// Dense edge of every k_dense_pairs work unit: unit_idx[u] = mask index.
+// One warp per dense edge.
+__global__ void k_unit_fill(const int64_t* __restrict__ unit_off, int64_t ndense,
+                            int32_t* __restrict__ unit_idx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; idx < ndense;
+       idx += warps)
+    for (int64_t u = unit_off[idx] + lane; u < unit_off[idx + 1]; u += 32)
+      unit_idx[u] = (int32_t)idx;
+}
+
 // Pairs of hub-matrix members of T in the dense edges: member w (slot s)
 // contributes popcount(w's matrix row AND the edge's T mask) over the bits
 // above s, so every adjacent pair of members counts once (k += 1, q += 2).
-// A CTA takes one dense edge at a time from a counter and stages its mask
-// (at most 2 KB) in shared memory; each warp takes 32 T entries at a time
-// and walks the rows of the members among them with lanes over 128-bit
-// groups (coalesced 512-byte reads of the L2-resident matrix).
+// Work units are kDenseUnit consecutive T entries of one dense edge
+// (unit_off: exclusive scan of the units per dense edge, unit_idx: the
+// dense edge of each unit); a CTA takes one unit at a time from a counter
+// and stages the edge's mask (at most 2 KB) in shared memory; each warp
+// takes 32 of the unit's entries at a time and walks the rows of the
+// members among them with lanes over 128-bit groups (coalesced 512-byte
+// reads of the L2-resident matrix).
 __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
     k_dense_pairs(const uint32_t* __restrict__ hm_bits, int64_t hm_words,
                   const int64_t* __restrict__ toff, const unsigned long long* __restrict__ t,
                   const int16_t* __restrict__ T_hm, const uint32_t* __restrict__ tmask,
-                  const int64_t* __restrict__ dense_e, int64_t ndense, int need_q,
+                  const int64_t* __restrict__ dense_e, const int64_t* __restrict__ unit_off,
+                  const int32_t* __restrict__ unit_idx, int64_t ndense, int need_q,
                   unsigned long long* __restrict__ k_out, unsigned long long* __restrict__ q,
                   unsigned long long* __restrict__ counter,
                   unsigned long long* __restrict__ tests) {
@@ -319,15 +341,18 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
   for (;;) {
     if (threadIdx.x == 0) cur = (int64_t)atomicAdd(counter, 1ull);
     __syncthreads();
-    const int64_t idx = cur;
-    if (idx >= ndense) break;
+    const int64_t unit = cur;
+    if (unit >= __ldg(unit_off + ndense)) break;
+    const int64_t idx = __ldg(unit_idx + unit);
     const int64_t e = dense_e[idx];
     const uint4* m = reinterpret_cast<const uint4*>(tmask + idx * hm_words);
     for (int i = threadIdx.x; i < G; i += kThreads) smask[i] = m[i];
     __syncthreads();
-    const int64_t b = toff[e], len = (int64_t)t[e];
+    const int64_t b = toff[e];
+    const int64_t r0 = (unit - __ldg(unit_off + idx)) * kDenseUnit;
+    const int64_t len = min((int64_t)t[e], r0 + kDenseUnit);
     unsigned long long acc = 0, groups = 0;
-    for (int64_t c0 = (int64_t)wid * 32; c0 < len; c0 += kThreads) {
+    for (int64_t c0 = r0 + (int64_t)wid * 32; c0 < len; c0 += kThreads) {
       const int xs = c0 + lane < len ? (int)__ldg(T_hm + b + c0 + lane) : -1;
       unsigned members = __ballot_sync(kFull, xs >= 0);
       while (members) {
@@ -371,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
       }
       if (sg) atomicAdd(tests, sg);
     }
-    __syncthreads();  // smask, part and cur are reused for the next edge
+    __syncthreads();  // smask, part and cur are reused for the next unit
   }
 }
 
@@ -462,11 +487,10 @@ __device__ __forceinline__ uint32_t table_codeg(const DevGraph& g, int32_t a, in
   return 0;
 }
 
-// What the cost pass learnt about an item, for the 4-node pass (hint < 0:
-// nothing; compute everything): it has tests, and a co-degree table
-// answered its segment B (so the 4-node pass needs neither the table nor
-// the item when it has no tests). The constant q terms are added by the cost
-// pass alone.
+// What the cost pass learnt about an item, for the 4-node pass: it has
+// tests, and a co-degree table answered its segment B (so the 4-node pass
+// needs neither the table nor the item when it has no tests). The constant
+// q terms are added by the cost pass alone.
 constexpr int kHintLive = 1;
 constexpr int kHintTabled = 2;
 
@@ -521,7 +545,7 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
                                           const int32_t* __restrict__ T,
                                           const int16_t* __restrict__ T_hm, int64_t i,
                                           uint32_t tword, int32_t tbase, int lane, bool need_k,
-                                          bool need_q, int hint, Item& it) {
+                                          bool need_q, Item& it) {
   it.a.cnt = it.b.cnt = 0;
   it.tabled = false;
   it.a.it = it.a.sl = it.b.it = it.b.sl = g.col;
@@ -535,7 +559,6 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   it.amode = 0;
   it.rest_w = -1;
   if (i >= c.du) return;
-  if (hint >= 0 && !(hint & kHintLive)) return;  // no tests (known from the cost pass)
   const int32_t w = __ldg(g.col + c.bu + i);
   if (w == c.v) return;
   const bool in_t = (tword >> lane) & 1u;
@@ -579,7 +602,7 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
     if (need_q) {
       // segment B: -(c(w, u) - 1)
       it.bsign = -1;
-      const uint32_t tc = hint >= 0 ? (hint & kHintTabled ? 1u : 0u) : table_codeg(g, w, c.u);
+      const uint32_t tc = table_codeg(g, w, c.u);
       it.tabled = tc != 0;
       if (tc != 0) {
         it.qconst = 1 - (int64_t)(tc - 1u);
@@ -591,7 +614,7 @@ __device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
   } else if (need_q) {
     // segment B: c(w, v) - 1
     it.bsign = 1;
-    const uint32_t tc = hint >= 0 ? (hint & kHintTabled ? 1u : 0u) : table_codeg(g, w, c.v);
+    const uint32_t tc = table_codeg(g, w, c.v);
     it.tabled = tc != 0;
     if (tc != 0) {
       it.qconst = (int64_t)(tc - 1u) - 1;
@@ -632,7 +655,7 @@ __global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
     if (e != c.e) load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
     Item it;
     load_item(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), __ldg(tpre + gi),
-              lane, need_k, need_q, -1, it);
+              lane, need_k, need_q, it);
     const unsigned live = __ballot_sync(kFull, it.a.cnt + it.b.cnt > 0);
     const unsigned tabled = __ballot_sync(kFull, it.tabled);
     if (lane == 0) reinterpret_cast<uint2*>(cbits)[gi] = make_uint2(live, tabled);
@@ -684,38 +707,86 @@ static_assert(sizeof(SharedItem) == 64, "SharedItem size");
 
 // Item set-up of k_quad, out of line: it runs once per chunk and its
 // temporaries would otherwise raise the register count of the test loop.
-// Writes the lane's descriptor straight to shared memory (no Item or edge
-// context passes through local memory) and returns the item's test count.
+// Follows load_item, with the cost pass's hint in place of the table reads,
+// and stores each field to the lane's shared-memory descriptor as soon as
+// it is known (only the segments that have tests are written; a segment
+// with no tests is never read). Returns the item's test count.
 __device__ __noinline__ int64_t setup_item(const DevGraph& g, const int2* __restrict__ uv,
                                            const unsigned long long* __restrict__ t,
                                            const int64_t* __restrict__ toff,
                                            const int32_t* __restrict__ mask_idx,
                                            const uint32_t* __restrict__ tmask, int64_t e,
-                                           const int32_t* __restrict__ T,
-                                           const int16_t* __restrict__ T_hm, int64_t i,
-                                           uint32_t tword, int32_t tbase, int lane, bool need_k,
-                                           bool need_q, int hint, SharedItem* si,
+                                           const int32_t* __restrict__ T, int64_t i,
+                                           uint32_t tword, int32_t tbase, int lane, bool need_q,
+                                           int hint, SharedItem* si,
                                            const uint32_t** chunk_mask) {
   EdgeCtx c;
   load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
-  Item it;
-  load_item(g, c, T, T_hm, i, tword, tbase, lane, need_k, need_q, hint, it);
-  si->it[0] = it.a.it;
-  si->it[1] = it.b.it;
-  si->sl[0] = it.a.sl;
-  si->sl[1] = it.b.sl;
-  si->sslot[0] = (int16_t)it.a.sslot;
-  si->sslot[1] = (int16_t)it.b.sslot;
-  si->sbm[0] = it.amode == 2 ? it.rest_w : it.a.sbm;
-  si->sbm[1] = it.b.sbm;
-  si->slen[0] = it.a.slen;
-  si->slen[1] = it.b.slen;
-  si->ca = it.a.cnt;
-  // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2 when q
-  // is wanted); segment B adds +-1 to q
-  si->mode = it.amode | ((it.bsign + 1) << 8);
   if (lane == 0) *chunk_mask = c.tmask;
-  return (int64_t)it.a.cnt + it.b.cnt;
+  int32_t ca = 0, cb = 0, amode = 0, bsign = 0;
+  if (i < c.du && (hint & kHintLive)) {
+    const int32_t w = __ldg(g.col + c.bu + i);
+    if (w != c.v) {
+      const bool in_t = (tword >> lane) & 1u;
+      int64_t bw;
+      const int64_t dw = deg_of(g.row_ptr, w, &bw);
+      if (in_t && c.tmask != nullptr) {
+        // dense edge: only a vertex without a matrix slot has segment A here
+        if (table_slot(g, w) < 0) {
+          amode = 2;
+          si->it[0] = g.col + bw;
+          si->sl[0] = T + c.toff;
+          si->slen[0] = (int32_t)c.te;
+          si->sslot[0] = -1;
+          si->sbm[0] = w;
+          ca = (int32_t)dw;
+        }
+      } else if (in_t) {
+        const int64_t iw = tbase + __popc(tword & ((1u << lane) - 1u));
+        const int64_t tg = c.te - iw - 1;
+        const int64_t upw = __ldg(g.up_ptr + w);
+        const int64_t dup = bw + dw - upw;
+        if (dup <= tg) {
+          si->it[0] = g.col + upw;
+          si->sl[0] = T + c.toff + iw + 1;
+          si->slen[0] = (int32_t)tg;
+          si->sslot[0] = -1;
+          si->sbm[0] = -1;
+          ca = (int32_t)dup;
+        } else {
+          Seg sa;
+          set_search(g, w, bw, dw, sa);
+          si->it[0] = T + c.toff + iw + 1;
+          si->sl[0] = sa.sl;
+          si->slen[0] = sa.slen;
+          si->sslot[0] = (int16_t)sa.sslot;
+          si->sbm[0] = sa.sbm;
+          ca = (int32_t)tg;
+        }
+      }
+      if (need_q) {
+        // segment B: c(w, u) for w in T (q -= 1 per hit), c(w, v) for w in
+        // S_u (q += 1 per hit), unless a co-degree table answered it
+        bsign = in_t ? -1 : 1;
+        if (!(hint & kHintTabled)) {
+          Seg sb;
+          if (in_t) codeg_segment(g, w, bw, dw, c.u, c.bu, c.du, sb);
+          else codeg_segment(g, w, bw, dw, c.v, c.bv, c.dv, sb);
+          si->it[1] = sb.it;
+          si->sl[1] = sb.sl;
+          si->slen[1] = sb.slen;
+          si->sslot[1] = (int16_t)sb.sslot;
+          si->sbm[1] = sb.sbm;
+          cb = sb.cnt;
+        }
+      }
+    }
+  }
+  si->ca = ca;
+  // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2 when q
+  // is wanted); segment B adds bsign to q
+  si->mode = amode | ((bsign + 1) << 8);
+  return (int64_t)ca + cb;
 }
 
 __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
@@ -764,8 +835,8 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
       const int hint = (int)((cb.x >> lane) & 1u) * kHintLive +
                        (int)((cb.y >> lane) & 1u) * kHintTabled;
       const int64_t mine =
-          setup_item(g, uv, t, toff, mask_idx, tmask, e, T, T_hm, gi * 32 + lane - __ldg(off + e),
-                     __ldg(tbits + gi), __ldg(tpre + gi), lane, need_k, need_q, hint, my + lane,
+          setup_item(g, uv, t, toff, mask_idx, tmask, e, T, gi * 32 + lane - __ldg(off + e),
+                     __ldg(tbits + gi), __ldg(tpre + gi), lane, need_q, hint, my + lane,
                      my_mask);
       __syncwarp();
       int64_t incl = mine;
@@ -1238,8 +1309,11 @@ int64_t launch_compact(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
 int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
   if (b.ndense <= 0 || g.col_hm == nullptr) return 0;
   k_build_tmask<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(
-      b.toff, b.t, b.T_hm, b.mask_idx, b.K, g.hm_words, b.tmask, b.dense_e);
-  return 1;
+      b.toff, b.t, b.T_hm, b.mask_idx, b.K, g.hm_words, b.tmask, b.dense_e, b.unit_off);
+  exclusive_scan_i64(b.unit_off, b.unit_off, b.ndense, b.unit_tmp, stream);
+  k_unit_fill<<<grid_for(b.ndense * 32, kThreads, 8), kThreads, 0, stream>>>(b.unit_off, b.ndense,
+                                                                              b.unit_idx);
+  return 5;
 }
 
 // Pairs among the matrix members of T in the dense edges (k_dense_pairs).
@@ -1247,7 +1321,8 @@ int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
 int64_t launch_dense(const DevGraph& g, bool need_q, CountBufs& b, cudaStream_t stream) {
   if (b.ndense <= 0 || g.col_hm == nullptr) return 0;
   k_dense_pairs<<<sm_count() * kDenseBlocksPerSm, kThreads, 0, stream>>>(
-      g.hm_bits, g.hm_words, b.toff, b.t, b.T_hm, b.tmask, b.dense_e, b.ndense, need_q ? 1 : 0,
+      g.hm_bits, g.hm_words, b.toff, b.t, b.T_hm, b.tmask, b.dense_e, b.unit_off, b.unit_idx,
+      b.ndense, need_q ? 1 : 0,
       b.k2, b.q, b.stats + 7, b.stats + 1);
   return 1;
 }
@@ -1401,11 +1476,18 @@ gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs
       void* base4 = nullptr;
       GS_TRY(ws_reserve(ws, 4,
                         Carve::bytes_for<uint32_t>(b.ndense * g.hm_words) +
-                            Carve::bytes_for<int64_t>(b.ndense),
+                            Carve::bytes_for<int64_t>(b.ndense) +
+                            Carve::bytes_for<int64_t>(b.ndense + 1) +
+                            Carve::bytes_for<int64_t>(scan_tmp_elems(b.ndense + 1)) +
+                            Carve::bytes_for<int32_t>(b.tsum / kDenseUnit + b.ndense),
                         stream, &base4));
       Carve c4{(char*)base4, 0};
       b.tmask = c4.take<uint32_t>(b.ndense * g.hm_words);
       b.dense_e = c4.take<int64_t>(b.ndense);
+      b.unit_off = c4.take<int64_t>(b.ndense + 1);
+      b.unit_tmp = c4.take<int64_t>(scan_tmp_elems(b.ndense + 1));
+      // units of an edge: ceil(t / kDenseUnit) <= t / kDenseUnit + 1
+      b.unit_idx = c4.take<int32_t>(b.tsum / kDenseUnit + b.ndense);
     }
     timer.stop(2);
     timer.start(3);
