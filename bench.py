@@ -296,16 +296,18 @@ def run_gpu(args, rank, world, device):
 
     peak, peak_kind = load_peaks()
     achieved = (quad_bytes / (quad_ms / 1e3)) / 1e9 if quad_ms > 0 else 0.0
-    traffic = load_traffic("k_quad")
+    traffic = load_traffic("quad_phase")
     tests_per_launch = quad_tests / max(quad_launches, 1)
     traffic_bytes = (traffic["dram_bytes_per_test"] * tests_per_launch) if traffic else None
     avg_s = quad_ms / max(quad_launches, 1) / 1e3
-    roofline = {"kernel": "k_quad (4-node membership tests)", "bound": "hbm",
+    roofline = {"kernel": "4-node phase: k_quad (membership tests) + k_dense_pairs (dense-edge "
+                          "member pairs)", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                 "traffic": round(traffic_bytes) if traffic_bytes else None,
-                "traffic_source": ("ncu dram bytes per membership test on a 0.1% sample x tests "
-                                   "per launch") if traffic else None,
+                "traffic_source": ("ncu dram bytes of k_quad + k_dense_pairs per membership test "
+                                   "(or matrix group) on a 0.1% sample x tests per launch")
+                if traffic else None,
                 "dram_frac": round(traffic_bytes / avg_s / 1e9 / peak, 4) if traffic_bytes else None,
                 "avg_launch_ms": round(quad_ms / max(quad_launches, 1), 3),
                 "model_bytes_per_launch": quad_bytes // max(quad_launches, 1),

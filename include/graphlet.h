@@ -204,7 +204,8 @@ gs_status gs_estimate(const gs_sums* s, double z, gs_result* out);
 typedef struct {
   int64_t k;              /* sampled edges counted */
   int64_t tri_tests;      /* membership tests of the triangle pass (sum d_u) */
-  int64_t quad_tests;     /* membership tests of the 4-node pass */
+  int64_t quad_tests;     /* membership tests of the 4-node pass (plus the
+                             128-bit matrix-row groups of the dense edges) */
   int64_t t_sum;          /* sum over J of |T_e| */
   int64_t tasks;          /* 4-node work units of kTaskProbes tests */
   uint64_t model_bytes;   /* sum over J of B(e) */
@@ -214,6 +215,8 @@ typedef struct {
   int64_t launches_total; /* kernels launched through this workspace so far */
   int32_t timed;          /* 1 if the ms_* fields below are valid */
   float ms_prep, ms_tri, ms_compact, ms_cost, ms_quad, ms_fold; /* device ms per phase */
+  int64_t dense_edges;    /* sampled edges whose pairs of hub-matrix members in T
+                             were counted word-parallel (matrix row AND T mask) */
 } gs_stats;
 
 /* Turns per-phase CUDA-event timing of gs_count on (1) or off (0). Events are

@@ -1562,6 +1562,7 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   gs_stats& st = ws->stats;
   st.k = K;
   st.tri_tests = (int64_t)hs[0];
+  st.dense_edges = (int64_t)hs[6];
   st.quad_tests = (int64_t)hs[1];
   st.model_bytes = hs[2] + hs[3];
   st.model_tri_bytes = hs[2];

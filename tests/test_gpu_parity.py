@@ -335,6 +335,7 @@ def test_dense_clique_mode_closed_form():
     rp, col = synth.from_pairs(n, np.array([e[0] for e in edges]), np.array([e[1] for e in edges]))
     g = _graph(rp, col)
     res = gs.gs_estimate(g.count(None)).as_dict()
+    assert g.ws.stats()["dense_edges"] == g.m  # every edge's T is the other 298 vertices
     want = brute.closed_form("complete", 300)
     for i in ALL:
         assert res[i]["exact"] == want[i], i
@@ -344,5 +345,10 @@ def test_dense_clique_mode_closed_form():
 def test_dense_clique_mode_mixed_t_against_oracle():
     rp, col = _core_periphery()
     sample = synth.explicit_sample(rp, col, 0.03, seed=9)
+    g = _graph(rp, col)
+    g.count(torch.as_tensor(sample, device="cuda"))
+    st = g.ws.stats()
+    assert 0 < st["dense_edges"] < len(sample)  # core edges dense, periphery edges not
+    g.close()
     _full_check(rp, col, sample)
     _full_check(rp, col, sample, hub_budget=NO_HUBS)
