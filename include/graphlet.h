@@ -207,7 +207,7 @@ typedef struct {
   int64_t quad_tests;     /* membership tests of the 4-node pass (plus the
                              128-bit matrix-row groups of the dense edges) */
   int64_t t_sum;          /* sum over J of |T_e| */
-  int64_t tasks;          /* 4-node work units of kTaskProbes tests */
+  int64_t tasks;          /* 4-node work units (task_probes tests each, default 512) */
   uint64_t model_bytes;   /* sum over J of B(e) */
   uint64_t model_tri_bytes;  /* the 24 + 4 (d_u + d_v) part (triangle pass) */
   uint64_t model_quad_bytes; /* the 4-clique + 4-cycle part (4-node pass) */
@@ -226,8 +226,10 @@ gs_status gs_workspace_set_timing(gs_workspace* ws, int enable);
 /* Launch choices for gs_count on this workspace (the batched path's
  * autotuner searches the same knobs): resident CTAs per SM of the triangle
  * pass (1..8) and of the 4-node pass (1..8), membership tests per 4-node
- * work unit (32..2^20), and use_hubs = 0 to ignore the hub bitmaps,
- * co-degree table and hub-pair matrix. Results do not depend on them. */
+ * work unit (32..2^20), and use_hubs = 0 to ignore the per-graph index
+ * (bitmaps, co-degree tables, hub-pair matrix, bucket directories).
+ * Without a call the defaults are 8, 8, 512, 1. Results do not depend on
+ * them. */
 gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_per_sm, int quad_blocks_per_sm,
                                   int64_t task_probes, int use_hubs);
 

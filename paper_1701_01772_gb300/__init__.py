@@ -389,8 +389,8 @@ class Workspace:
     def set_timing(self, enable: bool = True) -> None:
         gs_workspace_set_timing(self.handle, enable)
 
-    def set_tuning(self, tri_blocks_per_sm: int = 4, quad_blocks_per_sm: int = 8,
-                   task_probes: int = 1024, use_hubs: bool = True) -> None:
+    def set_tuning(self, tri_blocks_per_sm: int = 8, quad_blocks_per_sm: int = 8,
+                   task_probes: int = 512, use_hubs: bool = True) -> None:
         gs_workspace_set_tuning(self.handle, tri_blocks_per_sm, quad_blocks_per_sm, task_probes,
                                 use_hubs)
 
