@@ -86,6 +86,8 @@ struct DevGraph {
   const uint32_t* dir;
   int32_t id_bits;          // vertex ids are below 2^id_bits
   int64_t dir_count;        // vertices with a directory
+  // beside the adjacency (NULL if absent): tb_slot[col[p]]
+  const int32_t* col_tb;
 };
 
 // log2 of the number of directory buckets of a vertex of degree d >= 2:
@@ -239,6 +241,7 @@ struct gs_graph {
   uint16_t* md_codeg;
   int64_t* dir_at;
   uint32_t* dir;
+  int32_t* col_tb;
 };
 
 namespace gs {

@@ -428,19 +428,11 @@ struct Seg {
   int32_t cnt;          // number of tests
 };
 
-// Segment-A modes of an item w in T: 0 = tests (pairs above w), 2 = rest
-// (w has no matrix slot and the edge is dense: x over N(w), counted when x
-// is in T and either has a matrix slot or is above w). A matrix member of
-// a dense edge has no segment A here: k_dense_pairs counts its pairs with
-// other members.
-struct Item {
-  Seg a, b;
-  int32_t amode;
-  int32_t rest_w;
-  int32_t bsign;        // +1 (w in S_u) or -1 (w in T) per segment-B hit
-  bool tabled;          // a co-degree table answered segment B
-  int64_t qconst;       // constant q contribution of this item
-};
+// Segment-A modes of an item w in T (k_quad): 0 = tests (pairs above w),
+// 2 = rest (w has no matrix slot and the edge is dense: x over N(w),
+// counted when x is in T and either has a matrix slot or is above w). A
+// matrix member of a dense edge has no segment A there: k_dense_pairs
+// counts its pairs with other members.
 
 struct EdgeCtx {
   int64_t e;
@@ -471,9 +463,11 @@ __device__ __forceinline__ void load_edge(const DevGraph& g, const int2* __restr
 // c(a, b) + 1 from the co-degree table when both are table hubs or from the
 // mid x big table when one is a mid vertex and the other a big hub; 0 when
 // neither can answer (the +1 marks a present entry).
-__device__ __forceinline__ uint32_t table_codeg(const DevGraph& g, int32_t a, int32_t b) {
+// sa is a's table slot (tb_slot[a], -1 without a table).
+__device__ __forceinline__ uint32_t table_codeg_s(const DevGraph& g, int32_t a, int32_t sa,
+                                                  int32_t b) {
   if (g.tb_slot == nullptr) return 0;
-  int32_t sa = __ldg(g.tb_slot + a), sb = __ldg(g.tb_slot + b);
+  const int32_t sb = __ldg(g.tb_slot + b);
   if (sa >= 0 && sb >= 0) {
     int32_t lo = min(sa, sb), hi = max(sa, sb);
     return ld_once(g.tb_codeg + (int64_t)lo * g.tb_count + hi) + 1u;
@@ -541,89 +535,53 @@ __device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int6
   }
 }
 
-__device__ __forceinline__ void load_item(const DevGraph& g, const EdgeCtx& c,
-                                          const int32_t* __restrict__ T,
-                                          const int16_t* __restrict__ T_hm, int64_t i,
-                                          uint32_t tword, int32_t tbase, int lane, bool need_k,
-                                          bool need_q, Item& it) {
-  it.a.cnt = it.b.cnt = 0;
-  it.tabled = false;
-  it.a.it = it.a.sl = it.b.it = it.b.sl = g.col;
-  it.a.its = it.b.its = nullptr;
-  it.a.svtx = it.b.svtx = -1;
-  it.a.sslot = it.b.sslot = -1;
-  it.a.sbm = it.b.sbm = -1;
-  it.a.slen = it.b.slen = 0;
-  it.qconst = 0;
-  it.bsign = 0;
-  it.amode = 0;
-  it.rest_w = -1;
-  if (i >= c.du) return;
-  const int32_t w = __ldg(g.col + c.bu + i);
-  if (w == c.v) return;
+// Tests of item i of an edge (segment A + segment B) and its constant q
+// term, for the cost pass (the 4-node pass re-derives the segments in
+// setup_item). The table slot of w comes from beside the adjacency when
+// the graph has it, so the table read does not wait for a gather.
+struct ItemCost {
+  int32_t a, b;    // tests of segments A and B
+  int64_t qconst;  // constant q contribution
+  bool tabled;     // a co-degree table answered segment B
+};
+
+__device__ __forceinline__ ItemCost item_cost(const DevGraph& g, const EdgeCtx& c, int64_t i,
+                                              uint32_t tword, int32_t tbase, int lane,
+                                              bool need_q) {
+  ItemCost r{0, 0, 0, false};
+  if (i >= c.du) return r;
+  const int64_t p = c.bu + i;
+  const int32_t w = __ldg(g.col + p);
+  if (w == c.v) return r;
   const bool in_t = (tword >> lane) & 1u;
-  int64_t bw;
-  const int64_t dw = deg_of(g.row_ptr, w, &bw);
-  if (in_t && c.tmask != nullptr) {
-    // dense edge: the pairs among matrix members come from k_dense_pairs
-    if (table_slot(g, w) < 0) {
-      // rest: x over N(w), x in T, and (x has a matrix slot or x > w)
-      it.amode = 2;
-      it.rest_w = w;
-      it.a.it = g.col + bw;
-      it.a.its = g.col_hm + bw;
-      it.a.sl = T + c.toff;
-      it.a.slen = (int32_t)c.te;
-      it.a.cnt = (int32_t)dw;
-    }
-  }
-  if (in_t && c.tmask == nullptr) {
-    // segment A: |N(w) above w  cap  T above w|
-    // index of w in T: T entries in earlier chunks plus earlier lanes of this one
-    const int64_t iw = tbase + __popc(tword & ((1u << lane) - 1u));
-    const int64_t tg = c.te - iw - 1;
-    const int64_t upw = __ldg(g.up_ptr + w);
-    const int64_t dup = bw + dw - upw;
-    if (dup <= tg) {
-      it.a.it = g.col + upw;
-      it.a.its = g.col_hm != nullptr ? g.col_hm + upw : nullptr;
-      it.a.sl = T + c.toff + iw + 1;
-      it.a.svtx = -1;
-      it.a.slen = (int32_t)tg;
-      it.a.cnt = (int32_t)dup;
-    } else {
-      it.a.it = T + c.toff + iw + 1;
-      it.a.its = T_hm != nullptr ? T_hm + c.toff + iw + 1 : nullptr;
-      it.a.cnt = (int32_t)tg;
-      set_search(g, w, bw, dw, it.a);
-    }
-  }
+  const int64_t dw = __ldg(g.row_ptr + w + 1) - __ldg(g.row_ptr + w);
   if (in_t) {
-    if (need_q) {
-      // segment B: -(c(w, u) - 1)
-      it.bsign = -1;
-      const uint32_t tc = table_codeg(g, w, c.u);
-      it.tabled = tc != 0;
-      if (tc != 0) {
-        it.qconst = 1 - (int64_t)(tc - 1u);
-      } else {
-        it.qconst = 1;
-        codeg_segment(g, w, bw, dw, c.u, c.bu, c.du, it.b);
-      }
-    }
-  } else if (need_q) {
-    // segment B: c(w, v) - 1
-    it.bsign = 1;
-    const uint32_t tc = table_codeg(g, w, c.v);
-    it.tabled = tc != 0;
-    if (tc != 0) {
-      it.qconst = (int64_t)(tc - 1u) - 1;
+    if (c.tmask != nullptr) {
+      // dense edge: only a vertex without a matrix slot scans N(w) here
+      if (__ldg(g.col_hm + p) < 0) r.a = (int32_t)dw;
     } else {
-      it.qconst = -1;
-      codeg_segment(g, w, bw, dw, c.v, c.bv, c.dv, it.b);
+      // |N(w) above w cap T above w|: the shorter side is iterated
+      const int64_t iw = tbase + __popc(tword & ((1u << lane) - 1u));
+      const int64_t tg = c.te - iw - 1;
+      const int64_t dup = __ldg(g.row_ptr + w + 1) - __ldg(g.up_ptr + w);
+      r.a = (int32_t)min(dup, tg);
     }
   }
-  (void)need_k;
+  if (need_q) {
+    // segment B: -(c(w, u) - 1) for w in T, c(w, v) - 1 for w in S_u
+    const int32_t o = in_t ? c.u : c.v;
+    const int32_t sw = g.col_tb != nullptr ? __ldg(g.col_tb + p)
+                       : g.tb_slot != nullptr ? __ldg(g.tb_slot + w) : -1;
+    const uint32_t tc = table_codeg_s(g, w, sw, o);
+    r.tabled = tc != 0;
+    if (tc != 0) {
+      r.qconst = in_t ? 1 - (int64_t)(tc - 1u) : (int64_t)(tc - 1u) - 1;
+    } else {
+      r.qconst = in_t ? 1 : -1;
+      r.b = (int32_t)min(dw, in_t ? c.du : c.dv);
+    }
+  }
+  return r;
 }
 
 
@@ -653,13 +611,12 @@ __global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
   for (int64_t gi = g0; gi < g1; ++gi) {
     while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
     if (e != c.e) load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
-    Item it;
-    load_item(g, c, T, T_hm, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi), __ldg(tpre + gi),
-              lane, need_k, need_q, it);
-    const unsigned live = __ballot_sync(kFull, it.a.cnt + it.b.cnt > 0);
+    const ItemCost it = item_cost(g, c, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi),
+                                  __ldg(tpre + gi), lane, need_q);
+    const unsigned live = __ballot_sync(kFull, it.a + it.b > 0);
     const unsigned tabled = __ballot_sync(kFull, it.tabled);
     if (lane == 0) reinterpret_cast<uint2*>(cbits)[gi] = make_uint2(live, tabled);
-    int64_t cost = warp_sum<int64_t>((int64_t)it.a.cnt + it.b.cnt);
+    int64_t cost = warp_sum<int64_t>((int64_t)it.a + it.b);
     int64_t qc = warp_sum<int64_t>(it.qconst);
     if (lane == 0) {
       task_cnt[gi] = (cost + task_probes - 1) / task_probes;
@@ -707,10 +664,11 @@ static_assert(sizeof(SharedItem) == 64, "SharedItem size");
 
 // Item set-up of k_quad, out of line: it runs once per chunk and its
 // temporaries would otherwise raise the register count of the test loop.
-// Follows load_item, with the cost pass's hint in place of the table reads,
-// and stores each field to the lane's shared-memory descriptor as soon as
-// it is known (only the segments that have tests are written; a segment
-// with no tests is never read). Returns the item's test count.
+// Derives the same segments as item_cost counts, with the cost pass's hint
+// in place of the table reads, and stores each field to the lane's
+// shared-memory descriptor as soon as it is known (only the segments that
+// have tests are written; a segment with no tests is never read). Returns
+// the item's test count.
 __device__ __noinline__ int64_t setup_item(const DevGraph& g, const int2* __restrict__ uv,
                                            const unsigned long long* __restrict__ t,
                                            const int64_t* __restrict__ toff,
@@ -1190,6 +1148,7 @@ DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
     g.md_codeg = nullptr;
     g.dir_at = nullptr;
     g.dir = nullptr;
+    g.col_tb = nullptr;
   }
   return g;
 }

@@ -172,6 +172,16 @@ __global__ void k_col_slots(const int32_t* __restrict__ col, int64_t nnz,
     col_hm[p] = (int16_t)__ldg(slot + col[p]);
 }
 
+// col_tb[p] = table slot of col[p] (tb_slot encoding, mid rows included):
+// stored beside the adjacency so the cost pass reads it with the element
+// instead of gathering it per item before the table read.
+__global__ void k_col_tb(const int32_t* __restrict__ col, int64_t nnz,
+                         const int32_t* __restrict__ tb_slot, int32_t* __restrict__ col_tb) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x)
+    col_tb[p] = __ldg(tb_slot + col[p]);
+}
+
 // Sets the adjacency bits of rows that have a dense block. One warp per row.
 __global__ void k_dense_rows(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                              int64_t n, const int64_t* __restrict__ dm_row,
@@ -632,9 +642,9 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   // ---- mid x big co-degrees: rows for the highest-degree vertices below
   // the table (degree >= kMidMinDegree), columns for the top kBigMax table
   // vertices; whatever the budget has left
-  const double used = (double)n_bm * (double)words * 4.0 +
-                      (double)n_hm * (double)g->dev.hm_words * 4.0 +
-                      (double)g->dev.tb_count * (double)g->dev.tb_count * 4.0 + dir_bytes;
+  double used = (double)n_bm * (double)words * 4.0 +
+                (double)n_hm * (double)g->dev.hm_words * 4.0 +
+                (double)g->dev.tb_count * (double)g->dev.tb_count * 4.0 + dir_bytes;
   const int64_t d_hi = d_tb < 65536 ? d_tb : 65536;
   if (g->dev.tb_count > 1 && d_hi > kMidMinDegree && (double)budget > used) {
     int64_t d_bg = 0, n_bg = 0;
@@ -671,8 +681,21 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
         g->dev.md_codeg = g->md_codeg;
         g->dev.md_count = rows;
         g->dev.bg_count = n_bg;
+        used += (double)nwords * 4.0;
       }
     }
+  }
+  // ---- table slot of every adjacency entry (cost pass), if the budget has
+  // room left after everything above
+  const size_t tb_bytes_col = sizeof(int32_t) * (size_t)g->dev.nnz;
+  if (g->dev.tb_count > 1 && g->dev.nnz > 0 && (double)budget >= used + (double)tb_bytes_col) {
+    cudaError_t ae = cudaMalloc(&g->col_tb, tb_bytes_col);
+    if (ae != cudaSuccess) return cuda_fail(ae, "adjacency table slots", __FILE__, __LINE__);
+    k_col_tb<<<grid_for(g->dev.nnz, 256, 8), 256, 0, stream>>>(g->dev.col, g->dev.nnz,
+                                                               g->tb_slot, g->col_tb);
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "adjacency table slots", __FILE__, __LINE__);
+    g->dev.col_tb = g->col_tb;
   }
   return GS_OK;
 }
@@ -837,6 +860,7 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->md_codeg);
   cudaFree(g->dir_at);
   cudaFree(g->dir);
+  cudaFree(g->col_tb);
   delete g;
   return GS_OK;
 }
