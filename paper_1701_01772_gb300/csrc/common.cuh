@@ -57,8 +57,13 @@ struct DevGraph {
   int64_t bm_count;
   // co-degree table |N(x) cap N(y)| for the highest-degree vertices
   const int32_t* tb_slot;   // [n] table slot of v, -1 if none, <= -2 mid row (NULL if no table)
-  const uint32_t* tb_codeg; // [tb_count][tb_count]
+  const uint16_t* tb_codeg; // upper triangle, entry tb_index(lo, hi); 0xFFFF: see below
   int64_t tb_count;
+  // pairs of "giant" table hubs (degree >= 65,536) have 32-bit co-degrees:
+  // tb_giant_codeg[tb_giant[lo]][tb_giant[hi]] (tb_giant NULL if none)
+  const int32_t* tb_giant;
+  const uint32_t* tb_giant_codeg;
+  int64_t tb_giants;
   // co-degrees between "mid" vertices (degree below the table's threshold,
   // tb_slot[a] = -2 - row) and the bg_count "big" table vertices
   // (bg_slot[b] >= 0): md_codeg[row][bg_slot[b]], 16-bit entries
@@ -89,6 +94,12 @@ struct DevGraph {
   // beside the adjacency (NULL if absent): tb_slot[col[p]]
   const int32_t* col_tb;
 };
+
+// Entry of the table pair (lo, hi), lo < hi < n, in the upper triangle
+// stored row by row.
+__host__ __device__ __forceinline__ int64_t tb_index(int64_t lo, int64_t hi, int64_t n) {
+  return lo * (2 * n - lo - 1) / 2 + (hi - lo - 1);
+}
 
 // log2 of the number of directory buckets of a vertex of degree d >= 2:
 // floor(log2 d) - 1, so a bucket holds 2 to 4 neighbours on average when
@@ -125,11 +136,6 @@ __device__ __forceinline__ uint4 ld_keep4(const uint4* a) {
   asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
       : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
       : "l"(a), "l"(l2_policy_keep()));
-  return v;
-}
-__device__ __forceinline__ uint32_t ld_once(const uint32_t* a) {
-  uint32_t v;
-  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(l2_policy_once()));
   return v;
 }
 __device__ __forceinline__ uint16_t ld_once16(const uint16_t* a) {
@@ -230,7 +236,7 @@ struct gs_graph {
   int32_t* bm_slot;
   uint32_t* bm_bits;
   int32_t* tb_slot;
-  uint32_t* tb_codeg;
+  uint16_t* tb_codeg;
   int32_t* hm_slot;
   uint32_t* hm_bits;
   int16_t* col_hm;
@@ -242,6 +248,8 @@ struct gs_graph {
   int64_t* dir_at;
   uint32_t* dir;
   int32_t* col_tb;
+  int32_t* tb_giant;
+  uint32_t* tb_giant_codeg;
 };
 
 namespace gs {

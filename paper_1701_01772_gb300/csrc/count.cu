@@ -469,8 +469,14 @@ __device__ __forceinline__ uint32_t table_codeg_s(const DevGraph& g, int32_t a, 
   if (g.tb_slot == nullptr) return 0;
   const int32_t sb = __ldg(g.tb_slot + b);
   if (sa >= 0 && sb >= 0) {
-    int32_t lo = min(sa, sb), hi = max(sa, sb);
-    return ld_once(g.tb_codeg + (int64_t)lo * g.tb_count + hi) + 1u;
+    const int32_t lo = min(sa, sb), hi = max(sa, sb);
+    const uint16_t c = ld_once16(g.tb_codeg + tb_index(lo, hi, g.tb_count));
+    if (c != 0xFFFFu) return (uint32_t)c + 1u;
+    if (g.tb_giant != nullptr) {  // a pair of giants
+      const int32_t ga = __ldg(g.tb_giant + lo), gb = __ldg(g.tb_giant + hi);
+      if (ga >= 0 && gb >= 0) return __ldg(g.tb_giant_codeg + (int64_t)ga * g.tb_giants + gb) + 1u;
+    }
+    return 0;  // a true co-degree of 65,535 is left to the tests
   }
   if (g.md_codeg != nullptr && (sa < -1 || sb < -1) && (sa >= 0 || sb >= 0)) {
     // one mid vertex (slot -2 - row), one table vertex that may be big
@@ -1140,6 +1146,7 @@ DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
     g.bm_count = 0;
     g.tb_slot = nullptr;
     g.tb_codeg = nullptr;
+    g.tb_giant = nullptr;
     g.tb_count = 0;
     g.hm_slot = nullptr;
     g.hm_bits = nullptr;

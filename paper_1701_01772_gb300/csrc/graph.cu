@@ -14,8 +14,10 @@ namespace gs {
 constexpr int64_t kHubMinDegree = 64;
 // Vertices of at least this degree (and no bitmap) get a bucket directory.
 constexpr int64_t kDirMinDegree = 16;
-// Mid rows of the mid x big co-degree table start at this degree.
-constexpr int64_t kMidMinDegree = 8;
+// Mid rows of the mid x big co-degree table start at this degree, and their
+// build adds at most kMidWorkMax wedge increments (higher-degree rows first).
+constexpr int64_t kMidMinDegree = 2;
+constexpr unsigned long long kMidWorkMax = 80000000000ull;
 
 // ------------------------------------------------------------- validation
 // One warp per row (grid-stride). Checks the simple-graph conditions of
@@ -242,6 +244,30 @@ __global__ void __launch_bounds__(256) k_mid_big_pairs(const int64_t* __restrict
   }
 }
 
+// Build work of the mid x big table for mid rows of degree [lo, hi) and big
+// columns of degree >= big: sum over x of (mid neighbours) x (big
+// neighbours). One warp per vertex.
+__global__ void k_mid_big_work(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               int64_t n, int64_t lo, int64_t hi, int64_t big,
+                               unsigned long long* __restrict__ total) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  unsigned long long acc = 0;
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    unsigned m = 0, b = 0;
+    for (int64_t p = row_ptr[x] + lane; p < row_ptr[x + 1]; p += 32) {
+      const int32_t y = col[p];
+      const int64_t d = __ldg(row_ptr + y + 1) - __ldg(row_ptr + y);
+      m += d >= lo && d < hi;
+      b += d >= big;
+    }
+    m = __reduce_add_sync(0xffffffffu, m);
+    b = __reduce_add_sync(0xffffffffu, b);
+    acc += (unsigned long long)m * b;
+  }
+  if (lane == 0 && acc) atomicAdd(total, acc);
+}
+
 // Marks mid vertices (lo <= degree < hi, no table slot) and big vertices
 // (table vertices of degree >= big).
 __global__ void k_flag_mid(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ tb_slot,
@@ -376,16 +402,72 @@ __global__ void k_hub_nbr_fill(const int64_t* __restrict__ row_ptr, const int32_
 }
 
 // One thread per list entry i of vertex x: adds 1 to c(L[i], L[j]) for every
-// later entry j, i.e. x is a common neighbour of that hub pair.
+// later entry j, i.e. x is a common neighbour of that hub pair (L is in
+// increasing slot order, so L[i] < L[j]). Entries are 16 bits wide, two to a
+// 32-bit word, in the upper triangle (tb_index). A co-degree is at most the
+// smaller degree, so it stays below 65,536 unless both hubs are "giants"
+// (degree >= 65,536, giant[slot] = index among them, else -1): those pairs
+// go to a 32-bit giant x giant table instead, and their 16-bit entry is
+// marked 0xFFFF afterwards.
 __global__ void k_codeg_pairs(const int32_t* __restrict__ lists, const int32_t* __restrict__ owner,
                               const int64_t* __restrict__ off, int64_t total, int64_t count,
-                              uint32_t* __restrict__ table) {
+                              const int32_t* __restrict__ giant, int64_t giants,
+                              uint32_t* __restrict__ giant_codeg, uint32_t* __restrict__ words) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t x = owner[i];
-    int64_t end = off[x + 1];
-    uint32_t* row = table + (int64_t)lists[i] * count;
-    for (int64_t j = i + 1; j < end; ++j) atomicAdd(row + __ldg(lists + j), 1u);
+    const int32_t x = owner[i];
+    const int64_t end = off[x + 1];
+    const int64_t a = lists[i];
+    const int32_t ga = giant != nullptr ? giant[a] : -1;
+    const int64_t base = a * (2 * count - a - 1) / 2 - a - 1;  // tb_index(a, b) = base + b
+    for (int64_t j = i + 1; j < end; ++j) {
+      const int64_t b = __ldg(lists + j);
+      if (ga >= 0) {
+        const int32_t gb = giant[b];
+        if (gb >= 0) {
+          atomicAdd(giant_codeg + (int64_t)ga * giants + gb, 1u);
+          continue;
+        }
+      }
+      const int64_t at = base + b;
+      atomicAdd(words + (at >> 1), 1u << (16 * (int)(at & 1)));
+    }
+  }
+}
+
+// flag[s] = 1 when the table hub with slot s has degree >= 65,536.
+__global__ void k_giant_flags(const int64_t* __restrict__ row_ptr,
+                              const int32_t* __restrict__ tb_slot, int64_t n,
+                              int64_t* __restrict__ flag) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t sl = tb_slot[v];
+    if (sl >= 0) flag[sl] = (row_ptr[v + 1] - row_ptr[v]) >= 65536;
+  }
+}
+
+// giant[s] = index of slot s among the giants (exclusive scan of the flags),
+// or -1.
+__global__ void k_giant_index(const int64_t* __restrict__ flag_scan, int64_t count,
+                              int32_t* __restrict__ giant) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < count;
+       s += (int64_t)gridDim.x * blockDim.x)
+    giant[s] = flag_scan[s + 1] > flag_scan[s] ? (int32_t)flag_scan[s] : -1;
+}
+
+// Marks the 16-bit entries of giant pairs 0xFFFF (answered by the giant
+// table). One thread per slot a; only giant rows do work.
+__global__ void k_mark_giant_pairs(const int32_t* __restrict__ giant, int64_t count,
+                                   uint32_t* __restrict__ words) {
+  for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < count;
+       a += (int64_t)gridDim.x * blockDim.x) {
+    if (giant[a] < 0) continue;
+    const int64_t base = a * (2 * count - a - 1) / 2 - a - 1;
+    for (int64_t b = a + 1; b < count; ++b)
+      if (giant[b] >= 0) {
+        const int64_t at = base + b;
+        atomicOr(words + (at >> 1), 0xFFFFu << (16 * (int)(at & 1)));
+      }
   }
 }
 
@@ -600,7 +682,8 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   // ---- co-degree table
   const double tb_bytes =
       (double)budget - share - (double)hm_cap * (double)hm_cap / 8.0 - dir_bytes;
-  int64_t tb_cap = tb_bytes > 0 ? (int64_t)sqrt(tb_bytes / 4.0) : 0;
+  // n (n - 1) / 2 entries of 2 bytes
+  int64_t tb_cap = tb_bytes > 0 ? (int64_t)sqrt(tb_bytes) : 0;
   if (tb_cap > 65535) tb_cap = 65535;
   int64_t d_tb = 0, n_tb = 0;
   if (tb_cap > 1) {
@@ -609,8 +692,27 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       int32_t* hubs = nullptr;
       GS_TRY(assign(d_tb, &g->tb_slot, &hubs, n_tb));
       cudaFree(hubs);
-      GS_CUDA(cudaMalloc(&g->tb_codeg, sizeof(uint32_t) * (size_t)(n_tb * n_tb)));
-      GS_CUDA(cudaMemsetAsync(g->tb_codeg, 0, sizeof(uint32_t) * (size_t)(n_tb * n_tb), stream));
+      const int64_t tb_words = (n_tb * (n_tb - 1) / 2 + 1) / 2;
+      GS_CUDA(cudaMalloc(&g->tb_codeg, sizeof(uint32_t) * (size_t)tb_words));
+      GS_CUDA(cudaMemsetAsync(g->tb_codeg, 0, sizeof(uint32_t) * (size_t)tb_words, stream));
+      int64_t giants = 0;
+      if (g->max_degree >= 65536) {
+        // giant table hubs: slot -> index, and their 32-bit pair table
+        GS_CUDA(cudaMemsetAsync(flag, 0, sizeof(int64_t) * (size_t)(n_tb + 1), stream));
+        k_giant_flags<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->tb_slot, n,
+                                                               flag);
+        GS_TRY(exclusive_scan_i64(flag, flag, n_tb, tmp, stream));
+        GS_CUDA(cudaMemcpyAsync(&giants, flag + n_tb, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                                stream));
+        GS_CUDA(cudaStreamSynchronize(stream));
+        if (giants > 0) {
+          GS_CUDA(cudaMalloc(&g->tb_giant, sizeof(int32_t) * (size_t)n_tb));
+          GS_CUDA(cudaMalloc(&g->tb_giant_codeg, sizeof(uint32_t) * (size_t)(giants * giants)));
+          GS_CUDA(cudaMemsetAsync(g->tb_giant_codeg, 0,
+                                  sizeof(uint32_t) * (size_t)(giants * giants), stream));
+          k_giant_index<<<grid_for(n_tb, 256, 8), 256, 0, stream>>>(flag, n_tb, g->tb_giant);
+        }
+      }
       // per-vertex lists of table-hub neighbours
       k_hub_nbr_count<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.col,
                                                                     g->tb_slot, n, flag);
@@ -628,8 +730,11 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       }
       k_hub_nbr_fill<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(
           g->dev.row_ptr, g->dev.col, g->tb_slot, n, flag, lists, owner);
-      k_codeg_pairs<<<grid_for(total, 256, 8), 256, 0, stream>>>(lists, owner, flag, total, n_tb,
-                                                                 g->tb_codeg);
+      uint32_t* tb_w = reinterpret_cast<uint32_t*>(g->tb_codeg);
+      k_codeg_pairs<<<grid_for(total, 256, 8), 256, 0, stream>>>(
+          lists, owner, flag, total, n_tb, g->tb_giant, giants, g->tb_giant_codeg, tb_w);
+      if (g->tb_giant != nullptr)
+        k_mark_giant_pairs<<<grid_for(n_tb, 256, 8), 256, 0, stream>>>(g->tb_giant, n_tb, tb_w);
       cudaError_t e = cudaStreamSynchronize(stream);
       cudaFree(lists);
       cudaFree(owner);
@@ -637,6 +742,9 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       g->dev.tb_slot = g->tb_slot;
       g->dev.tb_codeg = g->tb_codeg;
       g->dev.tb_count = n_tb;
+      g->dev.tb_giant = g->tb_giant;
+      g->dev.tb_giant_codeg = g->tb_giant_codeg;
+      g->dev.tb_giants = giants;
     }
   }
   // ---- mid x big co-degrees: rows for the highest-degree vertices below
@@ -644,7 +752,7 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   // vertices; whatever the budget has left
   double used = (double)n_bm * (double)words * 4.0 +
                 (double)n_hm * (double)g->dev.hm_words * 4.0 +
-                (double)g->dev.tb_count * (double)g->dev.tb_count * 4.0 + dir_bytes;
+                (double)g->dev.tb_count * (double)g->dev.tb_count + dir_bytes;
   const int64_t d_hi = d_tb < 65536 ? d_tb : 65536;
   if (g->dev.tb_count > 1 && d_hi > kMidMinDegree && (double)budget > used) {
     int64_t d_bg = 0, n_bg = 0;
@@ -655,6 +763,28 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     int64_t d_md = 0, n_ge = 0;
     if (md_cap > 0)
       GS_TRY(hub_threshold(g, md_cap + g->dev.tb_count, kMidMinDegree, d_cnt, stream, &d_md, &n_ge));
+    // and, raising d_md if needed, at most kMidWorkMax build increments
+    auto work_at = [&](int64_t lo, unsigned long long* w) -> gs_status {
+      GS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream));
+      k_mid_big_work<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.col, n,
+                                                                   lo, d_hi, d_bg, d_cnt);
+      GS_CUDA(cudaMemcpyAsync(w, d_cnt, sizeof(*w), cudaMemcpyDeviceToHost, stream));
+      GS_CUDA(cudaStreamSynchronize(stream));
+      return GS_OK;
+    };
+    if (md_cap > 0 && n_bg > 0 && d_md < d_hi) {
+      unsigned long long w = 0;
+      GS_TRY(work_at(d_md, &w));
+      if (w > kMidWorkMax) {
+        int64_t lo = d_md, hi = d_hi;  // work(lo) too large, work(hi) = 0
+        while (hi - lo > 1) {
+          const int64_t mid = lo + (hi - lo) / 2;
+          GS_TRY(work_at(mid, &w));
+          if (w <= kMidWorkMax) hi = mid; else lo = mid;
+        }
+        d_md = hi;
+      }
+    }
     if (md_cap > 0 && d_md < d_hi) {
       int32_t* hubs = nullptr;
       GS_TRY(assign(d_bg, &g->bg_slot, &hubs, n_bg));
@@ -861,6 +991,8 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->dir_at);
   cudaFree(g->dir);
   cudaFree(g->col_tb);
+  cudaFree(g->tb_giant);
+  cudaFree(g->tb_giant_codeg);
   delete g;
   return GS_OK;
 }
