@@ -352,3 +352,22 @@ def test_dense_clique_mode_mixed_t_against_oracle():
     g.close()
     _full_check(rp, col, sample)
     _full_check(rp, col, sample, hub_budget=NO_HUBS)
+
+
+# ------------------------------------------------------------------ giant hubs
+
+def test_giant_hub_pair_codegree_above_16_bits():
+    """K_{2,70000}: the two hubs share 70,000 neighbours, more than a 16-bit
+    co-degree entry holds, so c(a, b) must come from the 32-bit table of
+    giant pairs; every sampled leaf edge (x, b) has w = a in S_x and
+    q = c(a, b) - 1."""
+    n = 70000
+    leaves = np.arange(2, n + 2, dtype=np.int64)
+    a = np.concatenate([np.zeros(n, dtype=np.int64), np.ones(n, dtype=np.int64)])
+    b = np.concatenate([leaves, leaves])
+    rp, col = synth.from_pairs(n + 2, a, b)
+    g = _graph(rp, col)
+    assert g.info["table_hubs"] == 2
+    g.close()
+    sample = synth.explicit_sample(rp, col, 0.002, seed=5)
+    _full_check(rp, col, sample)
