@@ -12,8 +12,9 @@
 // c(x, y) = |N(x) cap N(y)|:
 //   q = sum_{w in S_u} (c(w, v) - 1) - sum_{r in T} (c(r, u) - 1) + 2k
 // (sum_{w in S_u} |N(w) cap T| counted from the T side). Co-degrees of hub
-// pairs come from a table built at registration; the rest are computed by
-// membership tests (see the item comment below).
+// pairs, and of mid-degree x top-hub pairs, come from tables built at
+// registration; the rest are computed by membership tests (see the item
+// comment below).
 //
 // GPU structure (all work is flattened so that per-edge cost skew -- power
 // law degrees -- does not serialise on one warp):
@@ -32,13 +33,15 @@
 //   cost     per chunk of 32 positions (items w = N(u)[i]): membership-test
 //            count of each item (iterate the shorter list, test in the
 //            longer); constant terms (the -1s, table co-degrees) added
-//            directly.
+//            directly; two ballots per chunk (items with tests, items a table
+//            answered) for the 4-node pass.
 //   quad     chunks are cut into tasks of task_probes tests; tasks are split
 //            evenly over all warps; inside a task lanes take consecutive
 //            tests (two per lane per iteration) and find their item by a
-//            search over the warp's scanned costs (load-balanced search). In
-//            a dense edge a "test" of a hub member of T is one 32-bit word of
-//            its matrix row ANDed with the T mask.
+//            search over the warp's scanned costs (load-balanced search).
+//   dense    in a dense edge the pairs of hub members of T are counted by
+//            k_dense_pairs: matrix rows ANDed with the T mask, 128 bits at a
+//            time, in work units of kDenseUnit T entries.
 //   fold     per edge numerators N_i in 128-bit, block partial sums, one
 //            final fixed-order pass (or per-segment limb sums, k_fold_seg).
 #include <string.h>
