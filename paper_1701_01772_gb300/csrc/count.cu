@@ -418,16 +418,15 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
 //                adjacency, tested in the longer; q -= 1 / q += 1 per hit.
 //                Skipped (constant term instead) when the co-degree table
 //                holds c(w, o).
+// The searched side is a vertex y's adjacency (set_search) or a T list.
 struct Seg {
-  const int32_t* it;    // iterated list
-  const int16_t* its;   // matrix slots of the iterated list's entries, or NULL
+  const int32_t* it;    // iterated list (its matrix slots lie beside it)
   const int32_t* sl;    // searched list
-  int32_t svtx;         // vertex whose adjacency sl is (bitmap-capable), or -1
-  int32_t sslot;        // matrix slot of svtx, or -1
-  int32_t sbm;          // bitmap slot of svtx (>= 0), -2 - s when svtx has a
+  int32_t sslot;        // matrix slot of y, or -1
+  int32_t sbm;          // bitmap slot of y (>= 0), -2 - s when y has a
                         // bucket directory with shift s, else -1
   int32_t slen;         // length of sl, or (sbm < -1) the first entry of
-                        // svtx's directory in g.dir
+                        // y's directory in g.dir
   int32_t cnt;          // number of tests
 };
 
@@ -505,7 +504,6 @@ constexpr int32_t kDenseRow = -3;
 // dense row, the hub-pair matrix, its bitmap, or a halving search.
 __device__ __forceinline__ void set_search(const DevGraph& g, int32_t y, int64_t by, int64_t dy,
                                            Seg& s) {
-  s.svtx = y;
   s.sl = g.col + by;
   s.slen = (int32_t)dy;
   if (g.dm_row != nullptr) {
@@ -533,12 +531,10 @@ __device__ __forceinline__ void codeg_segment(const DevGraph& g, int32_t w, int6
                                               int32_t o, int64_t bo, int64_t dob, Seg& s) {
   if (dw <= dob) {
     s.it = g.col + bw;
-    s.its = g.col_hm != nullptr ? g.col_hm + bw : nullptr;
     s.cnt = (int32_t)dw;
     set_search(g, o, bo, dob, s);
   } else {
     s.it = g.col + bo;
-    s.its = g.col_hm != nullptr ? g.col_hm + bo : nullptr;
     s.cnt = (int32_t)dob;
     set_search(g, w, bw, dw, s);
   }
@@ -600,9 +596,8 @@ __global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
     k_chunk_cost(DevGraph g, const int2* __restrict__ uv, const int64_t* __restrict__ off, int64_t K,
                  const unsigned long long* __restrict__ t, const int64_t* __restrict__ toff,
                  const uint32_t* __restrict__ tbits, const int32_t* __restrict__ tpre,
-                 const int32_t* __restrict__ T, const int16_t* __restrict__ T_hm,
                  const int32_t* __restrict__ mask_idx, const uint32_t* __restrict__ tmask,
-                 int need_k, int need_q, int64_t task_probes, int64_t* __restrict__ task_cnt,
+                 int need_q, int64_t task_probes, int64_t* __restrict__ task_cnt,
                  uint32_t* __restrict__ cbits, unsigned long long* __restrict__ q,
                  unsigned long long* __restrict__ stats) {
   unsigned long long tests = 0;
@@ -1301,11 +1296,11 @@ int64_t launch_dense(const DevGraph& g, bool need_q, CountBufs& b, cudaStream_t 
 // Chunk costs and the task scan. No host sync.
 int64_t launch_cost(const DevGraph& g, bool need_k, bool need_q, const Tuning& tu, CountBufs& b,
                     cudaStream_t stream) {
-  int16_t* T_hm = g.col_hm != nullptr ? b.T_hm : nullptr;
+  (void)need_k;  // every item's segment A feeds both k and q
   const int32_t* mi = g.col_hm != nullptr ? b.mask_idx : nullptr;
   k_chunk_cost<<<sm_count() * kCostBlocksPerSm, kThreads, 0, stream>>>(
-      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.tpre, b.T, T_hm, mi, b.tmask, need_k, need_q,
-      tu.task_probes, b.task_off, b.cbits, b.q, b.stats);
+      g, b.uv, b.off, b.K, b.t, b.toff, b.tbits, b.tpre, mi, b.tmask, need_q, tu.task_probes,
+      b.task_off, b.cbits, b.q, b.stats);
   exclusive_scan_i64(b.task_off, b.task_off, b.groups, b.tmp1, stream);
   return 4;
 }
