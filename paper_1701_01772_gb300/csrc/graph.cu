@@ -206,41 +206,47 @@ __global__ void k_dense_rows(const int64_t* __restrict__ row_ptr, const int32_t*
 // neighbour of w and h). Entries are 16 bits wide, updated through the 32-bit
 // word that holds them; a co-degree is below the mid vertex's degree
 // (< 65536), so no carry reaches the neighbouring entry. One warp per vertex;
-// x's big neighbours (at most kBigMax) are gathered in shared memory.
-constexpr int kBigMax = 1024;
+// x's big neighbours are gathered in shared memory kBigChunk at a time (the
+// table has at most kBigMax columns).
+constexpr int kBigMax = 4096;
+constexpr int kBigChunk = 1024;
 __global__ void __launch_bounds__(256) k_mid_big_pairs(const int64_t* __restrict__ row_ptr,
                                                        const int32_t* __restrict__ col, int64_t n,
                                                        const int32_t* __restrict__ tb_slot,
                                                        const int32_t* __restrict__ bg_slot,
                                                        int64_t bg_count,
                                                        uint32_t* __restrict__ words) {
-  __shared__ int32_t bigs[8][kBigMax];
+  __shared__ int32_t bigs[8][kBigChunk];
   const int lane = threadIdx.x & 31;
   int32_t* mine = bigs[threadIdx.x >> 5];
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
     const int64_t s = row_ptr[x], e = row_ptr[x + 1];
-    int nb = 0;
-    for (int64_t p0 = s; p0 < e; p0 += 32) {
-      const int64_t p = p0 + lane;
-      const int32_t c = p < e ? __ldg(bg_slot + col[p]) : -1;
-      const unsigned ball = __ballot_sync(0xffffffffu, c >= 0);
-      if (c >= 0) mine[nb + __popc(ball & ((1u << lane) - 1u))] = c;
-      nb += __popc(ball);
-    }
-    __syncwarp();
-    if (nb > 0) {
-      for (int64_t p = s + lane; p < e; p += 32) {
-        const int32_t r = __ldg(tb_slot + col[p]);
-        if (r > -2) continue;
-        const int64_t base = (int64_t)(-2 - r) * bg_count;
-        for (int i = 0; i < nb; ++i) {
-          const int64_t at = base + mine[i];
-          atomicAdd(words + (at >> 1), 1u << (16 * (int)(at & 1)));
+    int64_t p0 = s;  // next adjacency entry to scan for big neighbours
+    while (p0 < e) {
+      // gather big neighbours until the chunk could overflow on the next 32
+      int nb = 0;
+      for (; p0 < e && nb <= kBigChunk - 32; p0 += 32) {
+        const int64_t p = p0 + lane;
+        const int32_t c = p < e ? __ldg(bg_slot + col[p]) : -1;
+        const unsigned ball = __ballot_sync(0xffffffffu, c >= 0);
+        if (c >= 0) mine[nb + __popc(ball & ((1u << lane) - 1u))] = c;
+        nb += __popc(ball);
+      }
+      __syncwarp();
+      if (nb > 0) {
+        for (int64_t p = s + lane; p < e; p += 32) {
+          const int32_t r = __ldg(tb_slot + col[p]);
+          if (r > -2) continue;
+          const int64_t base = (int64_t)(-2 - r) * bg_count;
+          for (int i = 0; i < nb; ++i) {
+            const int64_t at = base + mine[i];
+            atomicAdd(words + (at >> 1), 1u << (16 * (int)(at & 1)));
+          }
         }
       }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -748,16 +754,34 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     }
   }
   // ---- mid x big co-degrees: rows for the highest-degree vertices below
-  // the table (degree >= kMidMinDegree), columns for the top kBigMax table
+  // the table (degree >= kMidMinDegree), columns for the top 1024-4096 table
   // vertices; whatever the budget has left
   double used = (double)n_bm * (double)words * 4.0 +
                 (double)n_hm * (double)g->dev.hm_words * 4.0 +
                 (double)g->dev.tb_count * (double)g->dev.tb_count + dir_bytes;
   const int64_t d_hi = d_tb < 65536 ? d_tb : 65536;
   if (g->dev.tb_count > 1 && d_hi > kMidMinDegree && (double)budget > used) {
+    // columns: the widest of 4096 / 2048 / 1024 top table vertices for which
+    // every vertex of degree [kMidMinDegree, d_hi) gets a row in the budget
+    auto count_ge = [&](int64_t d, int64_t* c) -> gs_status {
+      GS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream));
+      k_count_deg_ge<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, n, d, d_cnt);
+      unsigned long long h = 0;
+      GS_CUDA(cudaMemcpyAsync(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, stream));
+      GS_CUDA(cudaStreamSynchronize(stream));
+      *c = (int64_t)h;
+      return GS_OK;
+    };
+    int64_t c_lo = 0, c_hi = 0;
+    GS_TRY(count_ge(kMidMinDegree, &c_lo));
+    GS_TRY(count_ge(d_hi, &c_hi));
+    const double rows_all = (double)(c_lo - c_hi);
     int64_t d_bg = 0, n_bg = 0;
-    const int64_t bg_cap = g->dev.tb_count < kBigMax ? g->dev.tb_count : kBigMax;
-    GS_TRY(hub_threshold(g, bg_cap, d_tb, d_cnt, stream, &d_bg, &n_bg));
+    for (int64_t cols = kBigMax; cols >= kBigChunk; cols /= 2) {
+      const int64_t bg_cap = g->dev.tb_count < cols ? g->dev.tb_count : cols;
+      GS_TRY(hub_threshold(g, bg_cap, d_tb, d_cnt, stream, &d_bg, &n_bg));
+      if (rows_all * 2.0 * (double)n_bg <= (double)budget - used) break;
+    }
     const int64_t md_cap = n_bg > 0 ? (int64_t)(((double)budget - used) / (2.0 * (double)n_bg)) : 0;
     // lowest degree d_md >= kMidMinDegree with at most md_cap mid vertices
     int64_t d_md = 0, n_ge = 0;
