@@ -70,11 +70,12 @@ def load_peaks():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the 4-node kernel's source with comments and blank space
-    removed, so that a comment edit does not invalidate recorded counters."""
+    """Hash of the 4-node kernels' source and of the index they read (its
+    build in graph.cu), with comments and blank space removed, so that a
+    comment edit does not invalidate recorded counters."""
     import re
     h = hashlib.sha256()
-    for name in ("count.cu", "common.cuh"):
+    for name in ("count.cu", "common.cuh", "graph.cu"):
         with open(os.path.join(ROOT, "paper_1701_01772_gb300", "csrc", name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
