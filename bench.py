@@ -167,6 +167,15 @@ def percentile(xs, p):
 
 # ------------------------------------------------------------------ GPU arm
 
+def incidences_from_numerators(n: dict) -> int:
+    """Connected 3- and 4-node graphlet incidences of the counted edges,
+    sum over e of t + a + b + k + C(t,2) + t(a+b) + q + C(a,2) + C(b,2) + ab,
+    from the exact numerator sums {i: sum N_i}: N3 + N4 + 2 N7 + 5 N8
+    + (3 N9 + N11) / 2 + 2 N10 + N12, where per edge
+    (3 N9 + N11) / 2 = t(a+b) - 4 N8 + C(a,2) + C(b,2) is an integer."""
+    return (n[3] + n[4] + 2 * n[7] + 5 * n[8] + (3 * n[9] + n[11]) // 2 + 2 * n[10] + n[12])
+
+
 def run_gpu(args, rank, world, device):
     import numpy as np
     import torch
@@ -191,13 +200,7 @@ def run_gpu(args, rank, world, device):
         return (rank * 1_000_003 + step * 101 + fi * 7 + 1) & (2**63 - 1)
 
     def incidences(sums) -> int:
-        """Connected 3- and 4-node graphlet incidences of the counted edges,
-        sum over e of t + a + b + k + C(t,2) + t(a+b) + q + C(a,2) + C(b,2) + ab,
-        from the exact numerator sums (N3 + N4 + 2 N7 + 5 N8 + 3/2 N9 + 2 N10
-        + 1/2 N11 + N12; N9 + N11 is even)."""
-        n = {gid: v[0] for gid, v in sums.sums().items()}
-        return (n[3] + n[4] + 2 * n[7] + 5 * n[8] + (3 * n[9] + n[11]) // 2 + 2 * n[10]
-                + n[12])
+        return incidences_from_numerators({gid: v[0] for gid, v in sums.sums().items()})
 
     def one_step(step, record):
         """Sample + count + estimate for every fraction; returns (edges, per-call ms)."""
