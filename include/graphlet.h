@@ -75,6 +75,7 @@ enum {
 #define GS_F_EXACT 2u           /* every edge sampled: exact[] is valid, V = 0 */
 #define GS_F_VAR_UNDEFINED 4u   /* fewer than 2 sampled edges: V, lb, ub are NaN */
 #define GS_F_OVERFLOW 8u        /* exact count does not fit uint64 */
+#define GS_F_VAR_OVERFLOW 16u   /* a sum of squares exceeded 128 bits: V, lb, ub are NaN */
 
 /* Exact integer sums over the sampled edges J (Sec. 2.3, Alg. 2 accumulators).
  * For each graphlet i the per-edge numerator N_i(e) is the integer with
@@ -235,6 +236,57 @@ gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_per_sm, int q
 
 /* Host output: statistics of the last gs_count that used `ws`. */
 gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
+
+/* ---- disconnected graphlets (G5, G6, G13-G17) --------------------------
+ * Sec. 2.3's estimators of the disconnected 3- and 4-node graphlets, read
+ * with corrected terms (the printed block swaps C13 with C14 and C15 with
+ * C16 and its weights do not match): with R_e = n - 2 - t - a - b (vertices
+ * adjacent to neither end of e) and C16_e = m - d_u - d_v + 1 (edges
+ * touching neither end), X5 = sigma sum R, X13 = (sigma sum tR - X9) / 3,
+ * X14 = sigma sum (a+b)R / 2 - X12, X15 = sigma sum C16 / 2 - 3 X7 - 2 X8 -
+ * X9 - 2 X10 - X12, X16 = sigma sum C(R,2) - 2 X15, X6 = C(n,3) - X3 - X4 -
+ * X5, X17 = C(n,4) - (X7 + ... + X16); sigma = m / k. Each is a linear
+ * expansion estimator (plus a constant for X6, X17) of one per-edge integer
+ * numerator, which these calls fold exactly:
+ *   N5 = R                         D = 1
+ *   N6 = 2t + 3(a+b) + 6R          D = 6    X6 = C(n,3) - sigma sum N6 / 6
+ *   N13 = 2tR - N9                 D = 6
+ *   N14 = (a+b)R - 2 N12           D = 2
+ *   N15 = C16 - N7 - 4N8 - N9 - N10 - 2 N12             D = 2
+ *   N16 = C(R,2) - N15             D = 1
+ *   N17 = 2N7 + 12N8 + 6N9 + 3N10 + 2N11 + 12N12 + 2N13 + 6N14 + 6N15 + 12N16
+ *                                  D = 12   X17 = C(n,4) - sigma sum N17 / 12
+ * (N7..N12 as in gs_estimate). The paper has no variance for these either;
+ * gs_estimate's SRSWOR reading is applied to each numerator. */
+typedef struct {
+  int64_t k, m, n;      /* sampled edges, graph edges, graph vertices */
+  uint32_t overflow;    /* bit i: sum of squares i exceeded 128 bits (variance NaN) */
+  uint32_t reserved;
+  uint64_t sum[7][2];   /* order (5, 6, 13, 14, 15, 16, 17), 128-bit two's complement */
+  uint64_t sumsq[7][2]; /* sum N_i^2, 128-bit unsigned */
+} gs_sums_disc;
+
+typedef struct {
+  double x[7], var[7], lb[7], ub[7];  /* order (5, 6, 13, 14, 15, 16, 17) */
+  uint64_t exact[7];    /* exact counts when k = m (flag GS_F_EXACT) */
+  uint32_t flags[7];    /* GS_F_* */
+} gs_result_disc;
+
+/* Folds the disconnected numerators of the sampled edges d_pairs (device
+ * int32[2k], the list given to gs_count, any orientation) from the per-edge
+ * (t, k, q) that gs_count wrote to d_per_edge (device int64[3k]) for the
+ * same list with a mask holding every connected 4-node graphlet
+ * (GS_CONNECTED). For all edges, pass the list gs_sample writes at
+ * fraction 1. Results in *h_out (host). Uses the workspace's scratch;
+ * synchronises `stream`. */
+gs_status gs_count_disconnected(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs,
+                                int64_t k, const int64_t* d_per_edge, gs_sums_disc* h_out,
+                                void* stream);
+
+/* Host FP64 estimates, variances and bounds of G5, G6, G13-G17 from the
+ * folded sums (formulas above; var and bounds as in gs_estimate; exact
+ * counts when k = m, with GS_F_OVERFLOW when a count does not fit uint64). */
+gs_status gs_estimate_disconnected(const gs_sums_disc* s, double z, gs_result_disc* out);
 
 /* Exact merge of the sums of disjoint shards of one sample (host only):
  * acc += part. Splitting J across GPUs and merging their sums gives the

@@ -24,6 +24,9 @@ Statistics"):
   pinned to a direct two-pass sample variance and to the spread across seeds.
 * ``sample``        -- Algorithm 1 with uniform Bernoulli(p) selection of each
   edge, keyed by a SplitMix64 counter hash (project-defined random source).
+* ``disconnected_estimate`` -- Sec. 2.3's estimators of the disconnected
+  graphlets G5, G6, G13-G17 with their terms corrected (the printed block
+  swaps C13/C14 and C15/C16); exact rationals, variance read as above.
 """
 from __future__ import annotations
 
@@ -187,3 +190,80 @@ def count_estimate(row_ptr, col, pairs, z: float = Z95) -> dict:
     s, s2 = numerators(lc)
     return {"sums": s, "sq": s2, "K": len(pairs), "M": len(col) // 2,
             "est": estimate(s, s2, len(col) // 2, len(pairs), z)}
+
+
+#: disconnected graphlets, in output order
+DISCONNECTED = (5, 6, 13, 14, 15, 16, 17)
+
+
+def disconnected_estimate(row_ptr, col, pairs, z: float = Z95) -> dict:
+    """Estimators of the disconnected graphlets over the sampled edges
+    ``pairs`` (Sec. 2.3, sigma = M/K), read with corrected terms: with
+    R_e = N - 2 - t - a - b (vertices adjacent to neither end of e),
+    C5 = sum R, C13 = sum (a+b) R, C14 = sum t R, C15 = sum C(R,2),
+    C16 = sum (M - d_u - d_v + 1),
+
+        X5  = sigma C5
+        X6  = C(N,3) - X3 - X4 - X5
+        X13 = (sigma C14 - X9) / 3
+        X14 = sigma C13 / 2 - X12
+        X15 = sigma C16 / 2 - 3 X7 - 2 X8 - X9 - 2 X10 - X12
+        X16 = sigma C15 - 2 X15
+        X17 = C(N,4) - (X7 + X8 + ... + X16)
+
+    with X3..X12 the connected estimators. Each X is a constant plus sigma
+    times a sum over the sampled edges of a per-edge value y_e; V is the
+    SRSWOR variance of that sum, M (M - K) (K sum y^2 - (sum y)^2) /
+    (K^2 (K - 1)); lb, ub = X -/+ z sqrt(V); exact = X when K = M."""
+    row_ptr = np.asarray(row_ptr)
+    n = len(row_ptr) - 1
+    m = len(col) // 2
+    lc = local_counts(row_ptr, col, pairs)
+    K = len(pairs)
+    y = {g: [] for g in DISCONNECTED}  # 12 * y_e, integers
+    for t, a, b, k, q in zip(*(lc[x].tolist() for x in ("t", "a", "b", "k", "q"))):
+        R = n - 2 - t - a - b
+        c16 = m - (a + t + 1) - (b + t + 1) + 1
+        # per-edge parts of the connected estimators, times 12
+        x3, x4, x7 = 4 * t, 6 * (a + b), 2 * k
+        x8 = 12 * (t * (t - 1) // 2 - k)
+        x9 = 6 * (t * (a + b)) - 2 * x8          # (C9 - 4 X8) / 2
+        x10 = 3 * q
+        x11 = (12 * (a * (a - 1) // 2 + b * (b - 1) // 2) - x9) // 3   # (C11 - X9) / 3
+        x12 = 12 * (a * b - q)
+        x5 = 12 * R
+        x13 = (12 * t * R - x9) // 3
+        x14 = 6 * (a + b) * R - x12
+        x15 = 6 * c16 - 3 * x7 - 2 * x8 - x9 - 2 * x10 - x12
+        x16 = 12 * (R * (R - 1) // 2) - 2 * x15
+        y[5].append(x5)
+        y[6].append(x3 + x4 + x5)               # X6 = C(N,3) - (...)
+        y[13].append(x13)
+        y[14].append(x14)
+        y[15].append(x15)
+        y[16].append(x16)
+        y[17].append(x7 + x8 + x9 + x10 + x11 + x12 + x13 + x14 + x15 + x16)
+    const = {6: math.comb(n, 3), 17: math.comb(n, 4)}
+    res = {}
+    for g in DISCONNECTED:
+        S = sum(y[g])
+        S2 = sum(v * v for v in y[g])
+        r = {"X": math.nan, "V": math.nan, "lb": math.nan, "ub": math.nan, "exact": None}
+        if K >= 1:
+            lin = Fraction(m * S, K * 12)
+            X = const[g] - lin if g in const else lin
+            r["X"] = float(X)
+            if K == m:
+                if X.denominator != 1:
+                    raise ArithmeticError(f"X_{g} = {X} is not an integer at K = M")
+                r["exact"] = int(X)
+        if K >= 2:
+            V = Fraction(m * (m - K) * (K * S2 - S * S), K * K * (K - 1) * 144)
+            r["V"] = float(V)
+            half = z * math.sqrt(r["V"])
+            r["lb"], r["ub"] = r["X"] - half, r["X"] + half
+        elif K == m == 1:
+            r["V"] = 0.0
+            r["lb"] = r["ub"] = r["X"]
+        res[g] = r
+    return res

@@ -27,6 +27,10 @@ GS_THREE_NODE = GS_G3 | GS_G4
 GS_CONNECTED = GS_G3 | GS_G4 | GS_G7 | GS_G8 | GS_G9 | GS_G10 | GS_G11 | GS_G12
 GS_VALIDATE = 1
 GS_F_COMPUTED, GS_F_EXACT, GS_F_VAR_UNDEFINED, GS_F_OVERFLOW = 1, 2, 4, 8
+GS_F_VAR_OVERFLOW = 16
+# disconnected graphlets (gs_count_disconnected / gs_estimate_disconnected)
+DISCONNECTED = (5, 6, 13, 14, 15, 16, 17)
+DISC_DENOM = (1, 6, 6, 2, 2, 1, 12)
 
 STATUS = {0: "GS_OK", 1: "GS_EINVAL", 2: "GS_ENOTSORTED", 3: "GS_ESELFLOOP", 4: "GS_EDUP",
           5: "GS_EASYM", 6: "GS_EEDGE", 7: "GS_EDUPSAMPLE", 8: "GS_EOVERFLOW", 9: "GS_ENOMEM",
@@ -54,6 +58,37 @@ class GsSums(ctypes.Structure):
                 s -= 1 << 128
             s2 = (int(self.sumsq[i][1]) << 64) | int(self.sumsq[i][0])
             out[g] = (s, s2)
+        return out
+
+
+class GsSumsDisc(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int64), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("overflow", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("sum", (ctypes.c_uint64 * 2) * 7), ("sumsq", (ctypes.c_uint64 * 2) * 7)]
+
+    def sums(self) -> dict:
+        """{graphlet: (sum N_i, sum N_i^2)} as Python ints (order of DISCONNECTED)."""
+        out = {}
+        for i, g in enumerate(DISCONNECTED):
+            s = (int(self.sum[i][1]) << 64) | int(self.sum[i][0])
+            if s >> 127:
+                s -= 1 << 128
+            out[g] = (s, (int(self.sumsq[i][1]) << 64) | int(self.sumsq[i][0]))
+        return out
+
+
+class GsResultDisc(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double * 7), ("var", ctypes.c_double * 7),
+                ("lb", ctypes.c_double * 7), ("ub", ctypes.c_double * 7),
+                ("exact", ctypes.c_uint64 * 7), ("flags", ctypes.c_uint32 * 7)]
+
+    def as_dict(self) -> dict:
+        out = {}
+        for i, g in enumerate(DISCONNECTED):
+            f = int(self.flags[i])
+            out[g] = {"X": self.x[i], "V": self.var[i], "lb": self.lb[i], "ub": self.ub[i],
+                      "exact": int(self.exact[i]) if f & GS_F_EXACT and not f & GS_F_OVERFLOW
+                      else None, "flags": f}
         return out
 
 
@@ -150,6 +185,10 @@ def lib() -> ctypes.CDLL:
         "gs_graph_destroy": ([P], ctypes.c_int32),
         "gs_graph_info": ([P, PI64, PI64, PI64, PI64, PI64], ctypes.c_int32),
         "gs_graph_index_info": ([P, PI64, PI64, PI64, PI64], ctypes.c_int32),
+        "gs_count_disconnected": ([P, P, P, I64, P, ctypes.POINTER(GsSumsDisc), P],
+                                  ctypes.c_int32),
+        "gs_estimate_disconnected": ([ctypes.POINTER(GsSumsDisc), D,
+                                      ctypes.POINTER(GsResultDisc)], ctypes.c_int32),
         "gs_workspace_create": ([PP], ctypes.c_int32),
         "gs_workspace_destroy": ([P], ctypes.c_int32),
         "gs_workspace_bytes": ([P, ctypes.POINTER(U64)], ctypes.c_int32),
@@ -368,6 +407,23 @@ def gs_estimate(sums: GsSums, z: float = 1.96) -> GsResult:
     return out
 
 
+def gs_count_disconnected(graph: int, ws: int, pairs, k: int, per_edge, stream=None) -> GsSumsDisc:
+    """pairs: CUDA int32 [k, 2], the list given to gs_count; per_edge: CUDA
+    int64 [k, 3] that gs_count wrote for it with mask GS_CONNECTED."""
+    import torch
+    out = GsSumsDisc()
+    _check(lib().gs_count_disconnected(graph, ws, _dev(pairs, torch.int32, "pairs"), k,
+                                       _dev(per_edge, torch.int64, "per_edge"),
+                                       ctypes.byref(out), _stream_ptr(stream)))
+    return out
+
+
+def gs_estimate_disconnected(sums: GsSumsDisc, z: float = 1.96) -> GsResultDisc:
+    out = GsResultDisc()
+    _check(lib().gs_estimate_disconnected(ctypes.byref(sums), z, ctypes.byref(out)))
+    return out
+
+
 def gs_count_estimate(graph: int, ws: int, fraction: float, seed: int,
                       mask: int = GS_CONNECTED, z: float = 1.96, stream=None):
     out = GsResult()
@@ -447,6 +503,18 @@ class Graph:
     def count(self, pairs=None, mask: int = GS_CONNECTED, per_edge=None, stream=None) -> GsSums:
         k = self.m if pairs is None else pairs.shape[0]
         return gs_count(self.handle, self.ws.handle, pairs, k, mask, per_edge, stream)
+
+    def count_all(self, pairs=None, stream=None):
+        """Connected and disconnected sums of one sampled-edge list (None: every
+        edge, listed by the sampler at fraction 1): (GsSums, GsSumsDisc)."""
+        import torch
+        if pairs is None:
+            pairs = self.sample(1.0, 0)
+        k = pairs.shape[0]
+        per = torch.empty((k, 3), dtype=torch.int64, device=pairs.device)
+        conn = gs_count(self.handle, self.ws.handle, pairs, k, GS_CONNECTED, per, stream)
+        disc = gs_count_disconnected(self.handle, self.ws.handle, pairs, k, per, stream)
+        return conn, disc
 
     def count_estimate(self, fraction: float, seed: int = 0, mask: int = GS_CONNECTED,
                        z: float = 1.96, stream=None):

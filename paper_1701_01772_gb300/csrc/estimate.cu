@@ -58,6 +58,67 @@ double to_double_256(const U256& a) {
 i128 load_i128(const uint64_t v[2]) { return (i128)(((u128)v[1] << 64) | v[0]); }
 u128 load_u128(const uint64_t v[2]) { return ((u128)v[1] << 64) | v[0]; }
 
+// One estimator of the form X = c + sign * sigma * S / D (sigma = M / K; c and
+// sign = -1 only for the complements X6, X17): estimate, SRSWOR variance of
+// the linear part, bounds, and the exact count when K = M.
+struct One {
+  double x, var, lb, ub;
+  uint64_t exact;
+  uint32_t flags;
+};
+
+One estimate_one(i128 S, u128 S2, bool sq_wrapped, int64_t D, int64_t M, int64_t K, double z,
+                 bool complement, u128 c) {
+  One r{NAN, NAN, NAN, NAN, 0, GS_F_COMPUTED};
+  double x = NAN;
+  if (K >= 1) {
+    // M S / (K D): one rounding of the exact product when it fits.
+    const u128 absS = (u128)(S < 0 ? -S : S);
+    if (absS < ((u128)1 << 90) && M < ((int64_t)1 << 36)) {
+      x = (double)(S * (i128)M) / (double)(K * D);
+    } else {
+      x = ((double)M / (double)K) * ((double)S / (double)D);
+    }
+    if (complement) x = (double)c - x;
+  }
+  double var = NAN;
+  if (K == M && K >= 1) {
+    r.flags |= GS_F_EXACT;
+    var = 0.0;
+    if (S % D != 0) {
+      r.flags |= GS_F_OVERFLOW;
+    } else {
+      const i128 q = S / D;
+      const i128 cnt = complement ? (i128)c - q : q;
+      if (cnt < 0 || (u128)cnt > (u128)UINT64_MAX)
+        r.flags |= GS_F_OVERFLOW;
+      else
+        r.exact = (uint64_t)cnt;
+    }
+  } else if (K >= 2 && sq_wrapped) {
+    r.flags |= GS_F_VAR_OVERFLOW;
+  } else if (K >= 2) {
+    // Q = K sum N^2 - (sum N)^2 >= 0 exactly, in 256 bits.
+    const U256 a = mul_128x128(S2, (u128)K);
+    const u128 absS = (u128)(S < 0 ? -S : S);
+    const U256 b = mul_128x128(absS, absS);
+    const double Q = less_256(a, b) ? 0.0 : to_double_256(sub_256(a, b));
+    const double num = (double)M * (double)(M - K);
+    const double den = (double)K * (double)K * (double)(K - 1) * (double)(D * D);
+    var = num / den * Q;
+  } else {
+    r.flags |= GS_F_VAR_UNDEFINED;
+  }
+  r.x = x;
+  r.var = var;
+  if (!(r.flags & (GS_F_VAR_UNDEFINED | GS_F_VAR_OVERFLOW))) {
+    const double half = z * sqrt(var);
+    r.lb = x - half;
+    r.ub = x + half;
+  }
+  return r;
+}
+
 }  // namespace
 
 extern "C" gs_status gs_estimate(const gs_sums* s, double z, gs_result* out) {
@@ -65,55 +126,45 @@ extern "C" gs_status gs_estimate(const gs_sums* s, double z, gs_result* out) {
     gs::set_error("gs_estimate: invalid arguments (need 0 <= k <= m, z >= 0)");
     return GS_EINVAL;
   }
-  const int64_t M = s->m, K = s->k;
   for (int i = 0; i < 8; ++i) {
     out->x[i] = out->var[i] = out->lb[i] = out->ub[i] = NAN;
     out->exact[i] = 0;
     out->flags[i] = 0;
     if (!(s->mask & kBit[i])) continue;
-    uint32_t flags = GS_F_COMPUTED;
-    const i128 S = load_i128(s->sum[i]);
-    const u128 S2 = load_u128(s->sumsq[i]);
-    const int64_t D = kDenom[i];
-    double x = NAN;
-    if (K >= 1) {
-      // X = M S / (K D): one rounding of the exact product when it fits.
-      const u128 absS = (u128)(S < 0 ? -S : S);
-      if (absS < ((u128)1 << 90) && M < ((int64_t)1 << 36)) {
-        x = (double)(S * (i128)M) / (double)(K * D);
-      } else {
-        x = ((double)M / (double)K) * ((double)S / (double)D);
-      }
-    }
-    double var = NAN;
-    if (K == M && K >= 1) {
-      flags |= GS_F_EXACT;
-      var = 0.0;
-      if (S < 0 || S % D != 0 || (u128)(S / D) > (u128)UINT64_MAX) {
-        flags |= GS_F_OVERFLOW;
-      } else {
-        out->exact[i] = (uint64_t)(S / D);
-      }
-    } else if (K >= 2) {
-      // Q = K sum N^2 - (sum N)^2 >= 0 exactly, in 256 bits.
-      const U256 a = mul_128x128(S2, (u128)K);
-      const u128 absS = (u128)(S < 0 ? -S : S);
-      const U256 b = mul_128x128(absS, absS);
-      const double Q = less_256(a, b) ? 0.0 : to_double_256(sub_256(a, b));
-      const double num = (double)M * (double)(M - K);
-      const double den = (double)K * (double)K * (double)(K - 1) * (double)(D * D);
-      var = num / den * Q;
-    } else {
-      flags |= GS_F_VAR_UNDEFINED;
-    }
-    out->x[i] = x;
-    out->var[i] = var;
-    if (!(flags & GS_F_VAR_UNDEFINED)) {
-      const double half = z * sqrt(var);
-      out->lb[i] = x - half;
-      out->ub[i] = x + half;
-    }
-    out->flags[i] = flags;
+    const One r = estimate_one(load_i128(s->sum[i]), load_u128(s->sumsq[i]), false, kDenom[i],
+                               s->m, s->k, z, false, 0);
+    out->x[i] = r.x;
+    out->var[i] = r.var;
+    out->lb[i] = r.lb;
+    out->ub[i] = r.ub;
+    out->exact[i] = r.exact;
+    out->flags[i] = r.flags;
+  }
+  return GS_OK;
+}
+
+extern "C" gs_status gs_estimate_disconnected(const gs_sums_disc* s, double z, gs_result_disc* out) {
+  if (s == nullptr || out == nullptr || s->k < 0 || s->m < 0 || s->k > s->m || s->n < 0 ||
+      !(z >= 0.0)) {
+    gs::set_error("gs_estimate_disconnected: invalid arguments (need 0 <= k <= m, n >= 0, "
+                  "z >= 0)");
+    return GS_EINVAL;
+  }
+  static const int64_t D[7] = {1, 6, 6, 2, 2, 1, 12};  // order 5, 6, 13, 14, 15, 16, 17
+  const u128 n = (u128)s->n;
+  const u128 c3 = n < 3 ? 0 : n * (n - 1) * (n - 2) / 6;                  // C(n, 3)
+  const u128 c4 = n < 4 ? 0 : n * (n - 1) * (n - 2) / 6 * (n - 3) / 4;    // C(n, 4)
+  for (int i = 0; i < 7; ++i) {
+    const bool complement = i == 1 || i == 6;
+    const One r = estimate_one(load_i128(s->sum[i]), load_u128(s->sumsq[i]),
+                               (s->overflow >> i) & 1u, D[i], s->m, s->k, z, complement,
+                               i == 1 ? c3 : c4);
+    out->x[i] = r.x;
+    out->var[i] = r.var;
+    out->lb[i] = r.lb;
+    out->ub[i] = r.ub;
+    out->exact[i] = r.exact;
+    out->flags[i] = r.flags;
   }
   return GS_OK;
 }

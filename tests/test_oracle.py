@@ -284,3 +284,92 @@ def test_unbiased_and_covering_over_seeds():
         emp = float(np.var(xs[g], ddof=1))
         if exact[g] >= 1000:
             assert 0.6 < emp / float(np.mean(vs[g])) < 1.6, g
+
+
+# ------------------------------------------------------------------ disconnected graphlets
+
+DISC = oracle.DISCONNECTED
+
+
+def _disc_exact(rp, col):
+    return {g: r["exact"] for g, r in
+            oracle.disconnected_estimate(rp, col, synth.upper_pairs(rp, col)).items()}
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_disconnected_exact_counts_match_brute_force(seed):
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(12):
+        n = int(rng.integers(4, 12))
+        A = np.triu((rng.random((n, n)) < rng.random()).astype(np.int64), 1)
+        A = A + A.T
+        if A.sum() == 0:
+            continue
+        rp, col = brute.csr_from_adjacency(A)
+        want = brute.brute_counts(A)
+        got = _disc_exact(rp, col)
+        for g in DISC:
+            assert got[g] == want[g], (g, got[g], want[g])
+
+
+def test_disconnected_closed_forms():
+    # one edge on n vertices: every other vertex is isolated
+    for n in (4, 7, 30):
+        rp, col = synth.from_pairs(n, np.array([0]), np.array([1]))
+        got = _disc_exact(rp, col)
+        assert got[5] == n - 2 and got[6] == math.comb(n, 3) - (n - 2)
+        assert got[16] == math.comb(n - 2, 2)
+        assert got[17] == math.comb(n, 4) - math.comb(n - 2, 2)
+        assert got[13] == got[14] == got[15] == 0
+    # K_n has no disconnected induced subgraph
+    n, edges = brute.family_edges("complete", 9)
+    rp, col = synth.from_pairs(n, np.array([e[0] for e in edges]), np.array([e[1] for e in edges]))
+    assert all(v == 0 for v in _disc_exact(rp, col).values())
+    # a perfect matching on 2p vertices: pairs of matching edges are G15,
+    # an edge with two vertices of other edges is G16
+    p = 6
+    rp, col = synth.from_pairs(2 * p, np.arange(0, 2 * p, 2), np.arange(1, 2 * p, 2))
+    got = _disc_exact(rp, col)
+    assert got[15] == math.comb(p, 2)
+    assert got[16] == p * (math.comb(2 * p - 2, 2) - (p - 1))
+    assert got[5] == p * (2 * p - 2) and got[13] == got[14] == 0
+
+
+def test_printed_disconnected_block_disagrees_with_brute_force():
+    """As printed, the estimators of G13 and G14 use C13 and C14 the other
+    way round; that reading fails brute force (the corrected one passes in
+    the tests above)."""
+    rng = np.random.default_rng(7)
+    disagree = 0
+    for _ in range(30):
+        n = int(rng.integers(5, 10))
+        A = np.triu((rng.random((n, n)) < 0.5).astype(np.int64), 1)
+        A = A + A.T
+        if A.sum() == 0:
+            continue
+        rp, col = brute.csr_from_adjacency(A)
+        pairs = synth.upper_pairs(rp, col)
+        lc = oracle.local_counts(rp, col, pairs)
+        R = (n - 2 - lc["t"] - lc["a"] - lc["b"]).astype(object)
+        c13 = int(np.sum((lc["a"] + lc["b"]).astype(object) * R))  # (a+b) R
+        x9 = oracle.exact_counts(rp, col)[9]
+        literal_13 = (c13 - x9) / 3  # printed: C13 where C14 = sum t R belongs
+        if literal_13 != brute.brute_counts(A)[13]:
+            disagree += 1
+    assert disagree >= 20
+
+
+def test_disconnected_unbiased_over_seeds():
+    rp, col = synth.er(300, 3000, seed=5)
+    exact = _disc_exact(rp, col)
+    xs = {g: [] for g in DISC}
+    vs = {g: [] for g in DISC}
+    for sd in range(120):
+        est = oracle.disconnected_estimate(rp, col, oracle.sample(rp, col, 0.1, sd))
+        for g in DISC:
+            xs[g].append(est[g]["X"])
+            vs[g].append(est[g]["V"])
+    for g in DISC:
+        mean = float(np.mean(xs[g]))
+        se = math.sqrt(float(np.mean(vs[g])) / len(xs[g]))
+        assert abs(mean - exact[g]) <= 4.5 * se + 1e-6 * abs(exact[g]) + 1e-9, (g, mean, exact[g])
