@@ -237,6 +237,26 @@ gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_per_sm, int q
 /* Host output: statistics of the last gs_count that used `ws`. */
 gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
 
+/* Algorithm 8 (adaptive estimation): grows the sampled edge set until the
+ * estimates stop moving. Iteration t adds the edges whose sampler key
+ * (gs_sample's) lies between fractions p_{t-1} and p_t = p_{t-1} +
+ * phi_t (1 - p_{t-1}) -- a uniform sample without replacement of about
+ * phi_t of the edges not yet sampled -- counts only those (mask as in
+ * gs_count), merges their exact sums into the running ones and
+ * re-estimates; phi_{t+1} = phi_t / 2. The loss is the maximum relative
+ * change over the graphlets of the mask, max_i |X_i^(t) - X_i^(t-1)| /
+ * |X_i^(t-1)| (graphlets with X^(t-1) = 0 are skipped); the first iteration
+ * has no previous estimate (loss 1). The loop stops when the loss is at most
+ * beta or after t_max iterations. phi <= 0 selects phi_1 = 1 / sqrt(m).
+ * Outputs (host): the running sums, their estimates (z as gs_estimate),
+ * the iterations run and the final fraction p. Because the samples are
+ * nested, the result equals gs_count over gs_sample(p, seed).
+ * Synchronises `stream`. */
+gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, double beta, int32_t t_max,
+                            double phi, uint64_t seed, uint32_t mask, double z,
+                            gs_sums* sums_out, gs_result* out, int32_t* iters_out,
+                            double* fraction_out, void* stream);
+
 /* ---- disconnected graphlets (G5, G6, G13-G17) --------------------------
  * Sec. 2.3's estimators of the disconnected 3- and 4-node graphlets, read
  * with corrected terms (the printed block swaps C13 with C14 and C15 with

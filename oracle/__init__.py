@@ -24,6 +24,8 @@ Statistics"):
   pinned to a direct two-pass sample variance and to the spread across seeds.
 * ``sample``        -- Algorithm 1 with uniform Bernoulli(p) selection of each
   edge, keyed by a SplitMix64 counter hash (project-defined random source).
+* ``adaptive_estimate`` -- Algorithm 8 (adaptive estimation): grow the
+  sample until the maximum relative change of the estimates is at most beta.
 * ``disconnected_estimate`` -- Sec. 2.3's estimators of the disconnected
   graphlets G5, G6, G13-G17 with their terms corrected (the printed block
   swaps C13/C14 and C15/C16); exact rationals, variance read as above.
@@ -267,3 +269,43 @@ def disconnected_estimate(row_ptr, col, pairs, z: float = Z95) -> dict:
             r["lb"] = r["ub"] = r["X"]
         res[g] = r
     return res
+
+
+def adaptive_estimate(row_ptr, col, beta: float, t_max: int, phi: float, seed: int,
+                      graphlets=GRAPHLETS, z: float = Z95) -> dict:
+    """Algorithm 8 with the Bernoulli sampler of ``sample``: iteration t
+    grows the sampled set by about phi of the edges not yet sampled (the
+    fraction goes from p to p + phi (1 - p), which adds exactly the edges
+    whose key lies between the two, since the samples are nested), recomputes
+    the estimates from everything sampled so far, takes as loss the maximum
+    relative change max_i |X_i^(t) - X_i^(t-1)| / |X_i^(t-1)| (skipping
+    X^(t-1) = 0; none on the first iteration, loss 1) and halves phi; it
+    stops when the loss is at most beta or after t_max iterations.
+    phi <= 0 means 1 / sqrt(M)."""
+    m = len(col) // 2
+    if not phi > 0:
+        phi = 1.0 / math.sqrt(m) if m > 0 else 1.0
+    p, loss, t = 0.0, 1.0, 0
+    prev = None
+    pairs = np.zeros((0, 2), dtype=np.int32)
+    est = s = s2 = None
+    while loss > beta and t < t_max:
+        p_new = p + phi * (1.0 - p)
+        pairs = sample(row_ptr, col, p_new, seed)
+        lc = local_counts(row_ptr, col, pairs)
+        s, s2 = numerators(lc)
+        est = estimate(s, s2, m, len(pairs), z)
+        x = {g: est[g]["X"] for g in graphlets}
+        if prev is None:
+            loss = 1.0
+        else:
+            loss = 0.0
+            for g in graphlets:
+                if prev[g] != 0.0 and not math.isnan(prev[g]):
+                    r = abs(x[g] - prev[g]) / abs(prev[g])
+                    loss = max(loss, math.inf if math.isnan(r) else r)
+        prev = x
+        p = p_new
+        phi *= 0.5
+        t += 1
+    return {"iters": t, "p": p, "K": len(pairs), "sums": s, "sq": s2, "est": est}

@@ -185,6 +185,9 @@ def lib() -> ctypes.CDLL:
         "gs_graph_destroy": ([P], ctypes.c_int32),
         "gs_graph_info": ([P, PI64, PI64, PI64, PI64, PI64], ctypes.c_int32),
         "gs_graph_index_info": ([P, PI64, PI64, PI64, PI64], ctypes.c_int32),
+        "gs_count_adaptive": ([P, P, D, ctypes.c_int32, D, U64, U32, D, ctypes.POINTER(GsSums),
+                               ctypes.POINTER(GsResult), ctypes.POINTER(ctypes.c_int32),
+                               ctypes.POINTER(ctypes.c_double), P], ctypes.c_int32),
         "gs_count_disconnected": ([P, P, P, I64, P, ctypes.POINTER(GsSumsDisc), P],
                                   ctypes.c_int32),
         "gs_estimate_disconnected": ([ctypes.POINTER(GsSumsDisc), D,
@@ -416,6 +419,18 @@ def gs_count_disconnected(graph: int, ws: int, pairs, k: int, per_edge, stream=N
                                        _dev(per_edge, torch.int64, "per_edge"),
                                        ctypes.byref(out), _stream_ptr(stream)))
     return out
+
+
+def gs_count_adaptive(graph: int, ws: int, beta: float, t_max: int = 20, phi: float = 0.0,
+                      seed: int = 0, mask: int = GS_CONNECTED, z: float = 1.96, stream=None):
+    """Algorithm 8: (sums, result, iterations, final fraction)."""
+    sums, res = GsSums(), GsResult()
+    iters, frac = ctypes.c_int32(), ctypes.c_double()
+    _check(lib().gs_count_adaptive(graph, ws, float(beta), int(t_max), float(phi),
+                                   seed & (2**64 - 1), mask, z, ctypes.byref(sums),
+                                   ctypes.byref(res), ctypes.byref(iters), ctypes.byref(frac),
+                                   _stream_ptr(stream)))
+    return sums, res, iters.value, frac.value
 
 
 def gs_estimate_disconnected(sums: GsSumsDisc, z: float = 1.96) -> GsResultDisc:

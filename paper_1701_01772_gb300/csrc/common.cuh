@@ -293,9 +293,11 @@ gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint
                       int32_t* d_pairs, int64_t max_k, int64_t* k_out, int32_t** pairs_out,
                       cudaStream_t stream);
 // Samples canonical edges [e0, e0 + m) (hash index relative to e0).
+// Edges of [e0, e0 + m) whose sampler key lies in [fraction_lo, fraction)
+// x 2^53 (fraction_lo = 0: the Bernoulli(fraction) sample).
 gs_status sample_range(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
                        int64_t e0, int64_t m, int32_t* d_pairs, int64_t max_k, int64_t* k_out,
-                       int32_t** pairs_out, cudaStream_t stream);
+                       int32_t** pairs_out, cudaStream_t stream, double fraction_lo = 0.0);
 }  // namespace gs
 
 namespace gs {

@@ -213,3 +213,57 @@ extern "C" gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, doub
   if (k_out) *k_out = K;
   return gs_estimate(&sums, z, out);
 }
+
+extern "C" gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, double beta,
+                                       int32_t t_max, double phi, uint64_t seed, uint32_t mask,
+                                       double z, gs_sums* sums_out, gs_result* out,
+                                       int32_t* iters_out, double* fraction_out, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (g == nullptr || ws == nullptr || sums_out == nullptr || out == nullptr || !(beta >= 0.0) ||
+      t_max < 1 || !(phi <= 1.0) || !(z >= 0.0)) {
+    gs::set_error("gs_count_adaptive: invalid arguments (need beta >= 0, t_max >= 1, phi <= 1)");
+    return GS_EINVAL;
+  }
+  int64_t M = 0;
+  gs_graph_info(g, nullptr, &M, nullptr, nullptr, nullptr);
+  if (!(phi > 0.0)) phi = M > 0 ? 1.0 / sqrt((double)M) : 1.0;
+  memset(sums_out, 0, sizeof(*sums_out));
+  sums_out->m = M;
+  sums_out->mask = mask;
+  double p = 0.0, loss = 1.0;
+  double prev[8];
+  bool have_prev = false;
+  int32_t t = 0;
+  while (loss > beta && t < t_max) {
+    const double p_new = p + phi * (1.0 - p);
+    int64_t K = 0;
+    int32_t* pairs = nullptr;
+    GS_TRY(gs::sample_range(g, ws, p_new, seed, 0, M, nullptr, 0, &K, &pairs, stream, p));
+    if (K > 0) {  // (a ring can be empty on a small graph)
+      gs_sums part;
+      GS_TRY(gs_count(g, ws, pairs, K, mask, nullptr, &part, stream));
+      part.m = M;
+      part.mask = mask;
+      GS_TRY(gs_sums_merge(sums_out, &part));
+    }
+    GS_TRY(gs_estimate(sums_out, z, out));
+    double l = 0.0;
+    for (int i = 0; i < 8; ++i) {
+      if (!(out->flags[i] & GS_F_COMPUTED)) continue;
+      if (have_prev && prev[i] != 0.0 && !isnan(prev[i])) {
+        double r = fabs(out->x[i] - prev[i]) / fabs(prev[i]);
+        if (isnan(r)) r = INFINITY;  // an undefined change counts as large
+        if (r > l) l = r;
+      }
+      prev[i] = out->x[i];
+    }
+    loss = have_prev ? l : 1.0;
+    have_prev = true;
+    p = p_new;
+    phi *= 0.5;
+    ++t;
+  }
+  if (iters_out) *iters_out = t;
+  if (fraction_out) *fraction_out = p;
+  return GS_OK;
+}

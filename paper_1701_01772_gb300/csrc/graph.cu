@@ -1061,8 +1061,13 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
   return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ bool edge_kept(uint64_t seed, uint64_t i, uint64_t threshold) {
-  return (splitmix64(seed ^ splitmix64(i)) >> 11) < threshold;
+// Edge i is kept iff its 53-bit key lies in [lo, hi): lo = 0 is the plain
+// Bernoulli(hi / 2^53) sample, and for lo > 0 the keys between two
+// fractions give the edges one sample adds to a smaller one with the same
+// seed (the samples are nested).
+__device__ __forceinline__ bool edge_kept(uint64_t seed, uint64_t i, uint64_t lo, uint64_t hi) {
+  const uint64_t key = splitmix64(seed ^ splitmix64(i)) >> 11;
+  return key >= lo && key < hi;
 }
 
 constexpr int kSampThreads = 256;
@@ -1072,13 +1077,13 @@ constexpr int64_t kSampTile = (int64_t)kSampThreads * kSampItems;
 // Edges [e0, e0 + m) of the canonical order are sampled; the hash input is
 // the index relative to e0 (so a graph inside a disjoint union samples
 // exactly as it does on its own).
-__global__ void k_sample_count(int64_t m, uint64_t seed, uint64_t threshold,
+__global__ void k_sample_count(int64_t m, uint64_t seed, uint64_t lo, uint64_t threshold,
                                int64_t* __restrict__ tile_cnt) {
   int64_t base = (int64_t)blockIdx.x * kSampTile + (int64_t)threadIdx.x * kSampItems;
   int c = 0;
 #pragma unroll
   for (int j = 0; j < kSampItems; ++j)
-    if (base + j < m) c += edge_kept(seed, (uint64_t)(base + j), threshold);
+    if (base + j < m) c += edge_kept(seed, (uint64_t)(base + j), lo, threshold);
   c = __reduce_add_sync(0xffffffffu, c);
   __shared__ int wsum[kSampThreads / 32];
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
@@ -1092,14 +1097,14 @@ __global__ void k_sample_count(int64_t m, uint64_t seed, uint64_t threshold,
 
 __global__ void k_sample_write(const int32_t* __restrict__ col, const int64_t* __restrict__ up_ptr,
                                const int64_t* __restrict__ edge_off, int64_t n, int64_t e0,
-                               int64_t m, uint64_t seed, uint64_t threshold,
+                               int64_t m, uint64_t seed, uint64_t lo, uint64_t threshold,
                                const int64_t* __restrict__ tile_off, int32_t* __restrict__ pairs) {
   __shared__ int wsum[kSampThreads / 32];
   int64_t base = (int64_t)blockIdx.x * kSampTile + (int64_t)threadIdx.x * kSampItems;
   unsigned bits = 0;
 #pragma unroll
   for (int j = 0; j < kSampItems; ++j)
-    if (base + j < m && edge_kept(seed, (uint64_t)(base + j), threshold)) bits |= 1u << j;
+    if (base + j < m && edge_kept(seed, (uint64_t)(base + j), lo, threshold)) bits |= 1u << j;
   int c = __popc(bits);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int x = c;
@@ -1145,11 +1150,12 @@ gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint
 
 gs_status sample_range(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
                        int64_t e0, int64_t m, int32_t* d_pairs, int64_t max_k, int64_t* k_out,
-                       int32_t** pairs_out, cudaStream_t stream) {
+                       int32_t** pairs_out, cudaStream_t stream, double fraction_lo) {
   *k_out = 0;
   if (pairs_out) *pairs_out = d_pairs;
   if (m == 0) return GS_OK;
   const uint64_t threshold = (uint64_t)floor(fraction * 9007199254740992.0);
+  const uint64_t lo = (uint64_t)floor(fraction_lo * 9007199254740992.0);
   int64_t tiles = (m + kSampTile - 1) / kSampTile;
   size_t bytes = Carve::bytes_for<int64_t>(tiles + 1) * 2 +
                  Carve::bytes_for<int64_t>(scan_tmp_elems(tiles));
@@ -1159,7 +1165,7 @@ gs_status sample_range(const gs_graph* g, gs_workspace* ws, double fraction, uin
   int64_t* cnt = c.take<int64_t>(tiles + 1);
   int64_t* off = c.take<int64_t>(tiles + 1);
   int64_t* tmp = c.take<int64_t>(scan_tmp_elems(tiles));
-  k_sample_count<<<(unsigned)tiles, kSampThreads, 0, stream>>>(m, seed, threshold, cnt);
+  k_sample_count<<<(unsigned)tiles, kSampThreads, 0, stream>>>(m, seed, lo, threshold, cnt);
   GS_TRY(exclusive_scan_i64(cnt, off, tiles, tmp, stream));
   ws->launches_total += 4;
   int64_t kept = 0;
@@ -1178,7 +1184,7 @@ gs_status sample_range(const gs_graph* g, gs_workspace* ws, double fraction, uin
   }
   if (kept > 0) {
     k_sample_write<<<(unsigned)tiles, kSampThreads, 0, stream>>>(
-        g->dev.col, g->up_ptr, g->edge_off, g->dev.n, e0, m, seed, threshold, off, d_pairs);
+        g->dev.col, g->up_ptr, g->edge_off, g->dev.n, e0, m, seed, lo, threshold, off, d_pairs);
     ws->launches_total += 1;
   }
   GS_CUDA(cudaGetLastError());

@@ -373,3 +373,29 @@ def test_disconnected_unbiased_over_seeds():
         mean = float(np.mean(xs[g]))
         se = math.sqrt(float(np.mean(vs[g])) / len(xs[g]))
         assert abs(mean - exact[g]) <= 4.5 * se + 1e-6 * abs(exact[g]) + 1e-9, (g, mean, exact[g])
+
+
+# ------------------------------------------------------------------ Algorithm 8 (adaptive)
+
+def test_adaptive_with_zero_beta_runs_t_max_halving_phi():
+    rp, col = synth.er_2000()
+    r = oracle.adaptive_estimate(rp, col, 0.0, 6, 0.05, 3)
+    assert r["iters"] == 6
+    p, phi = 0.0, 0.05
+    for _ in range(6):
+        p, phi = p + phi * (1.0 - p), phi / 2
+    assert r["p"] == p
+
+
+def test_adaptive_result_is_the_nested_sample_and_larger_beta_stops_no_later():
+    rp, col = synth.chung_lu(3000, 20000, 2.1, 300.0, seed=8)
+    prev_iters = None
+    for beta in (0.001, 0.01, 0.1):
+        r = oracle.adaptive_estimate(rp, col, beta, 10, 0.02, 5)
+        pairs = oracle.sample(rp, col, r["p"], 5)
+        assert r["K"] == len(pairs)
+        s, s2 = oracle.numerators(oracle.local_counts(rp, col, pairs))
+        assert s == r["sums"] and s2 == r["sq"]
+        if prev_iters is not None:
+            assert r["iters"] <= prev_iters
+        prev_iters = r["iters"]
