@@ -247,7 +247,8 @@ gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
  * change over the graphlets of the mask, max_i |X_i^(t) - X_i^(t-1)| /
  * |X_i^(t-1)| (graphlets with X^(t-1) = 0 are skipped); the first iteration
  * has no previous estimate (loss 1). The loop stops when the loss is at most
- * beta or after t_max iterations. phi <= 0 selects phi_1 = 1 / sqrt(m).
+ * beta (0 <= beta < 1; the first iteration always runs) or after t_max
+ * iterations. phi <= 0 selects phi_1 = 1 / sqrt(m).
  * Outputs (host): the running sums, their estimates (z as gs_estimate),
  * the iterations run and the final fraction p. Because the samples are
  * nested, the result equals gs_count over gs_sample(p, seed).

@@ -219,9 +219,10 @@ extern "C" gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, doub
                                        double z, gs_sums* sums_out, gs_result* out,
                                        int32_t* iters_out, double* fraction_out, void* stream_) {
   cudaStream_t stream = (cudaStream_t)stream_;
-  if (g == nullptr || ws == nullptr || sums_out == nullptr || out == nullptr || !(beta >= 0.0) ||
-      t_max < 1 || !(phi <= 1.0) || !(z >= 0.0)) {
-    gs::set_error("gs_count_adaptive: invalid arguments (need beta >= 0, t_max >= 1, phi <= 1)");
+  if (g == nullptr || ws == nullptr || sums_out == nullptr || out == nullptr ||
+      !(beta >= 0.0 && beta < 1.0) || t_max < 1 || !(phi <= 1.0) || !(z >= 0.0)) {
+    gs::set_error("gs_count_adaptive: invalid arguments (need 0 <= beta < 1, t_max >= 1, "
+                  "phi <= 1, z >= 0)");
     return GS_EINVAL;
   }
   int64_t M = 0;
