@@ -97,3 +97,28 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gs, "_lib_handle", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         gs.lib()
+
+
+def test_header_is_plain_c_and_struct_layouts_match_the_binding(tmp_path):
+    """include/graphlet.h compiles as C99 (no C++ or CUDA types in the
+    boundary), and the sizes of its result structs equal the binding's."""
+    import shutil
+    import subprocess
+
+    import paper_1701_01772_gb300 as gs
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text('#include <stdio.h>\n#include "graphlet.h"\nint main(void) {\n'
+                   '  printf("%zu %zu %zu %zu %zu\\n", sizeof(gs_sums), sizeof(gs_result),\n'
+                   '         sizeof(gs_sums_disc), sizeof(gs_result_disc), sizeof(gs_stats));\n'
+                   '  return 0;\n}\n')
+    exe = tmp_path / "abi"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe)], check=True)
+    sizes = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                            check=True).stdout.split()]
+    want = [ctypes.sizeof(c) for c in (gs.GsSums, gs.GsResult, gs.GsSumsDisc, gs.GsResultDisc,
+                                       gs.GsStats)]
+    assert sizes == want
