@@ -304,6 +304,17 @@ gs_status gs_count_disconnected(const gs_graph* g, gs_workspace* ws, const int32
                                 int64_t k, const int64_t* d_per_edge, gs_sums_disc* h_out,
                                 void* stream);
 
+/* Micro-level output (Sec. 5's per-edge statistics, exact when every probe
+ * is made): row e of d_out (device int64[8k]) receives the per-edge
+ * numerators (N3, N4, N7, N8, N9, N10, N11, N12) of sampled edge e, from
+ * the per-edge (t, k, q) that gs_count wrote for the same list with mask
+ * GS_CONNECTED (N9 and N11 can be negative). The rows sum to gs_count's
+ * sums. Asynchronous apart from the final status check, which synchronises
+ * `stream`. */
+gs_status gs_per_edge_numerators(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs,
+                                 int64_t k, const int64_t* d_per_edge, int64_t* d_out,
+                                 void* stream);
+
 /* Host FP64 estimates, variances and bounds of G5, G6, G13-G17 from the
  * folded sums (formulas above; var and bounds as in gs_estimate; exact
  * counts when k = m, with GS_F_OVERFLOW when a count does not fit uint64). */

@@ -188,6 +188,7 @@ def lib() -> ctypes.CDLL:
         "gs_count_adaptive": ([P, P, D, ctypes.c_int32, D, U64, U32, D, ctypes.POINTER(GsSums),
                                ctypes.POINTER(GsResult), ctypes.POINTER(ctypes.c_int32),
                                ctypes.POINTER(ctypes.c_double), P], ctypes.c_int32),
+        "gs_per_edge_numerators": ([P, P, P, I64, P, P, P], ctypes.c_int32),
         "gs_count_disconnected": ([P, P, P, I64, P, ctypes.POINTER(GsSumsDisc), P],
                                   ctypes.c_int32),
         "gs_estimate_disconnected": ([ctypes.POINTER(GsSumsDisc), D,
@@ -431,6 +432,14 @@ def gs_count_adaptive(graph: int, ws: int, beta: float, t_max: int = 20, phi: fl
                                    ctypes.byref(res), ctypes.byref(iters), ctypes.byref(frac),
                                    _stream_ptr(stream)))
     return sums, res, iters.value, frac.value
+
+
+def gs_per_edge_numerators(graph: int, ws: int, pairs, k: int, per_edge, out, stream=None) -> None:
+    """out: CUDA int64 [k, 8] <- (N3, N4, N7, N8, N9, N10, N11, N12) per edge."""
+    import torch
+    _check(lib().gs_per_edge_numerators(graph, ws, _dev(pairs, torch.int32, "pairs"), k,
+                                        _dev(per_edge, torch.int64, "per_edge"),
+                                        _dev(out, torch.int64, "out"), _stream_ptr(stream)))
 
 
 def gs_estimate_disconnected(sums: GsSumsDisc, z: float = 1.96) -> GsResultDisc:

@@ -161,3 +161,66 @@ extern "C" gs_status gs_count_disconnected(const gs_graph* g, gs_workspace* ws, 
   h_out->overflow = hf[0];
   return GS_OK;
 }
+
+// ------------------------------------------------- per-edge numerator matrix
+
+namespace {
+
+// Row e of out = (N3, N4, N7, N8, N9, N10, N11, N12) of sampled edge e.
+__global__ void k_per_edge_numerators(const int64_t* __restrict__ row_ptr, int64_t n,
+                                      const int32_t* __restrict__ pairs, int64_t K,
+                                      const int64_t* __restrict__ per_edge,
+                                      int64_t* __restrict__ out, unsigned* __restrict__ bad) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < K;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = pairs[2 * e], y = pairs[2 * e + 1];
+    if (x < 0 || y < 0 || x >= n || y >= n) {
+      atomicOr(bad, 1u);
+      continue;
+    }
+    const int64_t du = row_ptr[x + 1] - row_ptr[x], dv = row_ptr[y + 1] - row_ptr[y];
+    const int64_t t = per_edge[3 * e], kk = per_edge[3 * e + 1], qq = per_edge[3 * e + 2];
+    const int64_t a = du - 1 - t, b = dv - 1 - t;
+    const int64_t n8 = t * (t - 1) / 2 - kk;
+    int64_t* o = out + 8 * e;
+    o[0] = t;
+    o[1] = a + b;
+    o[2] = kk;
+    o[3] = n8;
+    o[4] = t * (a + b) - 4 * n8;
+    o[5] = qq;
+    o[6] = 2 * (a * (a - 1) / 2 + b * (b - 1) / 2) - t * (a + b) + 4 * n8;
+    o[7] = a * b - qq;
+  }
+}
+
+}  // namespace
+
+extern "C" gs_status gs_per_edge_numerators(const gs_graph* g, gs_workspace* ws,
+                                            const int32_t* d_pairs, int64_t k,
+                                            const int64_t* d_per_edge, int64_t* d_out,
+                                            void* stream_) {
+  using namespace gs;
+  if (g == nullptr || ws == nullptr || k < 0 ||
+      (k > 0 && (d_pairs == nullptr || d_per_edge == nullptr || d_out == nullptr))) {
+    set_error("gs_per_edge_numerators: invalid arguments");
+    return GS_EINVAL;
+  }
+  if (k == 0) return GS_OK;
+  cudaStream_t stream = (cudaStream_t)stream_;
+  void* base = nullptr;
+  GS_TRY(ws_reserve(ws, 0, Carve::bytes_for<unsigned>(1), stream, &base));
+  unsigned* bad = (unsigned*)base;
+  GS_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned), stream));
+  k_per_edge_numerators<<<grid_for(k, kDiscThreads, 8), kDiscThreads, 0, stream>>>(
+      g->dev.row_ptr, g->dev.n, d_pairs, k, d_per_edge, d_out, bad);
+  GS_CUDA(cudaGetLastError());
+  unsigned hb = 0;
+  GS_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(hb), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  if (hb != 0) {
+    set_error("gs_per_edge_numerators: a sampled pair names a vertex outside the graph");
+    return GS_EINVAL;
+  }
+  return GS_OK;
+}

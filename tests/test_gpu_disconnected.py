@@ -86,3 +86,22 @@ def test_disconnected_rejects_pairs_outside_the_graph():
     with pytest.raises(gs.GraphletError):
         gs.gs_count_disconnected(g.handle, g.ws.handle, pairs, 1, per)
     g.close()
+
+
+def test_per_edge_numerator_rows_match_the_oracle_and_sum_to_the_totals():
+    rp, col = synth.chung_lu(20000, 150000, 2.1, 1500.0, seed=77)
+    g = gs.Graph.from_numpy(rp, col)
+    pairs_np = synth.explicit_sample(rp, col, 0.05, seed=6)
+    pairs = torch.as_tensor(pairs_np, dtype=torch.int32, device="cuda")
+    k = pairs.shape[0]
+    per = torch.empty((k, 3), dtype=torch.int64, device="cuda")
+    sums = g.count(pairs, gs.GS_CONNECTED, per_edge=per)
+    rows = torch.empty((k, 8), dtype=torch.int64, device="cuda")
+    gs.gs_per_edge_numerators(g.handle, g.ws.handle, pairs, k, per, rows)
+    got = rows.cpu().numpy()
+    _, _, want = oracle.numerators(oracle.local_counts(rp, col, pairs_np), per_edge=True)
+    assert np.array_equal(got, want)
+    tot = sums.sums()
+    for i, gid in enumerate(gs.GRAPHLETS):
+        assert int(got[:, i].astype(object).sum()) == tot[gid][0]
+    g.close()
