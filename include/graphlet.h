@@ -304,8 +304,8 @@ gs_status gs_count_disconnected(const gs_graph* g, gs_workspace* ws, const int32
                                 int64_t k, const int64_t* d_per_edge, gs_sums_disc* h_out,
                                 void* stream);
 
-/* Micro-level output (Sec. 5's per-edge statistics, exact when every probe
- * is made): row e of d_out (device int64[8k]) receives the per-edge
+/* Micro-level output (the per-edge statistics of Algorithm 7, here the
+ * exact case p_e = 1 that the counts fix): row e of d_out (device int64[8k]) receives the per-edge
  * numerators (N3, N4, N7, N8, N9, N10, N11, N12) of sampled edge e, from
  * the per-edge (t, k, q) that gs_count wrote for the same list with mask
  * GS_CONNECTED (N9 and N11 can be negative). The rows sum to gs_count's
