@@ -304,13 +304,13 @@ gs_status gs_count_disconnected(const gs_graph* g, gs_workspace* ws, const int32
                                 int64_t k, const int64_t* d_per_edge, gs_sums_disc* h_out,
                                 void* stream);
 
-/* Micro-level output (the per-edge statistics of Algorithm 7, here the
- * exact case p_e = 1 that the counts fix): row e of d_out (device int64[8k]) receives the per-edge
- * numerators (N3, N4, N7, N8, N9, N10, N11, N12) of sampled edge e, from
- * the per-edge (t, k, q) that gs_count wrote for the same list with mask
- * GS_CONNECTED (N9 and N11 can be negative). The rows sum to gs_count's
- * sums. Asynchronous apart from the final status check, which synchronises
- * `stream`. */
+/* Per-edge numerators (micro-level output): row e of d_out (device
+ * int64[8k]) receives (N3, N4, N7, N8, N9, N10, N11, N12) of sampled edge e
+ * (the numerators of gs_estimate; t, a+b, k, C(t,2) - k, q and ab - q are
+ * also Algorithm 7's exact per-edge statistics x3, x4, x7, x8, x10, x12),
+ * from the per-edge (t, k, q) that gs_count wrote for the same list with
+ * mask GS_CONNECTED (N9 and N11 can be negative). The rows sum to
+ * gs_count's sums. Synchronises `stream`. */
 gs_status gs_per_edge_numerators(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs,
                                  int64_t k, const int64_t* d_per_edge, int64_t* d_out,
                                  void* stream);
