@@ -125,8 +125,9 @@ const char* gs_version(void);
  * vertices, plus a mid x big co-degree table and adjacency bucket
  * directories, see gs_graph_index_info) in library-owned device memory;
  * hub_budget_bytes bounds that index (0 = default 20 GiB: bitmaps and
- * matrix up to 1/8 each, directories up to 1/16, the table the rest, at
- * most 65535 vertices, the mid x big table whatever remains).
+ * matrix up to 1/8 each, directories up to 1/16, the 16-bit co-degree table
+ * most of the rest, at most 65535 vertices, the mid x big table and a table
+ * slot per adjacency entry whatever remains).
  * Synchronises `stream`. */
 gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n, int64_t nnz,
                           uint32_t flags, uint64_t hub_budget_bytes, void* stream,

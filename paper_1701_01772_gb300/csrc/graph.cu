@@ -537,9 +537,11 @@ static gs_status hub_threshold(const gs_graph* g, int64_t cap, int64_t min_deg,
   return GS_OK;
 }
 
-// Builds bitmaps (up to 1/8 of the budget), the hub-pair matrix (up to 1/8,
-// at most kHubMatrixMax vertices) and the co-degree table (the rest) within
-// `budget` bytes (0 = 20 GiB).
+// Builds, within `budget` bytes (0 = 20 GiB): bitmaps (up to 1/8 of the
+// budget), the hub-pair matrix (up to 1/8, at most kHubMatrixMax vertices),
+// bucket directories (up to 1/16), the 16-bit co-degree table (most of the
+// rest, at most 65535 vertices), the mid x big table and, if room is left,
+// the table slot of every adjacency entry.
 static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stream) {
   const int64_t n = g->dev.n;
   if (budget == 0) budget = (uint64_t)20 << 30;
