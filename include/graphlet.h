@@ -321,6 +321,10 @@ gs_status gs_per_edge_numerators(const gs_graph* g, gs_workspace* ws, const int3
  * counts when k = m, with GS_F_OVERFLOW when a count does not fit uint64). */
 gs_status gs_estimate_disconnected(const gs_sums_disc* s, double z, gs_result_disc* out);
 
+/* gs_sums_merge for the disconnected sums (host only): acc += part; both
+ * from the same graph (m, n), disjoint samples. */
+gs_status gs_sums_disc_merge(gs_sums_disc* acc, const gs_sums_disc* part);
+
 /* Exact merge of the sums of disjoint shards of one sample (host only):
  * acc += part. Splitting J across GPUs and merging their sums gives the
  * same result as counting J on one GPU (the only exchange the path needs;

@@ -189,6 +189,8 @@ def lib() -> ctypes.CDLL:
                                ctypes.POINTER(GsResult), ctypes.POINTER(ctypes.c_int32),
                                ctypes.POINTER(ctypes.c_double), P], ctypes.c_int32),
         "gs_per_edge_numerators": ([P, P, P, I64, P, P, P], ctypes.c_int32),
+        "gs_sums_disc_merge": ([ctypes.POINTER(GsSumsDisc), ctypes.POINTER(GsSumsDisc)],
+                               ctypes.c_int32),
         "gs_count_disconnected": ([P, P, P, I64, P, ctypes.POINTER(GsSumsDisc), P],
                                   ctypes.c_int32),
         "gs_estimate_disconnected": ([ctypes.POINTER(GsSumsDisc), D,
@@ -440,6 +442,25 @@ def gs_per_edge_numerators(graph: int, ws: int, pairs, k: int, per_edge, out, st
     _check(lib().gs_per_edge_numerators(graph, ws, _dev(pairs, torch.int32, "pairs"), k,
                                         _dev(per_edge, torch.int64, "per_edge"),
                                         _dev(out, torch.int64, "out"), _stream_ptr(stream)))
+
+
+def disc_sums_from_ints(k: int, m: int, n: int, sums: dict, sq: dict) -> GsSumsDisc:
+    """Packs exact Python-int sums {graphlet: value} (graphlets of DISCONNECTED)
+    into a GsSumsDisc."""
+    out = GsSumsDisc()
+    out.k, out.m, out.n = k, m, n
+    for i, g in enumerate(DISCONNECTED):
+        s = sums.get(g, 0) % (1 << 128)
+        q = sq.get(g, 0)
+        out.sum[i][0], out.sum[i][1] = s & (2**64 - 1), s >> 64
+        out.sumsq[i][0], out.sumsq[i][1] = q & (2**64 - 1), q >> 64
+    return out
+
+
+def gs_sums_disc_merge(acc: GsSumsDisc, part: GsSumsDisc) -> GsSumsDisc:
+    out = GsSumsDisc.from_buffer_copy(acc)
+    _check(lib().gs_sums_disc_merge(ctypes.byref(out), ctypes.byref(part)))
+    return out
 
 
 def gs_estimate_disconnected(sums: GsSumsDisc, z: float = 1.96) -> GsResultDisc:

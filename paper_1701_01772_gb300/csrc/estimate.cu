@@ -268,3 +268,25 @@ extern "C" gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, doub
   if (fraction_out) *fraction_out = p;
   return GS_OK;
 }
+
+extern "C" gs_status gs_sums_disc_merge(gs_sums_disc* acc, const gs_sums_disc* part) {
+  if (acc == nullptr || part == nullptr || acc->m != part->m || acc->n != part->n ||
+      part->k < 0 || acc->k < 0 || acc->k + part->k > acc->m) {
+    gs::set_error("gs_sums_disc_merge: sums must come from the same graph, with disjoint "
+                  "samples (k_acc + k_part <= m)");
+    return GS_EINVAL;
+  }
+  acc->k += part->k;
+  for (int i = 0; i < 7; ++i) {
+    const u128 s = load_u128(acc->sum[i]) + load_u128(part->sum[i]);
+    const u128 a = load_u128(acc->sumsq[i]), b = load_u128(part->sumsq[i]);
+    const u128 q = a + b;
+    if (q < a) acc->overflow |= 1u << i;
+    acc->sum[i][0] = (uint64_t)s;
+    acc->sum[i][1] = (uint64_t)(s >> 64);
+    acc->sumsq[i][0] = (uint64_t)q;
+    acc->sumsq[i][1] = (uint64_t)(q >> 64);
+  }
+  acc->overflow |= part->overflow;
+  return GS_OK;
+}
