@@ -245,9 +245,12 @@ gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
  * phi_t of the edges not yet sampled -- counts only those (mask as in
  * gs_count), merges their exact sums into the running ones and
  * re-estimates; phi_{t+1} = phi_t / 2. The loss is the maximum relative
- * change over the graphlets of the mask, max_i |X_i^(t) - X_i^(t-1)| /
- * |X_i^(t-1)| (graphlets with X^(t-1) = 0 are skipped); the first iteration
- * has no previous estimate (loss 1). The loop stops when the loss is at most
+ * change max_i |X_i^(t) - X_i^(t-1)| / |X_i^(t-1)| over the 4-node
+ * graphlets of the mask (the objective of Sec. 4 takes its maximum over
+ * G^(4); a mask with none uses its 3-node graphlets); an unchanged estimate
+ * counts 0 (also 0 -> 0), a change away from 0 counts as infinite. An
+ * iteration with no earlier defined estimate (the first, or every earlier
+ * sample empty) has loss 1. The loop stops when the loss is at most
  * beta (0 <= beta < 1; the first iteration always runs) or after t_max
  * iterations. phi <= 0 selects phi_1 = 1 / sqrt(m).
  * Outputs (host): the running sums, their estimates (z as gs_estimate),
@@ -440,25 +443,28 @@ gs_status gs_server_destroy(gs_server* s);
  * with mask GS_G3 and/or GS_G4 (the mask must be a non-empty subset of
  * GS_THREE_NODE), but never calls cudaMalloc, cudaFree or any allocating
  * routine. It is meant for callers that cannot allocate device memory at
- * the time they count: code recording a CUDA graph (allocation is illegal
- * while a stream is captured), hosts that give the GPU a fixed memory pool
- * and forbid growth, or latency paths where a device-wide synchronising
- * cudaMalloc/cudaFree is not acceptable. The graph must still have been
- * registered with gs_graph_create beforehand.
+ * the time they count: hosts that give the GPU a fixed memory pool when
+ * they start and forbid any growth afterwards (an allocation that fails in
+ * the middle of a request is not acceptable there), and latency paths where
+ * a cudaMalloc / cudaFree pair, which can wait for the whole device to go
+ * idle, costs too much. The graph must still have been registered with
+ * gs_graph_create beforehand.
  *
  * Its scratch is one file-scope device array of GS_STATIC_SCRATCH_BYTES
- * (48 MiB), reserved on every GPU that loads the library until the process
- * exits. d_pairs: device int32[2*k], k <= GS_STATIC_MAX_PAIRS (2^20), each
- * pair an edge in either orientation, no edge twice; larger k is rejected
- * with GS_ECAPACITY (use gs_count). h_sums is host memory. The call
+ * (48 MiB). Every GPU that loads the library's code holds it until the
+ * process exits; with lazy module loading (the CUDA default) that can
+ * happen only at the first call on that device. d_pairs: device
+ * int32[2*k], k <= GS_STATIC_MAX_PAIRS (2^20), each pair an edge in either
+ * orientation, no edge twice; larger k is rejected with GS_ECAPACITY before
+ * anything is read (use gs_count). h_sums is host memory. The call
  * synchronises `stream`.
  *
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any
- * stream capture begins. All calls share the one array and it keeps the
- * previous call's contents (the call clears what must start at zero), so
- * calls whose GPU work overlaps -- on different streams or host threads,
- * for the same device -- race and give wrong results: serialise them.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (once per device, with that device current). All
+ * calls share the one array and it keeps the previous call's contents (the
+ * call clears what must start at zero), so calls whose GPU work overlaps --
+ * on different streams or host threads, for the same device -- race and
+ * give wrong results: serialise them.
  * ------------------------------------------------------------------------ */
 #define GS_STATIC_MAX_PAIRS (1 << 20)
 #define GS_STATIC_SCRATCH_BYTES (48u << 20)

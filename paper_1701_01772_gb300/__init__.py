@@ -253,6 +253,15 @@ def _dev(t, dtype, name):
     return t.data_ptr()
 
 
+def _check_pairs(pairs, k: int) -> None:
+    """A sampled-edge list is a [rows, 2] tensor holding at least k rows (the
+    library reads exactly k pairs)."""
+    if pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must be a [k, 2] tensor")
+    if not 0 <= k <= pairs.shape[0]:
+        raise ValueError(f"k = {k} outside [0, {pairs.shape[0]}] (rows of pairs)")
+
+
 # ------------------------------------------------------------------ C names
 
 def gs_version() -> str:
@@ -330,6 +339,11 @@ def gs_count(graph: int, ws: int, pairs, k: int, mask: int = GS_CONNECTED, per_e
     """pairs: CUDA int32 [k, 2] or None (all edges). per_edge: optional CUDA
     int64 [k, 3] receiving (t, k, q) per pair."""
     import torch
+    if pairs is not None:
+        _check_pairs(pairs, k)
+    if per_edge is not None and (per_edge.dim() != 2 or per_edge.shape[1] != 3
+                                 or per_edge.shape[0] < k):
+        raise ValueError("per_edge must be a [>= k, 3] tensor")
     out = GsSums()
     _check(lib().gs_count(graph, ws, None if pairs is None else _dev(pairs, torch.int32, "pairs"),
                           k, mask,
@@ -347,6 +361,8 @@ def gs_count3_static(graph: int, pairs, k: int, mask: int = GS_THREE_NODE,
     static scratch (no device allocation); k <= GS_STATIC_MAX_PAIRS. See
     include/graphlet.h for who needs it and its concurrency rules."""
     import torch
+    if pairs is not None:
+        _check_pairs(pairs, k)
     out = GsSums()
     _check(lib().gs_count3_static(graph, None if pairs is None else _dev(pairs, torch.int32, "pairs"),
                                   k, mask, ctypes.byref(out), _stream_ptr(stream)))

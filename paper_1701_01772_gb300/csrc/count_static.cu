@@ -3,12 +3,11 @@
 // inputs and outputs lives in one file-scope device array whose size is
 // fixed at compile time.
 //
-// Who needs this: code that runs where cudaMalloc is not allowed or not
-// wanted -- while a CUDA stream is being captured into a graph (allocation
-// calls are illegal there), inside a host that hands the GPU a fixed memory
-// pool up front and forbids later growth (embedded or real-time serving),
-// or on a latency path where a cudaMalloc / cudaFree pair (which can
-// synchronise the whole device) is too costly. The graph itself is still
+// Who needs this: hosts that hand the GPU a fixed memory pool when they
+// start and forbid any later growth (embedded or real-time serving, where a
+// failed allocation in the middle of a request is not an option), and
+// latency paths where a cudaMalloc / cudaFree pair is too costly (both can
+// wait for the whole device to become idle). The graph itself is still
 // registered once with gs_graph_create at set-up time.
 #include <mutex>
 #include <string.h>
@@ -39,7 +38,8 @@ constexpr int kThreads = 256;
 constexpr int kFoldBlocksMax = 1024;
 
 // The scratch: GS_STATIC_SCRATCH_BYTES of device memory, reserved on every
-// GPU that loads this library for as long as the library stays loaded.
+// GPU that loads this library's code (possibly only at the first call, when
+// the CUDA runtime loads modules lazily) for as long as the process runs.
 static __device__ __align__(256) unsigned char g_static_scratch[GS_STATIC_SCRATCH_BYTES];
 
 // Device address of g_static_scratch per device. In host code the symbol
