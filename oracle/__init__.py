@@ -271,6 +271,30 @@ def disconnected_estimate(row_ptr, col, pairs, z: float = Z95) -> dict:
     return res
 
 
+#: the 4-node graphlets over which Algorithm 8's objective takes its maximum
+FOUR_NODE = (7, 8, 9, 10, 11, 12)
+
+
+def adaptive_loss_graphlets(graphlets) -> tuple:
+    """Graphlets whose relative change is Algorithm 8's loss: the objective
+    of Sec. 4 takes the maximum over the 4-node graphlets G^(4); a request
+    holding no 4-node graphlet falls back to its 3-node ones."""
+    four = tuple(g for g in graphlets if g in FOUR_NODE)
+    return four if four else tuple(graphlets)
+
+
+def relative_change(x: float, prev: float) -> float:
+    """|x - prev| / |prev| (the maximum-relative-error objective of Sec. 4
+    with the previous estimate as reference); no change counts 0 even when
+    both are 0, a change away from 0 counts as infinitely large."""
+    if x == prev:
+        return 0.0
+    if prev == 0.0:
+        return math.inf
+    r = abs(x - prev) / abs(prev)
+    return math.inf if math.isnan(r) else r
+
+
 def adaptive_estimate(row_ptr, col, beta: float, t_max: int, phi: float, seed: int,
                       graphlets=GRAPHLETS, z: float = Z95) -> dict:
     """Algorithm 8 with the Bernoulli sampler of ``sample``: iteration t
@@ -278,13 +302,16 @@ def adaptive_estimate(row_ptr, col, beta: float, t_max: int, phi: float, seed: i
     fraction goes from p to p + phi (1 - p), which adds exactly the edges
     whose key lies between the two, since the samples are nested), recomputes
     the estimates from everything sampled so far, takes as loss the maximum
-    relative change max_i |X_i^(t) - X_i^(t-1)| / |X_i^(t-1)| (skipping
-    X^(t-1) = 0; none on the first iteration, loss 1) and halves phi; it
-    stops when the loss is at most beta or after t_max iterations.
-    phi <= 0 means 1 / sqrt(M)."""
+    relative change (``relative_change``) of the estimates of the 4-node
+    graphlets among ``graphlets`` (``adaptive_loss_graphlets``) since the
+    previous iteration, and halves phi after the draw; it stops when the
+    loss is at most beta or after t_max iterations. An iteration with no
+    previous defined estimate (the first, or every earlier sample empty) has
+    loss 1. phi <= 0 means 1 / sqrt(M)."""
     m = len(col) // 2
     if not phi > 0:
         phi = 1.0 / math.sqrt(m) if m > 0 else 1.0
+    loss_set = adaptive_loss_graphlets(graphlets)
     p, loss, t = 0.0, 1.0, 0
     prev = None
     pairs = np.zeros((0, 2), dtype=np.int32)
@@ -295,16 +322,13 @@ def adaptive_estimate(row_ptr, col, beta: float, t_max: int, phi: float, seed: i
         lc = local_counts(row_ptr, col, pairs)
         s, s2 = numerators(lc)
         est = estimate(s, s2, m, len(pairs), z)
-        x = {g: est[g]["X"] for g in graphlets}
+        x = {g: est[g]["X"] for g in loss_set}
         if prev is None:
             loss = 1.0
         else:
-            loss = 0.0
-            for g in graphlets:
-                if prev[g] != 0.0 and not math.isnan(prev[g]):
-                    r = abs(x[g] - prev[g]) / abs(prev[g])
-                    loss = max(loss, math.inf if math.isnan(r) else r)
-        prev = x
+            loss = max(relative_change(x[g], prev[g]) for g in loss_set)
+        if len(pairs) > 0:
+            prev = x
         p = p_new
         phi *= 0.5
         t += 1

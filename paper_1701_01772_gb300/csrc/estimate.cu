@@ -231,6 +231,12 @@ extern "C" gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, doub
   memset(sums_out, 0, sizeof(*sums_out));
   sums_out->m = M;
   sums_out->mask = mask;
+  // The loss runs over the 4-node graphlets of the mask (the objective of
+  // Sec. 4 takes its maximum over G^(4)); a mask without any falls back to
+  // its 3-node graphlets.
+  const uint32_t four = mask & (GS_G7 | GS_G8 | GS_G9 | GS_G10 | GS_G11 | GS_G12);
+  const uint32_t loss_mask = four != 0 ? four : mask;
+  static const uint32_t bit[8] = {GS_G3, GS_G4, GS_G7, GS_G8, GS_G9, GS_G10, GS_G11, GS_G12};
   double p = 0.0, loss = 1.0;
   double prev[8];
   bool have_prev = false;
@@ -248,18 +254,25 @@ extern "C" gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, doub
       GS_TRY(gs_sums_merge(sums_out, &part));
     }
     GS_TRY(gs_estimate(sums_out, z, out));
+    // relative change since the previous defined estimate: none counts 0
+    // (also 0 -> 0), a change away from 0 counts as infinitely large
     double l = 0.0;
     for (int i = 0; i < 8; ++i) {
-      if (!(out->flags[i] & GS_F_COMPUTED)) continue;
-      if (have_prev && prev[i] != 0.0 && !isnan(prev[i])) {
-        double r = fabs(out->x[i] - prev[i]) / fabs(prev[i]);
-        if (isnan(r)) r = INFINITY;  // an undefined change counts as large
+      if (!(loss_mask & bit[i])) continue;
+      if (have_prev) {
+        double r = 0.0;
+        if (out->x[i] != prev[i]) {
+          r = prev[i] == 0.0 ? INFINITY : fabs(out->x[i] - prev[i]) / fabs(prev[i]);
+          if (isnan(r)) r = INFINITY;
+        }
         if (r > l) l = r;
       }
-      prev[i] = out->x[i];
     }
     loss = have_prev ? l : 1.0;
-    have_prev = true;
+    if (sums_out->k > 0) {  // an empty sample has no estimate to compare with
+      for (int i = 0; i < 8; ++i) prev[i] = out->x[i];
+      have_prev = true;
+    }
     p = p_new;
     phi *= 0.5;
     ++t;
