@@ -1,14 +1,18 @@
 #!/usr/bin/env python
 """Benchmark: sampled edges/s for connected 3- and 4-node graphlet estimation.
 
-One step = the whole estimation path on the 1M-vertex Chung-Lu workload
-(n = 1,000,000, m ~ 20M, degree exponent 2.1, expected degree capped at
-50,000): for each edge-sample fraction (1%, 5%, 10% and exact at 100%) the
-library samples the edges on the device, counts all connected 3- and 4-node
-graphlets around them, folds the exact sums and returns estimates, variances
-and 95% bounds. value = sampled edges processed / device time.
+Headline workload (the largest configuration that fits one GPU): R-MAT scale
+24, edge factor 16, (a, b, c, d) = (0.57, 0.19, 0.19, 0.05), symmetrised,
+deduplicated, self-loops removed (16,777,216 vertices, 260,388,226 edges).
+One step = exact 3-node counts over every edge, then 4-node estimates (all
+connected graphlets, with variances and 95% bounds) on seeded edge samples of
+0.1% and 1% drawn by the library's sampler on the device.
+value = edges processed / device time. The 1M-vertex Chung-Lu configuration
+(fractions 1%, 5%, 10% and exact) is measured after it and reported under
+"extra".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                  [--workload rmat_24|chung_lu_1m|batch|serve]
 
 Under torchrun (N > 1) every rank runs the same step with its own seeds on its
 own GPU (weak scaling, no data-path collective); the time is the max over
@@ -31,10 +35,28 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sampled edges/s for 4-node graphlet counts; p50/p99 estimate latency"
 UNIT = "edges/s"
-WORKLOAD = ("chung_lu_1m: Chung-Lu n=1,000,000, m~20M, degree exponent 2.1, expected degree "
-            "cap 50,000, int32 CSR; edge-sample fractions 1%, 5%, 10% (seeded, library "
-            "sampler) plus exact counts at fraction 1; graphlets G3,G4,G7-G12")
-FRACTIONS = (0.01, 0.05, 0.10, 1.0)
+THREE, CONN = (1 << 3) | (1 << 4), sum(1 << b for b in (3, 4, 7, 8, 9, 10, 11, 12))
+
+# workload name -> (description, [(label, fraction, mask)])
+WORKLOADS = {
+    "rmat_24": (
+        "rmat_24: R-MAT scale 24, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
+        "symmetrised, deduplicated, self-loops removed (16,777,216 vertices, 260,388,226 "
+        "edges), int32 CSR; exact 3-node counts (G3, G4) over all edges plus 4-node "
+        "estimates (G3, G4, G7-G12) at 0.1% and 1% edge samples (seeded, library sampler)",
+        [("exact_3node", 1.0, THREE), ("0.001", 0.001, CONN), ("0.01", 0.01, CONN)]),
+    "chung_lu_1m": (
+        "chung_lu_1m: Chung-Lu n=1,000,000, m~20M, degree exponent 2.1, expected degree "
+        "cap 50,000, int32 CSR; edge-sample fractions 1%, 5%, 10% (seeded, library sampler) "
+        "plus exact counts at fraction 1; graphlets G3,G4,G7-G12",
+        [("0.01", 0.01, CONN), ("0.05", 0.05, CONN), ("0.1", 0.10, CONN), ("exact", 1.0, CONN)]),
+}
+# algorithmic bytes of the 4-node phase: a membership test reads one 4-byte
+# element of the iterated list and one 4-byte word (bitmap or matrix word,
+# directory entry, list entry) that answers it; a dense-edge matrix group
+# ANDs one 16-byte row group with the edge's 16-byte T-mask group
+BYTES_PER_TEST = 8
+BYTES_PER_DENSE_GROUP = 32
 
 
 def parse():
@@ -43,18 +65,28 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
-    ap.add_argument("--fractions", type=str, default=",".join(str(f) for f in FRACTIONS))
     ap.add_argument("--hub-budget", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("chung_lu_1m", "batch", "serve"), default="chung_lu_1m",
-                    help="chung_lu_1m = the headline line; batch / serve = the batched and "
-                         "served paths against one plain launch per graph / request")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the Chung-Lu 1M measurement after the headline")
+    ap.add_argument("--extra-steps", type=int, default=5)
+    ap.add_argument("--workload", choices=("rmat_24", "chung_lu_1m", "batch", "serve"),
+                    default="rmat_24",
+                    help="rmat_24 = the headline line; chung_lu_1m alone; batch / serve = the "
+                         "batched and served paths against one plain launch per graph / request")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-loads", type=str, default="0.3,0.6,0.9",
+                    help="offered loads as fractions of the measured capacity")
     return ap.parse_args()
+
+
+def generate(name):
+    import synth
+    return synth.rmat_24() if name == "rmat_24" else synth.chung_lu_1m()
 
 
 # ------------------------------------------------------------------ helpers
@@ -84,14 +116,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def load_traffic(key: str):
+    """DRAM bytes per test from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
-        rec = t.get(kernel)
+        rec = t.get(key)
         if rec and rec.get("source_hash") == kernel_source_hash():
             return rec
     except Exception:
@@ -172,201 +204,183 @@ def incidences_from_numerators(n: dict) -> int:
     sum over e of t + a + b + k + C(t,2) + t(a+b) + q + C(a,2) + C(b,2) + ab,
     from the exact numerator sums {i: sum N_i}: N3 + N4 + 2 N7 + 5 N8
     + (3 N9 + N11) / 2 + 2 N10 + N12, where per edge
-    (3 N9 + N11) / 2 = t(a+b) - 4 N8 + C(a,2) + C(b,2) is an integer."""
-    return (n[3] + n[4] + 2 * n[7] + 5 * n[8] + (3 * n[9] + n[11]) // 2 + 2 * n[10] + n[12])
+    (3 N9 + N11) / 2 = t(a+b) - 4 N8 + C(a,2) + C(b,2) is an integer.
+    Graphlets outside the mask count 0."""
+    g = lambda i: n.get(i, 0)  # noqa: E731
+    return (g(3) + g(4) + 2 * g(7) + 5 * g(8) + (3 * g(9) + g(11)) // 2 + 2 * g(10) + g(12))
 
 
-def run_gpu(args, rank, world, device):
-    import numpy as np
+def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
     import torch
 
     import paper_1701_01772_gb300 as gs
-    import synth
 
     torch.cuda.set_device(device)
     gs.build()
-    rp, col = synth.chung_lu_1m()
-    g = gs.Graph.from_numpy(rp, col, device=f"cuda:{device}", hub_budget_bytes=args.hub_budget)
+    desc, parts = WORKLOADS[name]
+    dev = f"cuda:{device}"
+    row_ptr = torch.as_tensor(rp, device=dev)
+    colt = torch.as_tensor(col, device=dev)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    t0 = time.perf_counter()
+    g = gs.Graph(row_ptr, colt, hub_budget_bytes=args.hub_budget)
+    torch.cuda.synchronize()
+    registration_s = time.perf_counter() - t0
+    free1, _ = torch.cuda.mem_get_info()
+    index_bytes = free0 - free1
     ws = g.ws
     ws.set_timing(True)
-    fractions = [float(x) for x in args.fractions.split(",")]
     stream = torch.cuda.current_stream()
     m = g.m
-    cap = int(max(fractions[:-1] if fractions[-1] == 1.0 else fractions) * m * 1.05) + 1024
-    pair_buf = torch.empty((min(cap, m), 2), dtype=torch.int32, device=f"cuda:{device}")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{device}")
+    sampled = [f for _, f, _ in parts if f < 1.0]
+    cap = int(max(sampled) * m * 1.05) + 1024 if sampled else 1
+    pair_buf = torch.empty((min(cap, m), 2), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def seed_of(step, fi):
         return (rank * 1_000_003 + step * 101 + fi * 7 + 1) & (2**63 - 1)
 
-    def incidences(sums) -> int:
-        return incidences_from_numerators({gid: v[0] for gid, v in sums.sums().items()})
-
-    def one_step(step, record):
-        """Sample + count + estimate for every fraction; returns (edges, per-call ms)."""
-        edges = 0
-        lat = []
-        quad = []
-        inc = 0
-        for fi, f in enumerate(fractions):
+    def one_step(step):
+        """Every part of the workload: sample (fraction < 1) + count +
+        estimate. Returns (edges, [(label, ms)], [(stats)], incidences)."""
+        edges, lat, quad, inc = 0, [], [], 0
+        for fi, (label, f, mask) in enumerate(parts):
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
             if f >= 1.0:
-                sums = gs.gs_count(g.handle, ws.handle, None, m, gs.GS_CONNECTED)
+                sums = gs.gs_count(g.handle, ws.handle, None, m, mask)
                 k = m
             else:
                 k = gs.gs_sample(g.handle, ws.handle, f, seed_of(step, fi), pair_buf)
-                sums = gs.gs_count(g.handle, ws.handle, pair_buf[:k], k, gs.GS_CONNECTED)
-            res = gs.gs_estimate(sums)
+                sums = gs.gs_count(g.handle, ws.handle, pair_buf[:k], k, mask)
+            gs.gs_estimate(sums)
             ev1.record(stream)
             st = gs.gs_count_stats(ws.handle)
             torch.cuda.synchronize()
-            lat.append((f, ev0.elapsed_time(ev1)))
-            quad.append((st.ms_quad, st.model_quad_bytes, st.quad_tests))
+            lat.append((label, ev0.elapsed_time(ev1)))
+            quad.append((st.ms_quad, st.quad_tests - st.dense_groups, st.dense_groups,
+                         st.model_quad_bytes))
             edges += k
-            inc += incidences(sums)
-            if record is not None:
-                record.append({"f": f, "K": k, "x": [res.x[i] for i in range(8)]})
+            inc += incidences_from_numerators({gid: v[0] for gid, v in sums.sums().items()})
         return edges, lat, quad, inc
 
-    # warm-up
-    for w in range(args.warmup):
+    for w in range(warmup):
         flush.fill_(w & 0xFF)
-        one_step(10_000 + w, None)
-    quad_launches = 0
+        one_step(10_000 + w)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     total_edges, total_ms, total_inc = 0, 0.0, 0
-    lat_by_f = {f: [] for f in fractions}
-    quad_ms, quad_bytes, quad_tests, launches = 0.0, 0, 0, 0
-    quad_launches = 0
-    wall0 = time.perf_counter()
+    lat_by = {label: [] for label, _, _ in parts}
+    quad_ms, tests, groups, model_bytes, quad_launches = 0.0, 0, 0, 0, 0
     launches0 = gs.gs_count_stats(ws.handle).launches_total
     with ClockSampler(device) as clocks:
-        for step in range(args.steps):
+        for step in range(steps):
             flush.fill_((step + 1) & 0xFF)  # L2 flush, outside the timed events
             torch.cuda.synchronize()
-            e, lat, quad, inc = one_step(step, None)
+            e, lat, quad, inc = one_step(step)
             total_edges += e
             total_inc += inc
             total_ms += sum(ms for _, ms in lat)
-            for f, ms in lat:
-                lat_by_f[f].append(ms)
-            for qms, qb, qt in quad:
+            for label, ms in lat:
+                lat_by[label].append(ms)
+            for qms, qt, qg, qb in quad:
                 if qms > 0:
                     quad_ms += qms
-                    quad_bytes += qb
-                    quad_tests += qt
+                    tests += qt
+                    groups += qg
+                    model_bytes += qb
                     quad_launches += 1
     torch.cuda.synchronize()
     launches = gs.gs_count_stats(ws.handle).launches_total - launches0
-    wall = time.perf_counter() - wall0
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{device}")
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e = torch.tensor([total_edges, total_inc], dtype=torch.float64, device=f"cuda:{device}")
+        e = torch.tensor([total_edges, total_inc], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(e, op=torch.distributed.ReduceOp.SUM)
         total_ms_max, edges_all, inc_all = float(t.item()), int(e[0].item()), float(e[1].item())
     else:
         total_ms_max, edges_all, inc_all = total_ms, total_edges, float(total_inc)
 
-    # ---- end to end through the C ABI with host buffers: the request's
-    # explicit edge list is copied from pinned host memory, counted and
-    # estimated; the sums come back to the host.
+    # ---- end to end through the C ABI with host buffers: each sampled
+    # part's explicit edge list is copied from pinned host memory, counted
+    # and estimated; the sums come back to the host. The exact pass names
+    # the resident graph's own edges (no input copy).
     host_lists = []
-    for fi, f in enumerate(fractions):
+    for fi, (label, f, mask) in enumerate(parts):
         if f >= 1.0:
-            host_lists.append(None)
+            host_lists.append((None, mask))
         else:
             k = gs.gs_sample(g.handle, ws.handle, f, seed_of(5000, fi), pair_buf)
-            host_lists.append(pair_buf[:k].cpu().pin_memory())
+            host_lists.append((pair_buf[:k].cpu().pin_memory(), mask))
     dev_buf = torch.empty_like(pair_buf)
     e2e_edges, e2e_ms, h2d, d2h = 0, 0.0, 0, 0
-    for step in range(args.steps):
+    for step in range(steps):
         flush.fill_((step + 7) & 0xFF)
         torch.cuda.synchronize()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
-        ev0.record(stream)
-        for f, hl in zip(fractions, host_lists):
+        for hl, mask in host_lists:
             if hl is None:
-                sums = gs.gs_count(g.handle, ws.handle, None, m, gs.GS_CONNECTED)
+                sums = gs.gs_count(g.handle, ws.handle, None, m, mask)
                 e2e_edges += m
             else:
                 k = hl.shape[0]
                 dev_buf[:k].copy_(hl, non_blocking=True)
-                sums = gs.gs_count(g.handle, ws.handle, dev_buf[:k], k, gs.GS_CONNECTED)
+                sums = gs.gs_count(g.handle, ws.handle, dev_buf[:k], k, mask)
                 e2e_edges += k
                 h2d += hl.numel() * 4
             gs.gs_estimate(sums)
             d2h += 280  # gs_sums returned to the host
-        ev1.record(stream)
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e = {"value": e2e_edges / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": h2d // max(args.steps, 1),
-           "d2h_bytes_per_step": d2h // max(args.steps, 1)}
+           "h2d_bytes_per_step": h2d // max(steps, 1),
+           "d2h_bytes_per_step": d2h // max(steps, 1)}
 
     peak, peak_kind = load_peaks()
-    achieved = (quad_bytes / (quad_ms / 1e3)) / 1e9 if quad_ms > 0 else 0.0
-    traffic = load_traffic("quad_phase")
-    tests_per_launch = quad_tests / max(quad_launches, 1)
-    traffic_bytes = (traffic["dram_bytes_per_test"] * tests_per_launch) if traffic else None
-    avg_s = quad_ms / max(quad_launches, 1) / 1e3
-    roofline = {"kernel": "4-node phase: k_quad (membership tests) + k_dense_pairs (dense-edge "
-                          "member pairs)", "bound": "hbm",
-                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-                "traffic": round(traffic_bytes) if traffic_bytes else None,
-                "traffic_source": ("ncu dram bytes of k_quad + k_dense_pairs per membership test "
-                                   "(or matrix group) on a 0.1% sample x tests per launch")
-                if traffic else None,
-                "dram_frac": round(traffic_bytes / avg_s / 1e9 / peak, 4) if traffic_bytes else None,
-                "avg_launch_ms": round(quad_ms / max(quad_launches, 1), 3),
-                "model_bytes_per_launch": quad_bytes // max(quad_launches, 1),
-                "tests_per_s": round(quad_tests / (quad_ms / 1e3), 1) if quad_ms > 0 else None}
-    return {
-        "edges_all": edges_all, "ms_total": total_ms_max, "wall_s": wall, "inc_all": inc_all,
-        "lat": {str(f): {"p50_ms": round(percentile(v, 50), 3), "p99_ms": round(percentile(v, 99), 3)}
-                for f, v in lat_by_f.items()},
-        "e2e": e2e, "roofline": roofline, "launches": launches,
-        "clocks": clocks.summary(), "graph": g.info, "fractions": fractions,
-        "rp": rp, "col": col,
+    alg_bytes = BYTES_PER_TEST * tests + BYTES_PER_DENSE_GROUP * groups
+    secs = quad_ms / 1e3
+    achieved = alg_bytes / secs / 1e9 if secs > 0 else 0.0
+    traffic = load_traffic(f"quad_phase_{name}")
+    units_per_launch = (tests + groups) / max(quad_launches, 1)
+    traffic_bytes = traffic["dram_bytes_per_test"] * units_per_launch if traffic else None
+    avg_s = secs / max(quad_launches, 1)
+    roofline = {
+        "kernel": "4-node phase: k_quad (membership tests) + k_dense_pairs (dense-edge "
+                  "member pairs), all 4-node launches of the timed steps",
+        "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+        "bytes_model": f"{BYTES_PER_TEST} B per membership test + {BYTES_PER_DENSE_GROUP} B per "
+                       "128-bit dense group",
+        "traffic": round(traffic_bytes) if traffic_bytes else None,
+        "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_quad + "
+                           "k_dense_pairs per test on a small case, x tests per launch")
+        if traffic else None,
+        "dram_frac": round(traffic_bytes / avg_s / 1e9 / peak, 4) if traffic_bytes else None,
+        "avg_launch_ms": round(quad_ms / max(quad_launches, 1), 3),
+        "tests_per_launch": round(tests / max(quad_launches, 1)),
+        "dense_groups_per_launch": round(groups / max(quad_launches, 1)),
+        "tests_per_s": round((tests + groups) / secs, 1) if secs > 0 else None,
+        "model_bytes_avoided_per_launch": model_bytes // max(quad_launches, 1),
     }
+    out = {
+        "desc": desc, "edges_all": edges_all, "ms_total": total_ms_max, "inc_all": inc_all,
+        "lat": {label: {"p50_ms": round(percentile(v, 50), 3),
+                        "p99_ms": round(percentile(v, 99), 3)} for label, v in lat_by.items()},
+        "e2e": e2e, "roofline": roofline, "launches": launches, "clocks": clocks.summary(),
+        "graph": g.info, "parts": [label for label, _, _ in parts],
+        "registration_s": round(registration_s, 3), "index_bytes": int(index_bytes),
+        "workspace_bytes": int(ws.nbytes()),
+    }
+    g.close()
+    del pair_buf, flush, dev_buf, row_ptr, colt
+    torch.cuda.empty_cache()
+    return out
 
 
 # ------------------------------------------------------------------ oracle arm
-
-def oracle_rate(rp, col, seconds: float, seed: int = 1):
-    """The CPU oracle (single thread) on the first edges of a 1% sample of
-    the workload, grown until about `seconds` of CPU time."""
-    import oracle
-    pairs = oracle.sample(rp, col, 0.01, seed)
-    n = 16
-    used = 0.0
-    edges = 0
-    while True:
-        chunk = pairs[edges:edges + n]
-        if len(chunk) == 0:
-            break
-        t0 = time.process_time()
-        lc = oracle.local_counts(rp, col, chunk)
-        s, s2 = oracle.numerators(lc)
-        oracle.estimate(s, s2, len(col) // 2, len(chunk))
-        used += time.process_time() - t0
-        edges += len(chunk)
-        if used >= seconds:
-            break
-        n = min(n * 2, 4096)
-    return edges, used, len(pairs)
-
-
-# Worker state of the multi-core oracle baseline (spawned processes).
-_ORACLE_CSR = None
-
 
 def _oracle_worker_init(rp_path, col_path):
     global _ORACLE_CSR
@@ -375,78 +389,108 @@ def _oracle_worker_init(rp_path, col_path):
     _ORACLE_CSR = (np.load(rp_path, mmap_mode="r"), np.load(col_path, mmap_mode="r"))
 
 
-def _oracle_worker_chunk(chunk):
+_ORACLE_CSR = None
+
+
+def _oracle_worker_chunk(job):
     """Per-edge local counts of one chunk of sampled edges by the oracle;
     returns the chunk's exact numerator sums."""
     import numpy as np
     import oracle
+    chunk, four = job
     rp, col = _ORACLE_CSR
-    lc = oracle.local_counts(np.asarray(rp), np.asarray(col), chunk)
+    lc = oracle.local_counts(np.asarray(rp), np.asarray(col), chunk, four=four)
     return oracle.numerators(lc)
 
 
-def oracle_rate_parallel(rp, col, seconds: float, seed: int = 1, workers: int | None = None):
+def oracle_part_rates(rp, col, parts, seconds: float, seed: int = 1, workers: int | None = None):
     """The CPU oracle, unchanged, run by one spawned process per host core
-    over disjoint chunks of a seeded 1% sample: a calibration pass on one
-    core sizes the chunks so the parallel pass takes about `seconds` of wall
-    time. Returns (edges, wall seconds, cores)."""
+    over disjoint chunks of each part's edges (the first edges of a seeded
+    sample at that part's fraction; all edges in canonical order for the
+    exact part): each part gets `seconds` / len(parts) of wall time, sized
+    by a single-core calibration pass. Returns ({label: (edges, wall s)},
+    cores)."""
     import multiprocessing as mp
     import tempfile
 
     import numpy as np
     import oracle
+    import synth
     workers = workers or os.cpu_count() or 1
-    pairs = oracle.sample(rp, col, 0.01, seed)
-    e1, t1, _ = oracle_rate(rp, col, max(0.5, seconds / 10), seed=seed)  # single-core rate
-    per_core = max(16, int(e1 / max(t1, 1e-6) * seconds))
-    total = min(len(pairs), per_core * workers)
-    chunks = [pairs[i:i + max(1, total // (4 * workers))]
-              for i in range(0, total, max(1, total // (4 * workers)))]
+    budget = seconds / max(len(parts), 1)
     tmp = tempfile.mkdtemp(prefix="gs_oracle_")
     rp_path, col_path = os.path.join(tmp, "rp.npy"), os.path.join(tmp, "col.npy")
     np.save(rp_path, rp)
     np.save(col_path, col)
+    rates = {}
     try:
         with mp.get_context("spawn").Pool(workers, _oracle_worker_init, (rp_path, col_path)) as pool:
-            pool.map(_oracle_worker_chunk, [pairs[:workers]], chunksize=1)  # workers up
-            t0 = time.perf_counter()
-            parts = pool.map(_oracle_worker_chunk, chunks, chunksize=1)
-            wall = time.perf_counter() - t0
+            for label, f, mask in parts:
+                four = bool(mask & ~THREE)
+                if f >= 1.0:
+                    pairs = synth.upper_pairs(rp, col)[: max(1, 400_000 * workers)]
+                else:
+                    pairs = oracle.sample(rp, col, f, seed)
+                # single-core calibration
+                n, used, done = 16, 0.0, 0
+                while done < len(pairs) and used < max(0.3, budget / 8):
+                    t0 = time.process_time()
+                    oracle.numerators(oracle.local_counts(rp, col, pairs[done:done + n], four=four))
+                    used += time.process_time() - t0
+                    done += n
+                    n = min(2 * n, 65536)
+                per_core = max(16, int(done / max(used, 1e-6) * budget))
+                total = min(len(pairs), per_core * workers)
+                step = max(1, total // (4 * workers))
+                jobs = [(pairs[i:i + step], four) for i in range(0, total, step)]
+                pool.map(_oracle_worker_chunk, [(pairs[:workers], four)], chunksize=1)
+                t0 = time.perf_counter()
+                pool.map(_oracle_worker_chunk, jobs, chunksize=1)
+                rates[label] = (total, time.perf_counter() - t0)
     finally:
         for f in (rp_path, col_path):
             os.remove(f)
         os.rmdir(tmp)
-    s = {g: sum(p[0][g] for p in parts) for g in parts[0][0]}
-    s2 = {g: sum(p[1][g] for p in parts) for g in parts[0][1]}
-    oracle.estimate(s, s2, len(col) // 2, total)
-    return total, wall, workers
+    return rates, workers
+
+
+def oracle_step_rate(rp, col, parts, seconds, seed=1):
+    """Edges/s of the oracle on one whole step of the workload: each part's
+    measured per-edge rate applied to that part's full edge count."""
+    m = len(col) // 2
+    rates, cores = oracle_part_rates(rp, col, parts, seconds, seed)
+    step_edges = sum(m if f >= 1.0 else f * m for _, f, _ in parts)
+    step_secs = sum((m if f >= 1.0 else f * m) * rates[label][1] / max(rates[label][0], 1)
+                    for label, f, _ in parts)
+    sample = "; ".join(f"{label}: {rates[label][0]} edges in {rates[label][1]:.1f} s"
+                       for label, _, _ in parts)
+    return step_edges / step_secs, cores, sample, sum(r[1] for r in rates.values())
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    import synth
-    rp, col = synth.chung_lu_1m()
-    budget = max(2.0, min(30.0, 100.0 / max(args.steps + args.warmup, 1)))
-    for _ in range(args.warmup):
-        oracle_rate(rp, col, budget / 4, seed=99)
-    edges, secs, cores = 0, 0.0, 1
-    lat = []
-    for step in range(args.steps):
-        e, s, cores = oracle_rate_parallel(rp, col, budget, seed=1 + step)
-        edges += e
-        secs += s
-        lat.append(s * 1e3)
-    value = edges / secs
+    name = "chung_lu_1m" if args.workload == "chung_lu_1m" else "rmat_24"
+    desc, parts = WORKLOADS[name]
+    rp, col = generate(name)
+    budget = max(6.0, min(45.0, 150.0 / max(args.steps + args.warmup, 1)))
+    values, walls, cores, sample = [], 0.0, 1, ""
+    for step in range(args.warmup + args.steps):
+        v, cores, sample, wall = oracle_step_rate(rp, col, parts, budget, seed=1 + step)
+        if step >= args.warmup:
+            values.append(v)
+            walls += wall
+    value = statistics.median(values)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": walls * 1e3 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORKLOAD, "sample": "bounded: first edges of a 1% sample per step"},
+        "config": {"workload": desc,
+                   "sample": "bounded: per step, the first edges of each part (seeded sample "
+                             "or canonical edge order), per-edge rates scaled to the full step"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{edges} sampled edges over {args.steps} steps, one "
-                                   f"spawned process per core"},
+                         "sample": f"last step: {sample}; one spawned process per core"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -629,6 +673,26 @@ def run_serve_bench(args):
 
 # ------------------------------------------------------------------ main
 
+def line_from(r, args, world, steps, warmup, cpu=None):
+    value = r["edges_all"] / (r["ms_total"] / 1e3)
+    return {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warmup,
+        "ms_per_step": round(r["ms_total"] / steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": r["desc"], "parts": r["parts"],
+                   "l2": "flushed (256 MiB write) before every timed step; CSR > L2",
+                   "hub_index": {k: r["graph"][k] for k in ("bitmap_hubs", "table_hubs")},
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": r["lat"],
+        "graphlets_per_s": round(r["inc_all"] / (r["ms_total"] / 1e3), 1),
+        "registration_s": r["registration_s"], "index_bytes": r["index_bytes"],
+        "workspace_bytes": r["workspace_bytes"],
+        "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu,
+        "gpu_launches": r["launches"], "clocks": r["clocks"],
+    }
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -649,29 +713,29 @@ def main():
         import torch
         torch.cuda.set_device(local)
         torch.distributed.init_process_group("nccl")
-    r = run_gpu(args, rank, world, local)
+    name = args.workload
+    rp, col = generate(name)
+    r = run_gpu(args, rank, world, local, name, rp, col, args.steps, args.warmup)
+    extra = None
+    if name == "rmat_24" and not args.no_extra:
+        rp2, col2 = generate("chung_lu_1m")
+        es = max(1, min(args.steps, args.extra_steps))
+        r2 = run_gpu(args, rank, world, local, "chung_lu_1m", rp2, col2, es, min(args.warmup, 3))
+        extra = {"chung_lu_1m": line_from(r2, args, world, es, min(args.warmup, 3))}
+        for key in ("metric", "unit", "n_gpus", "higher_is_better", "scaling", "vs_baseline",
+                    "dtype", "data", "cpu_baseline", "e2e"):
+            extra["chung_lu_1m"].pop(key, None)
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            edges, secs, cores = oracle_rate_parallel(r["rp"], r["col"], args.cpu_seconds)
-            cpu = {"value": edges / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"first {edges} edges of a seeded 1% sample of chung_lu_1m, "
-                             f"{secs:.1f} s wall on {cores} spawned processes (one per core)"}
-        value = r["edges_all"] / (r["ms_total"] / 1e3)
-        line = {
-            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(r["ms_total"] / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "fractions": r["fractions"],
-                       "l2": "flushed (256 MiB write) before every timed step; CSR 168 MB > L2",
-                       "hub_index": {k: r["graph"][k] for k in ("bitmap_hubs", "table_hubs")},
-                       "parallelism": f"replicas x{world}"},
-            "latency_ms": r["lat"],
-            "graphlets_per_s": round(r["inc_all"] / (r["ms_total"] / 1e3), 1),
-            "e2e": r["e2e"], "roofline": r["roofline"], "cpu_baseline": cpu,
-            "gpu_launches": r["launches"], "clocks": r["clocks"],
-        }
+            v, cores, sample, wall = oracle_step_rate(rp, col, WORKLOADS[name][1],
+                                                      args.cpu_seconds)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{sample}; {wall:.1f} s wall on {cores} spawned processes (one "
+                             "per core); per-edge rates scaled to the full step"}
+        line = line_from(r, args, world, args.steps, args.warmup, cpu)
+        if extra:
+            line["extra"] = extra
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch

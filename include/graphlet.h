@@ -219,6 +219,8 @@ typedef struct {
   float ms_prep, ms_tri, ms_compact, ms_cost, ms_quad, ms_fold; /* device ms per phase */
   int64_t dense_edges;    /* sampled edges whose pairs of hub-matrix members in T
                              were counted word-parallel (matrix row AND T mask) */
+  int64_t dense_groups;   /* 128-bit matrix-row groups ANDed for those edges
+                             (included in quad_tests) */
 } gs_stats;
 
 /* Turns per-phase CUDA-event timing of gs_count on (1) or off (0). Events are

@@ -118,7 +118,7 @@ class GsStats(ctypes.Structure):
                 ("timed", ctypes.c_int32), ("ms_prep", ctypes.c_float), ("ms_tri", ctypes.c_float),
                 ("ms_compact", ctypes.c_float), ("ms_cost", ctypes.c_float),
                 ("ms_quad", ctypes.c_float), ("ms_fold", ctypes.c_float),
-                ("dense_edges", ctypes.c_int64)]
+                ("dense_edges", ctypes.c_int64), ("dense_groups", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -1289,7 +1289,7 @@ int64_t launch_dense(const DevGraph& g, bool need_q, CountBufs& b, cudaStream_t 
   k_dense_pairs<<<sm_count() * kDenseBlocksPerSm, kThreads, 0, stream>>>(
       g.hm_bits, g.hm_words, b.toff, b.t, b.T_hm, b.tmask, b.dense_e, b.unit_off, b.unit_idx,
       b.ndense, need_q ? 1 : 0,
-      b.k2, b.q, b.stats + 7, b.stats + 1);
+      b.k2, b.q, b.stats + 7, b.stats + 4);
   return 1;
 }
 
@@ -1529,7 +1529,8 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   st.k = K;
   st.tri_tests = (int64_t)hs[0];
   st.dense_edges = (int64_t)hs[6];
-  st.quad_tests = (int64_t)hs[1];
+  st.quad_tests = (int64_t)(hs[1] + hs[4]);
+  st.dense_groups = (int64_t)hs[4];
   st.model_bytes = hs[2] + hs[3];
   st.model_tri_bytes = hs[2];
   st.model_quad_bytes = hs[3];

@@ -21,9 +21,13 @@ def test_incidences_from_numerator_sums_equal_the_per_edge_definition():
     assert bench.incidences_from_numerators(s) == direct
 
 
-def test_parallel_oracle_baseline_counts_a_bounded_sample():
+def test_parallel_oracle_baseline_counts_a_bounded_sample_of_every_part():
     rp, col = synth.er(3000, 60000, seed=2)
-    edges, wall, cores = bench.oracle_rate_parallel(rp, col, 0.2, seed=3, workers=2)
-    assert cores == 2 and wall > 0
-    assert 0 < edges <= len(oracle.sample(rp, col, 0.01, 3))
-    assert np.isfinite(edges / wall)
+    parts = [("exact_3node", 1.0, bench.THREE), ("0.01", 0.01, bench.CONN)]
+    rates, cores = bench.oracle_part_rates(rp, col, parts, 0.4, seed=3, workers=2)
+    assert cores == 2
+    assert 0 < rates["0.01"][0] <= len(oracle.sample(rp, col, 0.01, 3))
+    assert 0 < rates["exact_3node"][0] <= len(col) // 2
+    assert all(w > 0 for _, w in rates.values())
+    v, cores, sample, wall = bench.oracle_step_rate(rp, col, parts, 0.4, seed=3)
+    assert np.isfinite(v) and v > 0 and "exact_3node" in sample

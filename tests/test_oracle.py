@@ -535,3 +535,16 @@ def test_adaptive_loss_helpers():
     assert oracle.relative_change(1.0, 0.0) == math.inf
     assert oracle.relative_change(90.0, 100.0) == 0.1
     assert oracle.relative_change(-110.0, -100.0) == 0.1
+
+
+def test_oracle_pool_returns_the_oracle_per_edge_output_in_order():
+    from oracle_pool import OraclePool
+    rp, col = synth.chung_lu(3000, 20000, 2.1, 300.0, seed=12)
+    pairs = synth.explicit_sample(rp, col, 0.3, seed=2)
+    want = oracle.local_counts(rp, col, pairs)
+    with OraclePool(rp, col, workers=2) as pool:
+        got = pool.local_counts(pairs)
+        got3 = pool.local_counts(pairs[:100], four=False)
+    for x in ("t", "a", "b", "k", "q"):
+        assert np.array_equal(got[x], want[x]), x
+    assert np.array_equal(got3["t"], want["t"][:100])
