@@ -26,6 +26,8 @@ Statistics"):
   edge, keyed by a SplitMix64 counter hash (project-defined random source).
 * ``adaptive_estimate`` -- Algorithm 8 (adaptive estimation): grow the
   sample until the maximum relative change of the estimates is at most beta.
+* ``micro``         -- Algorithm 7 (micro-level estimation): the per-edge
+  vector x3..x17 with neighbour probes ceil(d_w p_e); exact at p_e = 1.
 * ``disconnected_estimate`` -- Sec. 2.3's estimators of the disconnected
   graphlets G5, G6, G13-G17 with their terms corrected (the printed block
   swaps C13/C14 and C15/C16); exact rationals, variance read as above.
@@ -56,7 +58,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
         return _SO
     subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-std=gnu11", "-ffp-contract=off", src,
-                    "-o", _SO + ".tmp"], check=True, capture_output=True)
+                    "-o", _SO + ".tmp", "-lm"], check=True, capture_output=True)
     os.replace(_SO + ".tmp", _SO)
     return _SO
 
@@ -74,6 +76,8 @@ def _lib() -> ctypes.CDLL:
     lib.oracle_sample.restype = I64
     lib.oracle_splitmix64.argtypes = [U64]
     lib.oracle_splitmix64.restype = U64
+    lib.oracle_micro.argtypes = [I64, I64, P, P, I64, P, ctypes.c_double, U64, P, P]
+    lib.oracle_micro.restype = I
     return lib
 
 
@@ -104,6 +108,32 @@ def local_counts(row_ptr, col, pairs, four: bool = True, _literal_alg4: bool = F
     if rc != 0:
         raise ValueError("oracle: a sampled pair is not an edge of the graph")
     return out
+
+
+#: micro-level statistics of Algorithm 7, in output column order
+MICRO = tuple(range(3, 18))
+
+
+def micro(row_ptr, col, pairs, p_e: float = 1.0, seed: int = 0):
+    """Algorithm 7 (micro-level estimation) for every pair of ``pairs``: the
+    per-edge vector (x3, ..., x17) as float64 [K, 15] and omega [K] (hits
+    from S_u or S_v into T, which x15 uses). Each vertex w of the edge's
+    neighbourhood probes ceil(d_w p_e) consecutive entries of N(w) from a
+    seeded offset; p_e = 1 gives the exact per-edge statistics (see
+    ``oracle_micro`` in oracle.c for the reading of every line)."""
+    row_ptr, col = _c(row_ptr, np.int64), _c(col, np.int32)
+    pairs = _c(pairs, np.int32).reshape(-1, 2)
+    if not 0.0 < p_e <= 1.0:
+        raise ValueError("p_e must lie in (0, 1]")
+    k = len(pairs)
+    x = np.zeros((k, 15), dtype=np.float64)
+    om = np.zeros(k, dtype=np.float64)
+    rc = _lib().oracle_micro(len(row_ptr) - 1, len(col) // 2, row_ptr.ctypes.data,
+                             col.ctypes.data, k, pairs.ctypes.data, float(p_e),
+                             seed & (2**64 - 1), x.ctypes.data, om.ctypes.data)
+    if rc != 0:
+        raise ValueError("oracle: a sampled pair is not an edge of the graph")
+    return x, om
 
 
 def _u128(lo: int, hi: int) -> int:

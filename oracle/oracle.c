@@ -14,6 +14,7 @@
  * Graph: simple undirected, int64 row offsets + int32 sorted adjacency, both
  * orientations stored (the paper's "ordered" neighbour sets, Sec. 2.1).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -220,4 +221,172 @@ int64_t oracle_sample(int64_t n, const int64_t* row_ptr, const int32_t* col, uin
     }
   }
   return kept;
+}
+
+/* ----------------------------------------------------------------------
+ * Algorithm 7 (micro-level estimation) for each sampled edge.
+ *
+ * The marker table Phi carries the labels of Algorithm 7:
+ *   L1  neighbours of v other than u (S_v, and T until relabelled)
+ *   L2  S_u = neighbours of u that are not neighbours of v (not v itself)
+ *   L3  T_e = common neighbours of u and v, not yet processed
+ *   L4  T_e members already processed by the 4-clique loop
+ *   0   an S_u or S_v member already processed (its pairs are counted)
+ * Each loop visits its set in increasing vertex id (the sorted neighbour
+ * lists), so an unordered pair inside a set is counted once, from its
+ * smaller member -- the effect of the paper's resets.
+ *
+ * Neighbour selection for a vertex w of degree d_w: c_w = ceil(d_w p_e)
+ * probes, read as a circular window of c_w consecutive entries of N(w)
+ * starting at offset o_w = floor(h d_w / 2^64), h = sm(sm(seed ^ sm(key))
+ * ^ w), key = (min(u,v) << 32) | max(u,v), sm = SplitMix64. Every
+ * neighbour lies in the window with probability c_w / d_w, so weighting each
+ * hit by d_w / c_w (as the algorithm does) is unbiased; p_e = 1 probes every
+ * neighbour once and the statistics are exact.
+ *
+ * Output row j (x3 .. x17, 15 doubles) with t = |T_e|, a = |S_u|,
+ * b = |S_v|, R = n - 2 - t - a - b:
+ *   x3 = t, x4 = a + b, x5 = R, x6 = C(n,3) - x3 - x4 - x5,
+ *   x7 = 4-clique hits (pairs inside T),  x8 = C(t,2) - x7,
+ *   x9 = tailed-triangle hits (pairs inside S_u, pairs inside S_v),
+ *   x10 = 4-cycle hits (S_u to S_v),
+ *   x11 = C(a,2) + C(b,2) - x9,  x12 = a b - x10,
+ *   x13 = t R,  x14 = (a + b) R,  x15 = m - (t + d_u + d_v + 1) - omega,
+ *   x16 = C(R,2),  x17 = C(n,4) - (x7 + ... + x16),
+ * and omega_out[j] = omega (hits from S_u or S_v into T). Weighted hit sums
+ * are formed with Neumaier's compensated summation. Returns 0, or -1 if a
+ * pair is not an edge.
+ * ---------------------------------------------------------------------- */
+typedef struct { double s, c; } nsum;
+
+static void nsum_add(nsum* a, double x) {
+  double t = a->s + x;
+  if ((a->s >= 0 ? a->s : -a->s) >= (x >= 0 ? x : -x)) a->c += (a->s - t) + x;
+  else a->c += (x - t) + a->s;
+  a->s = t;
+}
+
+static double nsum_value(const nsum* a) { return a->s + a->c; }
+
+static int64_t micro_probes(int64_t d, double pe) {
+  double c = ceil((double)d * pe);
+  return (int64_t)c;
+}
+
+static int64_t micro_offset(uint64_t seed, int64_t x, int64_t y, int64_t w, int64_t d) {
+  uint64_t key = ((uint64_t)(x < y ? x : y) << 32) | (uint64_t)(x < y ? y : x);
+  uint64_t h = oracle_splitmix64(oracle_splitmix64(seed ^ oracle_splitmix64(key)) ^ (uint64_t)w);
+  return (int64_t)(((u128)h * (u128)(uint64_t)d) >> 64);
+}
+
+int oracle_micro(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t* col,
+                 int64_t num_pairs, const int32_t* pairs, double pe, uint64_t seed,
+                 double* x_out, double* omega_out) {
+  int64_t* phi = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int32_t* T = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  int32_t* Su = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  int32_t* Sv = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+  if (!phi || !T || !Su || !Sv) return -2;
+  const i128 N = n;
+  const i128 cn3 = N * (N - 1) * (N - 2) / 6;
+  const i128 cn4 = N * (N - 1) / 2 * (N - 2) * (N - 3) / 12;
+  int rc = 0;
+  for (int64_t j = 0; j < num_pairs; ++j) {
+    int64_t x = pairs[2 * j], y = pairs[2 * j + 1];
+    if (x < 0 || y < 0 || x >= n || y >= n || x == y) { rc = -1; break; }
+    int64_t dx = row_ptr[x + 1] - row_ptr[x], dy = row_ptr[y + 1] - row_ptr[y];
+    int64_t u, v;
+    if (dx < dy || (dx == dy && x < y)) { u = x; v = y; } else { u = y; v = x; }
+    const int64_t E = 5 * (j + 1);
+    const int64_t L1 = E + 1, L2 = E + 2, L3 = E + 3, L4 = E + 4;
+    /* mark N(v) \ {u} with L1 */
+    int adjacent = 0;
+    for (int64_t p = row_ptr[v]; p < row_ptr[v + 1]; ++p) {
+      if (col[p] == u) { adjacent = 1; continue; }
+      phi[col[p]] = L1;
+    }
+    if (!adjacent) { rc = -1; break; }
+    /* N(u) \ {v}: a triangle (L3) or a 2-star of u (L2) */
+    int64_t t = 0, a = 0, b = 0;
+    for (int64_t p = row_ptr[u]; p < row_ptr[u + 1]; ++p) {
+      int64_t w = col[p];
+      if (w == v) continue;
+      if (phi[w] == L1) { T[t++] = (int32_t)w; phi[w] = L3; }
+      else { Su[a++] = (int32_t)w; phi[w] = L2; }
+    }
+    for (int64_t p = row_ptr[v]; p < row_ptr[v + 1]; ++p)
+      if (col[p] != u && phi[col[p]] == L1) Sv[b++] = col[p];
+    const int64_t du = row_ptr[u + 1] - row_ptr[u], dv = row_ptr[v + 1] - row_ptr[v];
+    const int64_t R = n - 2 - t - a - b;
+    nsum s7 = {0, 0}, s9 = {0, 0}, s10 = {0, 0}, sw = {0, 0};
+    /* 4-cliques: probes of N(w) for w in T that land on unprocessed T */
+    for (int64_t i = 0; i < t; ++i) {
+      const int64_t w = T[i], bw = row_ptr[w], dw = row_ptr[w + 1] - bw;
+      const int64_t c = micro_probes(dw, pe), o = micro_offset(seed, x, y, w, dw);
+      int64_t h7 = 0;
+      for (int64_t q = 0; q < c; ++q)
+        if (phi[col[bw + (o + q) % dw]] == L3) ++h7;
+      if (h7) nsum_add(&s7, ((double)h7 * (double)dw) / (double)c);
+      phi[w] = L4;
+    }
+    /* S_u: 4-cycles (S_v, L1), tailed triangles (unprocessed S_u, L2) and
+     * omega (T, L4) */
+    for (int64_t i = 0; i < a; ++i) {
+      const int64_t w = Su[i], bw = row_ptr[w], dw = row_ptr[w + 1] - bw;
+      const int64_t c = micro_probes(dw, pe), o = micro_offset(seed, x, y, w, dw);
+      int64_t h10 = 0, h9 = 0, hw = 0;
+      for (int64_t q = 0; q < c; ++q) {
+        const int64_t lab = phi[col[bw + (o + q) % dw]];
+        if (lab == L1) ++h10;
+        if (lab == L2) ++h9;
+        if (lab == L4) ++hw;
+      }
+      if (h10) nsum_add(&s10, ((double)h10 * (double)dw) / (double)c);
+      if (h9) nsum_add(&s9, ((double)h9 * (double)dw) / (double)c);
+      if (hw) nsum_add(&sw, ((double)hw * (double)dw) / (double)c);
+      phi[w] = 0;
+    }
+    /* S_v: tailed triangles (unprocessed S_v, L1) and omega (T, L4) */
+    for (int64_t i = 0; i < b; ++i) {
+      const int64_t w = Sv[i], bw = row_ptr[w], dw = row_ptr[w + 1] - bw;
+      const int64_t c = micro_probes(dw, pe), o = micro_offset(seed, x, y, w, dw);
+      int64_t h9 = 0, hw = 0;
+      for (int64_t q = 0; q < c; ++q) {
+        const int64_t lab = phi[col[bw + (o + q) % dw]];
+        if (lab == L1) ++h9;
+        if (lab == L4) ++hw;
+      }
+      if (h9) nsum_add(&s9, ((double)h9 * (double)dw) / (double)c);
+      if (hw) nsum_add(&sw, ((double)hw * (double)dw) / (double)c);
+      phi[w] = 0;
+    }
+    /* clear the remaining labels of this edge (T members) */
+    for (int64_t i = 0; i < t; ++i) phi[T[i]] = 0;
+    const double x7 = nsum_value(&s7), x9 = nsum_value(&s9), x10 = nsum_value(&s10);
+    const double om = nsum_value(&sw);
+    double* r = x_out + 15 * j;
+    r[0] = (double)t;
+    r[1] = (double)(a + b);
+    r[2] = (double)R;
+    r[3] = (double)(cn3 - t - (a + b) - R);
+    r[4] = x7;
+    r[5] = (double)(t * (t - 1) / 2) - x7;
+    r[6] = x9;
+    r[7] = x10;
+    r[8] = (double)(a * (a - 1) / 2 + b * (b - 1) / 2) - x9;
+    r[9] = (double)(a * b) - x10;
+    r[10] = (double)((i128)t * R);
+    r[11] = (double)((i128)(a + b) * R);
+    r[12] = (double)(m - (t + du + dv + 1)) - om;
+    r[13] = (double)((i128)R * (R - 1) / 2);
+    double s = 0.0;
+    for (int i = 4; i <= 13; ++i) s += r[i];
+    r[14] = (double)cn4 - s;
+    if (omega_out) omega_out[j] = om;
+  }
+  free(phi);
+  free(T);
+  free(Su);
+  free(Sv);
+  return rc;
 }

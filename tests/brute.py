@@ -236,3 +236,48 @@ def identities(row_ptr, col) -> dict:
         "M": int(up.sum()),
     }
     return out
+
+
+def edge_roles(A: np.ndarray, u: int, v: int) -> dict:
+    """Brute force over every 3- and 4-vertex set containing the edge (u, v):
+    the induced subgraph's graphlet and the edge's role in it.
+
+    Keys: 'tri' (triangles with e), 'wedge' (2-stars with e), 'lone'
+    (3-sets where e is the only edge), 'k4', 'diamond_chord' (e joins the
+    two degree-3 vertices), 'diamond_rim', 'tailed_tail' (e is the pendant
+    edge of a tailed triangle), 'tailed_other', 'c4', 'star' (3-stars with
+    e), 'path_mid' (e is the middle edge of a 4-path), 'path_end',
+    'tri_far' (pairs w in T, r adjacent to neither u nor v)."""
+    n = len(A)
+    others = [x for x in range(n) if x not in (u, v)]
+    out = {k: 0 for k in ("tri", "wedge", "lone", "k4", "diamond_chord", "diamond_rim",
+                          "tailed_tail", "tailed_other", "c4", "star", "path_mid", "path_end",
+                          "tri_far")}
+    for w in others:
+        e = A[u, w] + A[v, w]
+        out["tri" if e == 2 else "wedge" if e == 1 else "lone"] += 1
+    for w, r in itertools.combinations(others, 2):
+        S = [u, v, w, r]
+        sub = A[np.ix_(S, S)]
+        deg = sub.sum(1)
+        m = int(sub.sum()) // 2
+        du, dv = int(deg[0]), int(deg[1])
+        if m == 6:
+            out["k4"] += 1
+        elif m == 5:
+            out["diamond_chord" if du == 3 and dv == 3 else "diamond_rim"] += 1
+        elif m == 4:
+            if sorted(deg.tolist()) == [2, 2, 2, 2]:
+                out["c4"] += 1
+            else:
+                out["tailed_tail" if min(du, dv) == 1 else "tailed_other"] += 1
+        elif m == 3:
+            s = sorted(deg.tolist())
+            if s == [1, 1, 1, 3]:
+                out["star"] += 1
+            elif s == [1, 1, 2, 2]:
+                out["path_mid" if du == 2 and dv == 2 else "path_end"] += 1
+        for a_, b_ in ((w, r), (r, w)):
+            if A[u, a_] and A[v, a_] and not A[u, b_] and not A[v, b_]:
+                out["tri_far"] += 1
+    return out
