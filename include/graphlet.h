@@ -221,6 +221,7 @@ typedef struct {
                              were counted word-parallel (matrix row AND T mask) */
   int64_t dense_groups;   /* 128-bit matrix-row groups ANDed for those edges
                              (included in quad_tests) */
+  int64_t micro_probes;   /* gs_micro only: neighbour probes, sum of ceil(d_w p_e) */
 } gs_stats;
 
 /* Turns per-phase CUDA-event timing of gs_count on (1) or off (0). Events are
@@ -320,6 +321,38 @@ gs_status gs_count_disconnected(const gs_graph* g, gs_workspace* ws, const int32
 gs_status gs_per_edge_numerators(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs,
                                  int64_t k, const int64_t* d_per_edge, int64_t* d_out,
                                  void* stream);
+
+/* Micro-level estimation (Algorithm 7): for every sampled edge e = (u, v)
+ * (d_pairs: device int32[2k], each pair an edge in either orientation, no
+ * edge twice) the per-edge statistics x3 .. x17 of the paper's micro-level
+ * problem, written as row e of d_x (device double[15k]). u is the endpoint
+ * of smaller degree (ties: smaller id); T = N(u) cap N(v), S_u, S_v the
+ * rest of N(u) \ {v}, N(v) \ {u}; t, a, b their sizes, R = n - 2 - t - a - b.
+ * Every w in T, S_u and S_v probes c_w = ceil(d_w p_e) consecutive entries
+ * of N(w), a circular window from offset floor(h d_w / 2^64), h =
+ * sm(sm(seed ^ sm(key)) ^ w), key = (min(u,v) << 32) | max(u,v) (sm =
+ * SplitMix64), each probe landing in the tested set adding d_w / c_w
+ * (every neighbour is in the window with probability c_w / d_w, so the
+ * weighted counts are unbiased; 0 < p_e <= 1, p_e = 1 probes every
+ * neighbour once and gives exact counts):
+ *   x7  = probes from T into T above the prober      (4-cliques with e)
+ *   x9  = probes from S_u into S_u above the prober and from S_v into S_v
+ *         above the prober            (tailed triangles with e as tail)
+ *   x10 = probes from S_u into S_v                   (4-cycles with e)
+ *   omega = probes from S_u or S_v into T   (diamonds with e on the rim)
+ * and, as printed in Algorithm 7 (x5 with the sign of R, x11 over S_u and
+ * S_v): x3 = t, x4 = a + b, x5 = R, x6 = C(n,3) - x3 - x4 - x5,
+ * x8 = C(t,2) - x7, x11 = C(a,2) + C(b,2) - x9, x12 = ab - x10, x13 = tR,
+ * x14 = (a+b)R, x15 = m - (t + d_u + d_v + 1) - omega, x16 = C(R,2),
+ * x17 = C(n,4) - (x7 + ... + x16) (x6, x17 rounded to FP64).
+ * Weighted probe sums are accumulated exactly in fixed point (2^-64) and
+ * rounded once. h_max / h_argmax (host double[15] / int64[15], either may
+ * be NULL) receive the largest value of each statistic over the sample and
+ * the first edge that has it: Sec. 7's extremal statistic Z_j = max_e x_j(e).
+ * gs_count_stats then reports micro_probes. Synchronises `stream`. */
+gs_status gs_micro(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs, int64_t k,
+                   double p_e, uint64_t seed, double* d_x, double* h_max, int64_t* h_argmax,
+                   void* stream);
 
 /* Host FP64 estimates, variances and bounds of G5, G6, G13-G17 from the
  * folded sums (formulas above; var and bounds as in gs_estimate; exact

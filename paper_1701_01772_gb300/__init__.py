@@ -118,7 +118,8 @@ class GsStats(ctypes.Structure):
                 ("timed", ctypes.c_int32), ("ms_prep", ctypes.c_float), ("ms_tri", ctypes.c_float),
                 ("ms_compact", ctypes.c_float), ("ms_cost", ctypes.c_float),
                 ("ms_quad", ctypes.c_float), ("ms_fold", ctypes.c_float),
-                ("dense_edges", ctypes.c_int64), ("dense_groups", ctypes.c_int64)]
+                ("dense_edges", ctypes.c_int64), ("dense_groups", ctypes.c_int64),
+                ("micro_probes", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -222,6 +223,8 @@ def lib() -> ctypes.CDLL:
         "gs_server_info": ([P, ctypes.POINTER(GsServerStats)], ctypes.c_int32),
         "gs_server_destroy": ([P], ctypes.c_int32),
         "gs_count_stats": ([P, ctypes.POINTER(GsStats)], ctypes.c_int32),
+        "gs_micro": ([P, P, P, I64, D, U64, P, ctypes.POINTER(ctypes.c_double),
+                      ctypes.POINTER(ctypes.c_int64), P], ctypes.c_int32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -458,6 +461,25 @@ def gs_per_edge_numerators(graph: int, ws: int, pairs, k: int, per_edge, out, st
     _check(lib().gs_per_edge_numerators(graph, ws, _dev(pairs, torch.int32, "pairs"), k,
                                         _dev(per_edge, torch.int64, "per_edge"),
                                         _dev(out, torch.int64, "out"), _stream_ptr(stream)))
+
+
+MICRO = tuple(range(3, 18))
+
+
+def gs_micro(graph: int, ws: int, pairs, k: int, p_e: float, seed: int, out, stream=None):
+    """Algorithm 7: out (CUDA float64 [k, 15]) <- x3..x17 per sampled edge.
+    Returns (max per statistic, first edge index holding it) over the
+    sample (Sec. 7's extremal statistic)."""
+    import torch
+    _check_pairs(pairs, k)
+    if out.dim() != 2 or out.shape[1] != 15 or out.shape[0] < k:
+        raise ValueError("out must be a [>= k, 15] float64 tensor")
+    mx = (ctypes.c_double * 15)()
+    arg = (ctypes.c_int64 * 15)()
+    _check(lib().gs_micro(graph, ws, _dev(pairs, torch.int32, "pairs"), k, float(p_e),
+                          seed & (2**64 - 1), _dev(out, torch.float64, "out"), mx, arg,
+                          _stream_ptr(stream)))
+    return list(mx), list(arg)
 
 
 def disc_sums_from_ints(k: int, m: int, n: int, sums: dict, sq: dict) -> GsSumsDisc:

@@ -30,6 +30,13 @@ def _chunk(job):
     return oracle.local_counts(np.asarray(rp), np.asarray(col), pairs, four=four)
 
 
+def _micro_chunk(job):
+    import oracle
+    pairs, p_e, seed = job
+    rp, col = _CSR
+    return oracle.micro(np.asarray(rp), np.asarray(col), pairs, p_e, seed)
+
+
 class OraclePool:
     """with OraclePool(rp, col) as pool: lc = pool.local_counts(pairs)"""
 
@@ -51,6 +58,16 @@ class OraclePool:
         jobs = [(pairs[i:i + step], four) for i in range(0, len(pairs), step)]
         parts = self.pool.map(_chunk, jobs, chunksize=1)
         return {x: np.concatenate([p[x] for p in parts]) for x in ("t", "a", "b", "k", "q")}
+
+    def micro(self, pairs, p_e=1.0, seed=0, chunks_per_worker=8):
+        """oracle.micro over the pool (rows in input order)."""
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        if len(pairs) == 0:
+            return np.zeros((0, 15)), np.zeros(0)
+        step = max(1, -(-len(pairs) // (self.workers * chunks_per_worker)))
+        jobs = [(pairs[i:i + step], p_e, seed) for i in range(0, len(pairs), step)]
+        parts = self.pool.map(_micro_chunk, jobs, chunksize=1)
+        return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]))
 
     def close(self):
         self.pool.close()
