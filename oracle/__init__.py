@@ -28,6 +28,10 @@ Statistics"):
   sample until the maximum relative change of the estimates is at most beta.
 * ``micro``         -- Algorithm 7 (micro-level estimation): the per-edge
   vector x3..x17 with neighbour probes ceil(d_w p_e); exact at p_e = 1.
+* ``core_numbers``, ``sample_weighted``, ``ht_estimate`` -- Algorithm 1 with
+  a weighted distribution F (k-core numbers, degrees; Sec. 3.1) and the
+  estimators with a per-edge inverse inclusion probability sigma_e = 1/pi_e
+  (Horvitz-Thompson), exact rationals.
 * ``disconnected_estimate`` -- Sec. 2.3's estimators of the disconnected
   graphlets G5, G6, G13-G17 with their terms corrected (the printed block
   swaps C13/C14 and C15/C16); exact rationals, variance read as above.
@@ -78,6 +82,9 @@ def _lib() -> ctypes.CDLL:
     lib.oracle_splitmix64.restype = U64
     lib.oracle_micro.argtypes = [I64, I64, P, P, I64, P, ctypes.c_double, U64, P, P]
     lib.oracle_micro.restype = I
+    lib.oracle_core_numbers.argtypes = [I64, P, P, P]
+    lib.oracle_sample_weighted.argtypes = [I64, P, P, P, ctypes.c_double, U64, P, P, I64, P]
+    lib.oracle_sample_weighted.restype = I64
     return lib
 
 
@@ -134,6 +141,69 @@ def micro(row_ptr, col, pairs, p_e: float = 1.0, seed: int = 0):
     if rc != 0:
         raise ValueError("oracle: a sampled pair is not an edge of the graph")
     return x, om
+
+
+def core_numbers(row_ptr, col) -> np.ndarray:
+    """k-core number of every vertex (int32 [n]), bucket peeling."""
+    row_ptr, col = _c(row_ptr, np.int64), _c(col, np.int32)
+    n = len(row_ptr) - 1
+    out = np.zeros(max(n, 1), dtype=np.int32)
+    _lib().oracle_core_numbers(n, row_ptr.ctypes.data, col.ctypes.data, out.ctypes.data)
+    return out[:n].copy()
+
+
+def sample_weighted(row_ptr, col, vertex_w, fraction: float, seed: int):
+    """Weighted Bernoulli sample: edge (u < v) with weight w_e = min(w_u, w_v)
+    kept with probability pi_e = min(1, s w_e), s = fraction M / sum_e w_e,
+    by the same key as ``sample``. Returns (pairs int32 [K, 2], w_e int32
+    [K], s)."""
+    row_ptr, col = _c(row_ptr, np.int64), _c(col, np.int32)
+    vw = _c(vertex_w, np.int32)
+    if not (0.0 <= fraction <= 1.0) or (vw < 0).any():
+        raise ValueError("fraction must lie in [0, 1] and weights must be >= 0")
+    m = len(col) // 2
+    out = np.zeros((max(m, 1), 2), dtype=np.int32)
+    ow = np.zeros(max(m, 1), dtype=np.int32)
+    scale = ctypes.c_double()
+    kept = _lib().oracle_sample_weighted(len(row_ptr) - 1, row_ptr.ctypes.data, col.ctypes.data,
+                                         vw.ctypes.data, float(fraction), seed & (2**64 - 1),
+                                         out.ctypes.data, ow.ctypes.data, m, ctypes.byref(scale))
+    return out[:kept].copy(), ow[:kept].copy(), scale.value
+
+
+def inclusion_probability(weights, scale: float) -> list:
+    """pi_e = min(1, s w_e), evaluated in FP64 as the samplers do."""
+    return [min(1.0, scale * float(w)) for w in np.asarray(weights).tolist()]
+
+
+def ht_estimate(lc: dict, weights, scale: float, m: int, z: float = Z95) -> dict:
+    """Estimates under weighted Bernoulli (Poisson) sampling: with the
+    per-edge inverse inclusion probability sigma_e = 1 / pi_e in place of
+    Sec. 2.3's uniform sigma = M/K (Horvitz-Thompson),
+        X_i = sum_e N_i(e) / (D_i pi_e),
+        V_i = sum_e (1 - pi_e) N_i(e)^2 / (D_i^2 pi_e^2)
+    (the unbiased variance estimator of independent inclusions), bounds
+    X -/+ z sqrt(V) (Sec. 6.2); exact counts when every edge is sampled with
+    pi = 1. Exact rationals (pi_e taken as its exact FP64 value), rounded
+    once."""
+    pis = [Fraction(p) for p in inclusion_probability(weights, scale)]
+    _, _, nmat = numerators(lc, per_edge=True)
+    k = len(pis)
+    res = {}
+    all_one = k == m and all(p == 1 for p in pis)
+    for i, g in enumerate(GRAPHLETS):
+        d = DENOM[g]
+        col_i = nmat[:, i].tolist() if k else []
+        X = sum((Fraction(v) / p for v, p in zip(col_i, pis)), Fraction(0)) / d
+        V = sum((Fraction(v * v) * (1 - p) / (p * p) for v, p in zip(col_i, pis)),
+                Fraction(0)) / (d * d)
+        r = {"X": float(X), "V": float(V), "lb": math.nan, "ub": math.nan, "exact": None}
+        half = z * math.sqrt(r["V"])
+        r["lb"], r["ub"] = r["X"] - half, r["X"] + half
+        if all_one:
+            r["exact"] = int(X)
+        res[g] = r
+    return res
 
 
 def _u128(lo: int, hi: int) -> int:

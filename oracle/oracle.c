@@ -390,3 +390,110 @@ int oracle_micro(int64_t n, int64_t m, const int64_t* row_ptr, const int32_t* co
   free(Sv);
   return rc;
 }
+
+/* ----------------------------------------------------------------------
+ * k-core numbers (the weights of the k-core sampling distribution of
+ * Sec. 3.1 / Sec. 7): core[v] = the largest k such that v belongs to a
+ * subgraph whose every vertex has degree >= k. Bucket peeling of Batagelj
+ * and Zaversnik (2003): vertices in buckets by current degree; repeatedly
+ * remove a vertex of least current degree, its core number is that degree
+ * (never below the previous one), and move each later neighbour one bucket
+ * down.
+ * ---------------------------------------------------------------------- */
+void oracle_core_numbers(int64_t n, const int64_t* row_ptr, const int32_t* col, int32_t* core) {
+  if (n <= 0) return;
+  int64_t maxd = 0;
+  int64_t* deg = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  for (int64_t v = 0; v < n; ++v) {
+    deg[v] = row_ptr[v + 1] - row_ptr[v];
+    if (deg[v] > maxd) maxd = deg[v];
+  }
+  int64_t* bin = (int64_t*)calloc((size_t)(maxd + 2), sizeof(int64_t));
+  int64_t* pos = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  int64_t* vert = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  for (int64_t v = 0; v < n; ++v) bin[deg[v]]++;
+  int64_t start = 0;
+  for (int64_t d = 0; d <= maxd; ++d) {
+    int64_t num = bin[d];
+    bin[d] = start;
+    start += num;
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    pos[v] = bin[deg[v]];
+    vert[pos[v]] = v;
+    bin[deg[v]]++;
+  }
+  for (int64_t d = maxd; d >= 1; --d) bin[d] = bin[d - 1];
+  bin[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t v = vert[i];
+    core[v] = (int32_t)deg[v];
+    for (int64_t p = row_ptr[v]; p < row_ptr[v + 1]; ++p) {
+      int64_t x = col[p];
+      if (deg[x] > deg[v]) {
+        int64_t dx = deg[x], px = pos[x], pw = bin[dx], w = vert[pw];
+        if (x != w) {  /* swap x with the first vertex of its bucket */
+          pos[x] = pw;
+          vert[px] = w;
+          pos[w] = px;
+          vert[pw] = x;
+        }
+        bin[dx]++;
+        deg[x]--;
+      }
+    }
+  }
+  free(deg);
+  free(bin);
+  free(pos);
+  free(vert);
+}
+
+/* ----------------------------------------------------------------------
+ * Weighted edge sampling (Algorithm 1 with a non-uniform distribution F,
+ * Sec. 3.1: "k-core numbers, degrees, or any attribute of interest").
+ * Edge weight w_e = min(vw[u], vw[v]) (for core numbers: the edge's own
+ * core number); W = sum of w_e over the edges; each canonical edge i is
+ * kept independently with probability pi_e = min(1, s w_e), s = fraction
+ * M / W, by the sampler key of oracle_sample:
+ *   keep iff (sm(seed ^ sm(i)) >> 11) < floor(pi_e 2^53).
+ * Writes the kept pairs (u < v, increasing i) and their weights; returns
+ * the number kept (at most max_pairs written). *scale_out = s.
+ * ---------------------------------------------------------------------- */
+int64_t oracle_sample_weighted(int64_t n, const int64_t* row_ptr, const int32_t* col,
+                               const int32_t* vw, double fraction, uint64_t seed,
+                               int32_t* out_pairs, int32_t* out_w, int64_t max_pairs,
+                               double* scale_out) {
+  int64_t m = 0, W = 0;
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = row_ptr[u]; p < row_ptr[u + 1]; ++p) {
+      int64_t v = col[p];
+      if (v <= u) continue;
+      ++m;
+      W += vw[u] < vw[v] ? vw[u] : vw[v];
+    }
+  const double s = W > 0 ? fraction * (double)m / (double)W : 0.0;
+  *scale_out = s;
+  int64_t kept = 0;
+  uint64_t i = 0;
+  for (int64_t u = 0; u < n; ++u)
+    for (int64_t p = row_ptr[u]; p < row_ptr[u + 1]; ++p) {
+      int64_t v = col[p];
+      if (v <= u) continue;
+      const int32_t we = vw[u] < vw[v] ? vw[u] : vw[v];
+      double pi = s * (double)we;
+      if (pi > 1.0) pi = 1.0;
+      const uint64_t threshold = (uint64_t)floor(pi * 9007199254740992.0);
+      const uint64_t h = oracle_splitmix64(seed ^ oracle_splitmix64(i));
+      if ((h >> 11) < threshold) {
+        if (kept < max_pairs) {
+          out_pairs[2 * kept] = (int32_t)u;
+          out_pairs[2 * kept + 1] = (int32_t)v;
+          out_w[kept] = we;
+        }
+        ++kept;
+      }
+      ++i;
+    }
+  return kept;
+}
