@@ -354,6 +354,48 @@ gs_status gs_micro(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs, 
                    double p_e, uint64_t seed, double* d_x, double* h_max, int64_t* h_argmax,
                    void* stream);
 
+/* ---- weighted sampling (Sec. 3.1's weighted distribution F) ------------
+ * k-core numbers: d_core (device int32[n]) receives the largest k such that
+ * v lies in a subgraph whose every vertex has degree >= k (the weights of
+ * the k-core distribution that Sec. 7 uses for the extremal problem);
+ * *h_max_core (host, may be NULL) the largest. Parallel peeling; uses the
+ * workspace; synchronises `stream`. */
+gs_status gs_core_numbers(const gs_graph* g, gs_workspace* ws, int32_t* d_core,
+                          int32_t* h_max_core, void* stream);
+
+/* Weighted edge sampling (Algorithm 1 with a non-uniform F): with vertex
+ * weights d_vertex_w (device int32[n], >= 0; e.g. gs_core_numbers' output or
+ * the degrees) every edge e = (u, v) has weight w_e = min(w_u, w_v) and is
+ * kept independently with probability pi_e = min(1, s w_e),
+ * s = fraction m / sum_e w_e (so about fraction m edges are kept when no
+ * pi_e reaches 1), by the key of gs_sample: canonical edge i is kept iff
+ * (sm(seed ^ sm(i)) >> 11) < floor(pi_e 2^53). Equal weights give
+ * gs_sample's uniform sample. Kept edges go to d_pairs (device int32[2 max_k],
+ * (u, v), u < v, increasing i) and their w_e to d_pair_w (device
+ * int32[max_k], may be NULL); *k_out and *scale_out = s (host).
+ * GS_ECAPACITY if more than max_k are kept; GS_EINVAL for a negative weight
+ * or no positive edge weight. Synchronises `stream`. */
+gs_status gs_sample_weighted(const gs_graph* g, gs_workspace* ws, const int32_t* d_vertex_w,
+                             double fraction, uint64_t seed, int32_t* d_pairs, int32_t* d_pair_w,
+                             int64_t max_k, int64_t* k_out, double* scale_out, void* stream);
+
+/* Estimates from a weighted sample (d_pairs, k as gs_count; d_vertex_w and
+ * scale as given to / returned by gs_sample_weighted): the paper's inverse
+ * sampling probability taken per edge, sigma_e = 1 / pi_e with
+ * pi_e = min(1, scale w_e) (Horvitz-Thompson):
+ *   x_i   = sum_e N_i(e) / (D_i pi_e)
+ *   var_i = sum_e (1 - pi_e) N_i(e)^2 / (D_i^2 pi_e^2)   (independent
+ *           inclusions; unbiased for Var[x_i])
+ *   lb_i, ub_i = x_i -/+ z sqrt(var_i)
+ * with N_i, D_i as in gs_sums. The per-edge numerators are summed exactly
+ * per weight class on the device (every sampled edge needs 1 <= w_e < 2^22)
+ * and the classes are combined in FP64 on the host in increasing weight.
+ * When every edge is sampled with pi_e = 1 the counts are exact (flag
+ * GS_F_EXACT, exact[] valid). Synchronises `stream`. */
+gs_status gs_count_weighted(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs, int64_t k,
+                            const int32_t* d_vertex_w, double scale, uint32_t mask, double z,
+                            gs_result* out, void* stream);
+
 /* Host FP64 estimates, variances and bounds of G5, G6, G13-G17 from the
  * folded sums (formulas above; var and bounds as in gs_estimate; exact
  * counts when k = m, with GS_F_OVERFLOW when a count does not fit uint64). */

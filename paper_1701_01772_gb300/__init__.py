@@ -223,6 +223,11 @@ def lib() -> ctypes.CDLL:
         "gs_server_info": ([P, ctypes.POINTER(GsServerStats)], ctypes.c_int32),
         "gs_server_destroy": ([P], ctypes.c_int32),
         "gs_count_stats": ([P, ctypes.POINTER(GsStats)], ctypes.c_int32),
+        "gs_core_numbers": ([P, P, P, ctypes.POINTER(ctypes.c_int32), P], ctypes.c_int32),
+        "gs_sample_weighted": ([P, P, P, D, U64, P, P, I64, PI64, ctypes.POINTER(ctypes.c_double),
+                                P], ctypes.c_int32),
+        "gs_count_weighted": ([P, P, P, I64, P, D, U32, D, ctypes.POINTER(GsResult), P],
+                              ctypes.c_int32),
         "gs_micro": ([P, P, P, I64, D, U64, P, ctypes.POINTER(ctypes.c_double),
                       ctypes.POINTER(ctypes.c_int64), P], ctypes.c_int32),
     }
@@ -464,6 +469,43 @@ def gs_per_edge_numerators(graph: int, ws: int, pairs, k: int, per_edge, out, st
 
 
 MICRO = tuple(range(3, 18))
+
+
+def gs_core_numbers(graph: int, ws: int, out, stream=None) -> int:
+    """out (CUDA int32 [n]) <- k-core number per vertex; returns the largest."""
+    import torch
+    mx = ctypes.c_int32()
+    _check(lib().gs_core_numbers(graph, ws, _dev(out, torch.int32, "out"), ctypes.byref(mx),
+                                 _stream_ptr(stream)))
+    return mx.value
+
+
+def gs_sample_weighted(graph: int, ws: int, vertex_w, fraction: float, seed: int, out_pairs,
+                       out_w=None, stream=None):
+    """Weighted edge sample into out_pairs (CUDA int32 [max_k, 2]) and out_w
+    (CUDA int32 [max_k] or None); returns (K, scale s)."""
+    import torch
+    k = ctypes.c_int64()
+    sc = ctypes.c_double()
+    _check(lib().gs_sample_weighted(graph, ws, _dev(vertex_w, torch.int32, "vertex_w"),
+                                    float(fraction), seed & (2**64 - 1),
+                                    _dev(out_pairs, torch.int32, "out_pairs"),
+                                    None if out_w is None else _dev(out_w, torch.int32, "out_w"),
+                                    out_pairs.shape[0], ctypes.byref(k), ctypes.byref(sc),
+                                    _stream_ptr(stream)))
+    return k.value, sc.value
+
+
+def gs_count_weighted(graph: int, ws: int, pairs, k: int, vertex_w, scale: float,
+                      mask: int = GS_CONNECTED, z: float = 1.96, stream=None) -> GsResult:
+    """Horvitz-Thompson estimates of a weighted sample (sigma_e = 1 / pi_e)."""
+    import torch
+    _check_pairs(pairs, k)
+    out = GsResult()
+    _check(lib().gs_count_weighted(graph, ws, _dev(pairs, torch.int32, "pairs"), k,
+                                   _dev(vertex_w, torch.int32, "vertex_w"), float(scale), mask,
+                                   z, ctypes.byref(out), _stream_ptr(stream)))
+    return out
 
 
 def gs_micro(graph: int, ws: int, pairs, k: int, p_e: float, seed: int, out, stream=None):
