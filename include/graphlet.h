@@ -241,6 +241,19 @@ gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_per_sm, int q
 /* Host output: statistics of the last gs_count that used `ws`. */
 gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
 
+/* Sample size for a target error (Sec. 6.2: K = (z sqrt(Var[X]) / margin)^2),
+ * from a pilot sample's exact sums (host only): with the per-edge sample
+ * variance S^2 = (k sumsq - sum^2) / (k (k - 1) D^2) of y = N / D, the
+ * pilot estimate X and the margin h = rel_err |X| (the paper's margin read
+ * as a relative error of the estimate),
+ *   n0 = (z m S / h)^2,  K = ceil(n0 / (1 + n0 / m))
+ * (the finite-population correction of sampling without replacement),
+ * clamped to [1, m]. k_out (host int64[8], graphlet order of gs_sums):
+ * -1 outside the mask or when the pilot has fewer than 2 edges; the pilot
+ * size when its per-edge values do not vary; m when X = 0 but they do.
+ * Evaluated in FP64. */
+gs_status gs_sample_size(const gs_sums* s, double z, double rel_err, int64_t* k_out);
+
 /* Algorithm 8 (adaptive estimation): grows the sampled edge set until the
  * estimates stop moving. Iteration t adds the edges whose sampler key
  * (gs_sample's) lies between fractions p_{t-1} and p_t = p_{t-1} +

@@ -276,6 +276,40 @@ def estimate(s: dict, s2: dict, m: int, k: int, z: float = Z95) -> dict:
     return res
 
 
+def sample_size(s: dict, s2: dict, m: int, k: int, rel_err: float, z: float = Z95) -> dict:
+    """Sample size for a target error (Sec. 6.2: K = (z sqrt(Var) / margin)^2),
+    read with the per-edge standard deviation of a pilot sample of k edges
+    and a margin of rel_err |X| (relative error of the pilot estimate), with
+    the finite-population correction of sampling without replacement:
+        S^2 = (k sum N^2 - (sum N)^2) / (k (k - 1) D^2)   (sample variance of y)
+        n0  = (z m S / (rel_err |X|))^2,   K = ceil(n0 / (1 + n0 / m)),
+    capped to [1, m]; K = m when the pilot estimate is 0 and its spread is
+    not (no relative target is reachable); K = k when the pilot's per-edge
+    values do not vary. Exact rationals; None when the pilot has fewer than
+    2 edges."""
+    out = {}
+    for g in GRAPHLETS:
+        d = DENOM[g]
+        if k < 2:
+            out[g] = None
+            continue
+        S2 = Fraction(k * s2[g] - s[g] * s[g], k * (k - 1) * d * d)
+        X = Fraction(m * s[g], k * d)
+        if S2 == 0:
+            out[g] = k
+            continue
+        if X == 0:
+            out[g] = m
+            continue
+        h = Fraction(rel_err) * abs(X)
+        zf = Fraction(z)
+        n0 = zf * zf * m * m * S2 / (h * h)
+        K = n0 / (1 + n0 / m)
+        c = -((-K.numerator) // K.denominator)
+        out[g] = max(1, min(m, c))
+    return out
+
+
 def exact_counts(row_ptr, col) -> dict:
     """Exact connected 3- and 4-node graphlet counts (all edges sampled)."""
     from synth import upper_pairs  # input helper only: lists the edges

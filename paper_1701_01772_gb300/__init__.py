@@ -223,6 +223,7 @@ def lib() -> ctypes.CDLL:
         "gs_server_info": ([P, ctypes.POINTER(GsServerStats)], ctypes.c_int32),
         "gs_server_destroy": ([P], ctypes.c_int32),
         "gs_count_stats": ([P, ctypes.POINTER(GsStats)], ctypes.c_int32),
+        "gs_sample_size": ([ctypes.POINTER(GsSums), D, D, PI64], ctypes.c_int32),
         "gs_core_numbers": ([P, P, P, ctypes.POINTER(ctypes.c_int32), P], ctypes.c_int32),
         "gs_sample_weighted": ([P, P, P, D, U64, P, P, I64, PI64, ctypes.POINTER(ctypes.c_double),
                                 P], ctypes.c_int32),
@@ -435,6 +436,13 @@ def gs_estimate(sums: GsSums, z: float = 1.96) -> GsResult:
     out = GsResult()
     _check(lib().gs_estimate(ctypes.byref(sums), z, ctypes.byref(out)))
     return out
+
+
+def gs_sample_size(sums: GsSums, rel_err: float, z: float = 1.96) -> dict:
+    """Sample size per graphlet for a relative error of rel_err (host only)."""
+    out = (ctypes.c_int64 * 8)()
+    _check(lib().gs_sample_size(ctypes.byref(sums), float(z), float(rel_err), out))
+    return {g: (None if out[i] < 0 else int(out[i])) for i, g in enumerate(GRAPHLETS)}
 
 
 def gs_count_disconnected(graph: int, ws: int, pairs, k: int, per_edge, stream=None) -> GsSumsDisc:

@@ -214,6 +214,40 @@ extern "C" gs_status gs_count_estimate(const gs_graph* g, gs_workspace* ws, doub
   return gs_estimate(&sums, z, out);
 }
 
+extern "C" gs_status gs_sample_size(const gs_sums* s, double z, double rel_err, int64_t* k_out) {
+  if (s == nullptr || k_out == nullptr || !(z > 0.0) || !(rel_err > 0.0) || s->k < 0 ||
+      s->k > s->m) {
+    gs::set_error("gs_sample_size: invalid arguments (z > 0, rel_err > 0, 0 <= k <= m)");
+    return GS_EINVAL;
+  }
+  const int64_t K = s->k, M = s->m;
+  for (int i = 0; i < 8; ++i) {
+    k_out[i] = -1;
+    if (!(s->mask & kBit[i]) || K < 2) continue;
+    const i128 S = load_i128(s->sum[i]);
+    const u128 absS = (u128)(S < 0 ? -S : S);
+    const U256 a = mul_128x128(load_u128(s->sumsq[i]), (u128)K);
+    const U256 b = mul_128x128(absS, absS);
+    const double Q = less_256(a, b) ? 0.0 : to_double_256(sub_256(a, b));
+    const double D = (double)kDenom[i];
+    // per-edge sample variance of y = N / D and the pilot estimate
+    const double S2 = Q / ((double)K * (double)(K - 1) * D * D);
+    const double X = (double)M * ((double)S / D) / (double)K;
+    if (S2 == 0.0) {
+      k_out[i] = K;
+    } else if (X == 0.0) {
+      k_out[i] = M;
+    } else {
+      const double h = rel_err * fabs(X);
+      const double n0 = z * z * (double)M * (double)M * S2 / (h * h);
+      const double need = n0 / (1.0 + n0 / (double)M);
+      const double c = ceil(need);
+      k_out[i] = c < 1.0 ? 1 : c >= (double)M ? M : (int64_t)c;
+    }
+  }
+  return GS_OK;
+}
+
 extern "C" gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, double beta,
                                        int32_t t_max, double phi, uint64_t seed, uint32_t mask,
                                        double z, gs_sums* sums_out, gs_result* out,
