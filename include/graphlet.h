@@ -367,6 +367,17 @@ gs_status gs_micro(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs, 
                    double p_e, uint64_t seed, double* d_x, double* h_max, int64_t* h_argmax,
                    void* stream);
 
+/* Uniform sample of exactly k distinct edges (Algorithm 1 with a sample
+ * size, without replacement; Algorithm 8 draws its iterations this way):
+ * the k canonical edges with the smallest (key, i), key = gs_sample's
+ * 53-bit sampler key (sm(seed ^ sm(i)) >> 11), found by a radix select on
+ * the device. Every k-subset is equally likely, the samples of one seed
+ * are nested in k, and they are nested with gs_sample's Bernoulli samples
+ * of the same seed. Writes d_pairs (device int32[2k], (u, v), u < v,
+ * increasing i); 0 <= k <= m. Synchronises `stream`. */
+gs_status gs_sample_fixed(const gs_graph* g, gs_workspace* ws, int64_t k, uint64_t seed,
+                          int32_t* d_pairs, void* stream);
+
 /* ---- weighted sampling (Sec. 3.1's weighted distribution F) ------------
  * k-core numbers: d_core (device int32[n]) receives the largest k such that
  * v lies in a subgraph whose every vertex has degree >= k (the weights of

@@ -243,6 +243,37 @@ def sample(row_ptr, col, fraction: float, seed: int) -> np.ndarray:
     return out[:kept].copy()
 
 
+def sample_keys(row_ptr, col, seed: int) -> np.ndarray:
+    """The 53-bit sampler key (sm(seed ^ sm(i)) >> 11) of every canonical edge
+    i (uint64 [M]), SplitMix64 evaluated in Python integers."""
+    m = len(col) // 2
+    mask = 2**64 - 1
+
+    def sm(x):
+        z = (x + 0x9E3779B97F4A7C15) & mask
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+        return z ^ (z >> 31)
+
+    seed &= mask
+    return np.array([sm(seed ^ sm(i)) >> 11 for i in range(m)], dtype=np.uint64)
+
+
+def sample_fixed(row_ptr, col, k: int, seed: int) -> np.ndarray:
+    """Uniform sample of exactly k distinct edges (Algorithm 1 with a sample
+    size, without replacement): the k canonical edges with the smallest
+    (key, i), key = the Bernoulli sampler's 53-bit key, listed in increasing
+    i as int32 [k, 2]. Because the keys are those of ``sample``, the result
+    is nested with every Bernoulli sample of the same seed."""
+    from synth import upper_pairs  # input helper only: lists the edges
+    m = len(col) // 2
+    if not 0 <= k <= m:
+        raise ValueError("k must lie in [0, M]")
+    keys = sample_keys(row_ptr, col, seed)
+    order = np.lexsort((np.arange(m), keys))[:k]
+    return upper_pairs(np.asarray(row_ptr), np.asarray(col))[np.sort(order)].copy()
+
+
 def estimate(s: dict, s2: dict, m: int, k: int, z: float = Z95) -> dict:
     """Estimates, variances and bounds per graphlet from exact sums.
 

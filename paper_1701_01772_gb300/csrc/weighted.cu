@@ -1,4 +1,6 @@
-// Weighted edge sampling (Algorithm 1 with a non-uniform distribution F,
+// Fixed-size uniform edge sampling (Algorithm 1 with a sample size K,
+// without replacement: the K edges of smallest sampler key), weighted edge
+// sampling (Algorithm 1 with a non-uniform distribution F,
 // Sec. 3.1: edges drawn by k-core numbers, degrees or any vertex property),
 // the k-core numbers it is usually weighted by (the extremal problem of
 // Sec. 7 samples edges of large k-core number), and the estimators with a
@@ -24,6 +26,9 @@
 // neighbour from k + 1 to k adds it to the next frontier of the same level.
 #include <math.h>
 #include <string.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -223,6 +228,50 @@ __global__ void k_flag_write(const int32_t* __restrict__ col, const int64_t* __r
     pairs[2 * pos + 1] = v;
     if (pw != nullptr) pw[pos] = edge_weight(vw, (int32_t)lo, v);
     ++pos;
+  }
+}
+
+// ------------------------------------------------------------------ fixed size
+
+// Histogram of one radix digit of the 53-bit sampler keys, over the edges
+// whose key agrees with `prefix` on the bits above `shift + bits`.
+constexpr int kSelBins = 2048;
+
+__global__ void k_key_hist(int64_t m, uint64_t seed, uint64_t prefix, int above, int shift,
+                           int bits, unsigned long long* __restrict__ hist) {
+  __shared__ unsigned int h[kSelBins];
+  for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  const uint64_t dmask = ((uint64_t)1 << bits) - 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = splitmix(seed ^ splitmix((uint64_t)i)) >> 11;
+    if (above >= 53 || (key >> above) == prefix) atomicAdd(h + ((key >> shift) & dmask), 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < (1 << bits); b += blockDim.x)
+    if (h[b]) atomicAdd(hist + b, (unsigned long long)h[b]);
+}
+
+// Indices of the edges whose key equals T (ties of the order statistic).
+__global__ void k_key_ties(int64_t m, uint64_t seed, uint64_t T, int64_t cap,
+                           int64_t* __restrict__ out, unsigned long long* __restrict__ cnt) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if ((splitmix(seed ^ splitmix((uint64_t)i)) >> 11) == T) {
+      const unsigned long long at = atomicAdd(cnt, 1ull);
+      if ((int64_t)at < cap) out[at] = i;
+    }
+  }
+}
+
+// keep[i] = key < T, or key == T and i <= i_cut.
+__global__ void k_fixed_flags(int64_t m, uint64_t seed, uint64_t T, int64_t i_cut,
+                              uint8_t* __restrict__ keep) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t key = splitmix(seed ^ splitmix((uint64_t)i)) >> 11;
+    keep[i] = (key < T || (key == T && i <= i_cut)) ? 1 : 0;
   }
 }
 
@@ -536,5 +585,98 @@ extern "C" gs_status gs_count_weighted(const gs_graph* gr, gs_workspace* ws,
     }
   }
   delete[] h;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_sample_fixed(const gs_graph* gr, gs_workspace* ws, int64_t k,
+                                     uint64_t seed, int32_t* d_pairs, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (gr == nullptr || ws == nullptr || k < 0 || k > gr->m || (k > 0 && d_pairs == nullptr)) {
+    set_error("gs_sample_fixed: invalid arguments (need 0 <= k <= m and an output)");
+    return GS_EINVAL;
+  }
+  const int64_t n = gr->dev.n, m = gr->m;
+  if (k == 0) return GS_OK;
+  constexpr int64_t kTieCap = 1 << 16;
+  const int64_t tiles = (m + kSampTile - 1) / kSampTile;
+  const size_t bytes = Carve::bytes_for<unsigned long long>(kSelBins + 8) +
+                       Carve::bytes_for<int64_t>(kTieCap) + Carve::bytes_for<uint8_t>(m) +
+                       Carve::bytes_for<int64_t>(tiles + 1) * 2 +
+                       Carve::bytes_for<int64_t>(scan_tmp_elems(tiles));
+  void* base = nullptr;
+  GS_TRY(ws_reserve(ws, 0, bytes, stream, &base));
+  Carve c{(char*)base, 0};
+  unsigned long long* hist = c.take<unsigned long long>(kSelBins + 8);
+  int64_t* ties = c.take<int64_t>(kTieCap);
+  uint8_t* keep = c.take<uint8_t>(m);
+  int64_t* cnt = c.take<int64_t>(tiles + 1);
+  int64_t* off = c.take<int64_t>(tiles + 1);
+  int64_t* tmp = c.take<int64_t>(scan_tmp_elems(tiles));
+  // order statistic: the k-th smallest key T, five digits from the top
+  uint64_t prefix = 0;
+  int above = 53;
+  int64_t rank = k - 1;  // 0-based rank of T among the keys with this prefix
+  static const int kDigits[5] = {11, 11, 11, 10, 10};
+  int64_t launches = 0, tie_count = 0;
+  std::vector<unsigned long long> h(kSelBins);
+  for (int d = 0; d < 5; ++d) {
+    const int bits = kDigits[d], shift = above - bits;
+    GS_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kSelBins, stream));
+    k_key_hist<<<grid_for(m, kThreads, 4), kThreads, 0, stream>>>(m, seed, prefix, above, shift,
+                                                                   bits, hist);
+    ++launches;
+    GS_CUDA(cudaMemcpyAsync(h.data(), hist, sizeof(unsigned long long) << bits,
+                            cudaMemcpyDeviceToHost, stream));
+    GS_CUDA(cudaStreamSynchronize(stream));
+    int64_t accum = 0;
+    int b = 0;
+    for (; b < (1 << bits); ++b) {
+      if (accum + (int64_t)h[b] > rank) break;
+      accum += (int64_t)h[b];
+    }
+    if (b == (1 << bits)) {
+      set_error("gs_sample_fixed: key selection lost its rank");
+      return GS_ECUDA;
+    }
+    rank -= accum;
+    prefix = (prefix << bits) | (uint64_t)b;
+    above = shift;
+    tie_count = (int64_t)h[b];
+  }
+  const uint64_t T = prefix;
+  // rank = how many keys equal to T come before the last one kept
+  int64_t i_cut = m;  // every tie kept
+  if (rank + 1 < tie_count) {
+    if (tie_count > kTieCap) {
+      set_error("gs_sample_fixed: %lld sampler keys tie at the cut", (long long)tie_count);
+      return GS_ECAPACITY;
+    }
+    GS_CUDA(cudaMemsetAsync(hist + kSelBins, 0, sizeof(unsigned long long), stream));
+    k_key_ties<<<grid_for(m, kThreads, 4), kThreads, 0, stream>>>(m, seed, T, kTieCap, ties,
+                                                                   hist + kSelBins);
+    ++launches;
+    std::vector<int64_t> ht((size_t)tie_count);
+    GS_CUDA(cudaMemcpyAsync(ht.data(), ties, sizeof(int64_t) * (size_t)tie_count,
+                            cudaMemcpyDeviceToHost, stream));
+    GS_CUDA(cudaStreamSynchronize(stream));
+    std::sort(ht.begin(), ht.end());
+    i_cut = ht[(size_t)rank];
+  }
+  k_fixed_flags<<<grid_for(m, kThreads, 8), kThreads, 0, stream>>>(m, seed, T, i_cut, keep);
+  k_flag_count<<<(unsigned)tiles, kThreads, 0, stream>>>(keep, m, cnt);
+  GS_TRY(exclusive_scan_i64(cnt, off, tiles, tmp, stream));
+  k_flag_write<<<(unsigned)tiles, kThreads, 0, stream>>>(gr->dev.col, gr->up_ptr, gr->edge_off,
+                                                         nullptr, n, m, keep, off, d_pairs,
+                                                         nullptr);
+  launches += 6;
+  int64_t kept = 0;
+  GS_CUDA(cudaMemcpyAsync(&kept, off + tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+  GS_CUDA(cudaStreamSynchronize(stream));
+  ws->launches_total += launches;
+  if (kept != k) {
+    set_error("gs_sample_fixed: selected %lld edges instead of %lld", (long long)kept,
+              (long long)k);
+    return GS_ECUDA;
+  }
   return GS_OK;
 }

@@ -182,3 +182,35 @@ def test_core_numbers_and_weighted_sample_at_full_size():
     assert np.array_equal(pw.cpu().numpy(), ww)
     print("R-MAT 24: max core", mx, "weighted 0.1% sample", pairs.shape[0])
     g.close()
+
+
+@pytest.mark.parametrize("name", ["er_2000", "chung_lu_20k"])
+def test_fixed_size_sample_equals_the_oracle(name):
+    rp, col = GRAPHS[name]()
+    g = gs.Graph.from_numpy(rp, col)
+    m = g.m
+    buf = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+    for k, seed in ((0, 1), (1, 1), (17, 2), (m // 3, 3), (m - 1, 4), (m, 5)):
+        got = gs.gs_sample_fixed(g.handle, g.ws.handle, k, seed, buf).cpu().numpy()
+        assert np.array_equal(got, oracle.sample_fixed(rp, col, k, seed)), k
+    g.close()
+
+
+def test_fixed_size_samples_nest_with_bernoulli_at_full_size():
+    """R-MAT 24 (260M edges): exactly k distinct edges, nested in k and
+    between the Bernoulli samples of the same seed whose sizes bracket k."""
+    rp, col = synth.rmat_24()
+    g = gs.Graph.from_numpy(rp, col)
+    lo, hi = g.sample(0.001, 9), g.sample(0.0012, 9)
+    k = (lo.shape[0] + hi.shape[0]) // 2
+    buf = torch.empty((k + 10, 2), dtype=torch.int32, device="cuda")
+    fx = gs.gs_sample_fixed(g.handle, g.ws.handle, k, 9, buf).clone()
+    n = g.info["n"]
+    key = lambda p: (p[:, 0].long() * n + p[:, 1].long())  # noqa: E731
+    kl, kf, kh = key(lo), key(fx), key(hi)
+    assert fx.shape[0] == k and torch.unique(kf).numel() == k
+    assert torch.all(kf[1:] > kf[:-1])  # increasing canonical order
+    assert torch.isin(kl, kf).all() and torch.isin(kf, kh).all()
+    fx2 = gs.gs_sample_fixed(g.handle, g.ws.handle, k - 1000, 9, buf)
+    assert torch.isin(key(fx2), kf).all()
+    g.close()

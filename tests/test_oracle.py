@@ -548,3 +548,43 @@ def test_oracle_pool_returns_the_oracle_per_edge_output_in_order():
     for x in ("t", "a", "b", "k", "q"):
         assert np.array_equal(got[x], want[x]), x
     assert np.array_equal(got3["t"], want["t"][:100])
+
+
+def test_fixed_size_sample_is_the_smallest_keys_and_nested_with_bernoulli():
+    """The keys restated in Python integers agree with the C sampler (each
+    Bernoulli sample is the set of keys below its threshold); a fixed-size
+    sample has exactly k distinct edges, is nested in k, and lies between
+    the Bernoulli samples whose sizes bracket it."""
+    rp, col = synth.er(500, 3000, seed=4)
+    m = len(col) // 2
+    keys = oracle.sample_keys(rp, col, 9)
+    up = synth.upper_pairs(rp, col)
+    for frac in (0.05, 0.3):
+        want = up[keys < int(math.floor(frac * 2.0**53))]
+        assert np.array_equal(want, oracle.sample(rp, col, frac, 9))
+    prev = set()
+    for k in (0, 1, 17, 300, 1500, m):
+        smp = oracle.sample_fixed(rp, col, k, 9)
+        cur = set(map(tuple, smp.tolist()))
+        assert len(smp) == k == len(cur) and prev <= cur
+        prev = cur
+    small = set(map(tuple, oracle.sample(rp, col, 0.1, 9).tolist()))
+    big = set(map(tuple, oracle.sample(rp, col, 0.2, 9).tolist()))
+    mid = set(map(tuple, oracle.sample_fixed(rp, col, (len(small) + len(big)) // 2, 9).tolist()))
+    assert small <= mid <= big
+
+
+def test_fixed_size_sample_is_uniform():
+    """Each edge's inclusion frequency over seeds is k / M."""
+    rp, col = synth.er(60, 200, seed=2)
+    m = len(col) // 2
+    up = synth.upper_pairs(rp, col)
+    keyv = up[:, 0].astype(np.int64) * 60 + up[:, 1]
+    hits = np.zeros(m)
+    trials = 3000
+    for sd in range(trials):
+        smp = oracle.sample_fixed(rp, col, 50, sd)
+        hits[np.searchsorted(keyv, smp[:, 0].astype(np.int64) * 60 + smp[:, 1])] += 1
+    p = 50 / m
+    se = math.sqrt(p * (1 - p) / trials)
+    assert np.all(np.abs(hits / trials - p) <= 5 * se)
