@@ -54,9 +54,10 @@ WORKLOADS = {
 # algorithmic bytes of the 4-node phase: a membership test reads one 4-byte
 # element of the iterated list and one 4-byte word (bitmap or matrix word,
 # directory entry, list entry) that answers it; a dense-edge matrix group
-# ANDs one 16-byte row group with the edge's 16-byte T-mask group
+# reads one 16-byte group of a hub-matrix row (the edge's T-mask group it is
+# ANDed with sits in shared memory)
 BYTES_PER_TEST = 8
-BYTES_PER_DENSE_GROUP = 32
+BYTES_PER_DENSE_GROUP = 16
 
 
 def parse():
