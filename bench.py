@@ -78,7 +78,7 @@ def parse():
                     help="rmat_24 = the headline line; chung_lu_1m alone; batch / serve = the "
                          "batched and served paths against one plain launch per graph / request")
     ap.add_argument("--batch-graphs", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-loads", type=str, default="0.3,0.6,0.9",
                     help="offered loads as fractions of the measured capacity")
@@ -567,12 +567,16 @@ def run_batch_bench(args):
 # ------------------------------------------------------------------ serving
 
 def run_serve_bench(args):
-    """Poisson request stream over 8 resident graphs (ER 2000 x2, Chung-Lu
-    100k x2, Chung-Lu 1M x2, R-MAT 24 x2); fractions log-uniform in
-    [0.1%, 10%], random seeds and non-empty graphlet masks; 4-node masks are
-    not drawn for the R-MAT graphs (their 4-node requests take seconds to a
-    minute each). The server (40 GB budget, 2 lanes) against the same
-    requests run one by one with gs_count_estimate on the same GPU."""
+    """Serving: 8 resident graphs (ER 2000 x2, Chung-Lu 100k x2, Chung-Lu 1M
+    x2, R-MAT 24 x2); each request names a graph, a fraction log-uniform in
+    [0.1%, 10%], a seed and a random non-empty graphlet mask (3-node masks
+    only on the R-MAT graphs: a 4-node R-MAT request takes about 0.7 s per
+    0.1% of its edges, up to 70 s at 10%, four orders of magnitude beyond
+    the offered rate). The capacity of one launch per request (requests run
+    one by one with gs_count_estimate) is measured first; then open-loop
+    Poisson streams at 30%, 60% and 90% of it, and at the offered 2000
+    req/s, run through the server (40 GB budget, 2 lanes) and through one
+    launch per request on the same GPU, with identical results required."""
     import numpy as np
     import torch
 
@@ -592,83 +596,113 @@ def run_serve_bench(args):
             graphs.append(make(base + 10 * len(graphs) + rep))
             names.append(name)
     gen_s = time.time() - t0
-    rng = np.random.default_rng(base)
-    n_req = args.serve_requests
-    arrivals = np.cumsum(rng.exponential(1.0 / args.serve_rate, size=n_req))
-    gidx = rng.integers(0, len(graphs), size=n_req)
-    frac = 10 ** rng.uniform(-3, -1, size=n_req)
-    seeds = rng.integers(1, 2**62, size=n_req)
     all_bits = [3, 4, 7, 8, 9, 10, 11, 12]
-    masks = []
-    for i in range(n_req):
-        bits = [b for b in all_bits if rng.random() < 0.5] or [3]
-        if names[gidx[i]] == "rmat_24":
-            bits = [b for b in bits if b in (3, 4)] or [3]
-        masks.append(sum(1 << b for b in bits))
-    # --- server
+
+    def draw(n_req, seed):
+        rng = np.random.default_rng(seed)
+        gidx = rng.integers(0, len(graphs), size=n_req)
+        frac = 10 ** rng.uniform(-3, -1, size=n_req)
+        seeds = rng.integers(1, 2**62, size=n_req)
+        masks = []
+        for i in range(n_req):
+            bits = [b for b in all_bits if rng.random() < 0.5] or [3]
+            if names[gidx[i]] == "rmat_24":
+                bits = [b for b in bits if b in (3, 4)] or [3]
+            masks.append(sum(1 << b for b in bits))
+        return [(int(gidx[i]), float(frac[i]), int(seeds[i]), masks[i]) for i in range(n_req)]
+
     srv = gs.Server(hbm_budget_bytes=40 << 30, max_batch=64, lanes=2)
     ids = [srv.add_numpy(rp, col) for rp, col in graphs]
     t0 = time.time()
     srv.start()
     start_s = time.time() - t0
-    # warm-up: one request per graph
-    for gi in range(len(graphs)):
+    singles = [gs.Graph.from_numpy(rp, col) for rp, col in graphs]
+    for gi in range(len(graphs)):  # warm-up
         srv.wait(srv.submit(ids[gi], 0.001, 1, gs.GS_THREE_NODE))
-    tickets = []
-    lat, served = [], []
-    try:
+        singles[gi].count_estimate(0.001, 1, gs.GS_THREE_NODE)
+    torch.cuda.synchronize()
+
+    def run_baseline(reqs, arrivals):
+        """One launch per request, in arrival order, open loop."""
+        lat, res = [], []
         t_begin = time.perf_counter()
-        for i in range(n_req):
-            delay = t_begin + arrivals[i] - time.perf_counter()
+        for (gi, f, sd, mk), at in zip(reqs, arrivals):
+            delay = t_begin + at - time.perf_counter()
             if delay > 0:
                 time.sleep(delay)
-            tickets.append(srv.submit(ids[gidx[i]], float(frac[i]), int(seeds[i]), masks[i]))
+            r, _ = singles[gi].count_estimate(f, sd, mk)
+            lat.append((time.perf_counter() - t_begin - at) * 1e3)
+            res.append(r)
+        return lat, res, time.perf_counter() - t_begin
+
+    def run_server(reqs, arrivals):
+        tickets = []
+        t_begin = time.perf_counter()
+        for (gi, f, sd, mk), at in zip(reqs, arrivals):
+            delay = t_begin + at - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append(srv.submit(ids[gi], f, sd, mk))
+        lat, res = [], []
         for t in tickets:
-            res, st = srv.wait(t, 600.0)
+            r, st = srv.wait(t, 900.0)
             lat.append(st["latency_s"] * 1e3)
-            served.append(res)
-        makespan = time.perf_counter() - t_begin
-        info = srv.info()
-    finally:
-        srv.close()
-    torch.cuda.synchronize()
-    # --- baseline: one gs_count_estimate per request, in arrival order
-    singles = [gs.Graph.from_numpy(rp, col) for rp, col in graphs]
-    for g in singles:
-        g.count_estimate(0.001, 1, gs.GS_THREE_NODE)
-    torch.cuda.synchronize()
-    base_lat = []
-    same = True
-    t_begin = time.perf_counter()
-    for i in range(n_req):
-        delay = t_begin + arrivals[i] - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        res, _ = singles[gidx[i]].count_estimate(float(frac[i]), int(seeds[i]), masks[i])
-        base_lat.append((time.perf_counter() - t_begin - arrivals[i]) * 1e3)
-        a, c = res.as_dict(), served[i].as_dict()
-        for g in a:
-            for key in ("X", "V"):
-                x, y = a[g][key], c[g][key]
-                if not ((x != x and y != y) or x == y):
-                    same = False
-    base_makespan = time.perf_counter() - t_begin
+            res.append(r)
+        return lat, res, time.perf_counter() - t_begin
+
+    def same(a_list, b_list):
+        for ra, rb in zip(a_list, b_list):
+            a, c = ra.as_dict(), rb.as_dict()
+            for g in a:
+                for key in ("X", "V"):
+                    x, y = a[g][key], c[g][key]
+                    if not ((x != x and y != y) or x == y):
+                        return False
+        return True
+
+    # capacity of one launch per request: a burst run one by one
+    n_cap = max(40, args.serve_requests // 2)
+    cap_reqs = draw(n_cap, base + 1)
+    lat, _, mk = run_baseline(cap_reqs, [0.0] * n_cap)
+    capacity = n_cap / mk
+    slat, _, smk = run_server(cap_reqs, [0.0] * n_cap)
+    loads = [float(x) for x in args.serve_loads.split(",")]
+    points = []
+    for li, load in enumerate(loads + [None]):
+        rate = args.serve_rate if load is None else load * capacity
+        n_req = args.serve_requests
+        reqs = draw(n_req, base + 10 + li)
+        rng = np.random.default_rng(base + 100 + li)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req)).tolist()
+        s_lat, s_res, s_mk = run_server(reqs, arrivals)
+        b_lat, b_res, b_mk = run_baseline(reqs, arrivals)
+        points.append({
+            "offered": "spec 2000 req/s" if load is None else f"{load:.0%} of capacity",
+            "rate_req_s": round(rate, 2), "requests": n_req,
+            "server": {"p50_ms": round(percentile(s_lat, 50), 2),
+                       "p99_ms": round(percentile(s_lat, 99), 2),
+                       "req_s": round(n_req / s_mk, 2)},
+            "one_launch_per_request": {"p50_ms": round(percentile(b_lat, 50), 2),
+                                       "p99_ms": round(percentile(b_lat, 99), 2),
+                                       "req_s": round(n_req / b_mk, 2)},
+            "identical_results": same(s_res, b_res)})
+    info = srv.info()
+    srv.close()
     for g in singles:
         g.close()
+    head = points[-1]
     return {
-        "metric": "requests/s served (p50/p99 latency)", "value": round(n_req / makespan, 1),
-        "unit": "req/s", "p50_ms": round(percentile(lat, 50), 3),
-        "p99_ms": round(percentile(lat, 99), 3), "higher_is_better": True, "data": "synthetic",
+        "metric": "requests/s served (p50/p99 latency)", "value": head["server"]["req_s"],
+        "unit": "req/s", "p50_ms": head["server"]["p50_ms"], "p99_ms": head["server"]["p99_ms"],
+        "higher_is_better": True, "data": "synthetic",
         "config": {"workload": "serve: 8 resident graphs (ER 2000 x2, Chung-Lu 100k x2, Chung-Lu "
                                "1M x2, R-MAT 24 x2), Poisson arrivals, fractions log-uniform "
                                "[0.1%, 10%], random masks (3-node only on R-MAT)",
-                   "requests": n_req, "offered_rate": args.serve_rate, "budget_gb": 40,
-                   "lanes": 2, "generation_s": round(gen_s, 1), "start_s": round(start_s, 2)},
-        "server": info,
-        "baseline_one_launch_per_request": {"value": round(n_req / base_makespan, 1),
-                                            "p50_ms": round(percentile(base_lat, 50), 3),
-                                            "p99_ms": round(percentile(base_lat, 99), 3)},
-        "identical_results": same,
+                   "budget_gb": 40, "lanes": 2, "generation_s": round(gen_s, 1),
+                   "start_s": round(start_s, 2)},
+        "capacity_one_launch_per_request_req_s": round(capacity, 2),
+        "capacity_server_req_s": round(n_cap / smk, 2),
+        "loads": points, "server": info,
     }
 
 
