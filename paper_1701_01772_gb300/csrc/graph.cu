@@ -17,7 +17,7 @@ constexpr int64_t kDirMinDegree = 16;
 // Mid rows of the mid x big co-degree table start at this degree, and their
 // build adds at most kMidWorkMax wedge increments (higher-degree rows first).
 constexpr int64_t kMidMinDegree = 2;
-constexpr unsigned long long kMidWorkMax = 80000000000ull;
+constexpr unsigned long long kMidWorkMax = 160000000000ull;
 
 // ------------------------------------------------------------- validation
 // One warp per row (grid-stride). Checks the simple-graph conditions of
@@ -208,7 +208,7 @@ __global__ void k_dense_rows(const int64_t* __restrict__ row_ptr, const int32_t*
 // (< 65536), so no carry reaches the neighbouring entry. One warp per vertex;
 // x's big neighbours are gathered in shared memory kBigChunk at a time (the
 // table has at most kBigMax columns).
-constexpr int kBigMax = 4096;
+constexpr int kBigMax = 16384;
 constexpr int kBigChunk = 1024;
 __global__ void __launch_bounds__(256) k_mid_big_pairs(const int64_t* __restrict__ row_ptr,
                                                        const int32_t* __restrict__ col, int64_t n,
@@ -272,6 +272,63 @@ __global__ void k_mid_big_work(const int64_t* __restrict__ row_ptr, const int32_
     acc += (unsigned long long)m * b;
   }
   if (lane == 0 && acc) atomicAdd(total, acc);
+}
+
+// Pilot of the mid x big table's shape: for a deterministic spread of
+// canonical edges (edge j * m / P for j < P), every 4-node item w of the
+// edge (w in N(u) \ {v}, u the endpoint of smaller degree) queries the
+// co-degree c(w, o), o = u for w in T, o = v otherwise, which costs
+// min(d_w, d_o) membership tests unless a table answers it. Items with
+// exactly one table vertex among (w, o) are recorded as (degree of the
+// table vertex, degree of the other, cost); the cost of items with none
+// is added to rest[0]. One warp per pilot edge.
+struct PilotItem {
+  int32_t d_tab, d_other, cost, pad;
+};
+
+__global__ void k_md_pilot(DevGraph g, const int32_t* __restrict__ tb_slot,
+                           const int64_t* __restrict__ edge_off, int64_t P, int64_t cap,
+                           PilotItem* __restrict__ items, unsigned long long* __restrict__ count,
+                           unsigned long long* __restrict__ rest) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t m = g.nnz / 2;
+  unsigned long long none = 0;
+  for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < P; j += warps) {
+    const int64_t i = (int64_t)((__int128)j * m / P);
+    int64_t lo = 0, len = g.n;  // row owning canonical edge i
+    while (len > 1) {
+      const int64_t half = len >> 1;
+      lo = (edge_off[lo + half] <= i) ? lo + half : lo;
+      len -= half;
+    }
+    const int32_t x = (int32_t)lo, y = g.col[g.up_ptr[lo] + (i - edge_off[lo])];
+    const int64_t dx = g.row_ptr[x + 1] - g.row_ptr[x], dy = g.row_ptr[y + 1] - g.row_ptr[y];
+    const bool xs = dx < dy || (dx == dy && x < y);
+    const int32_t u = xs ? x : y, v = xs ? y : x;
+    const int64_t bu = g.row_ptr[u], du = xs ? dx : dy, bv = g.row_ptr[v], dv = xs ? dy : dx;
+    for (int64_t p = lane; p < du; p += 32) {
+      const int32_t w = g.col[bu + p];
+      if (w == v) continue;
+      const bool in_t = adj_contains(g, v, bv, dv, w);
+      const int32_t o = in_t ? u : v;
+      const int64_t dw = g.row_ptr[w + 1] - g.row_ptr[w], dob = in_t ? du : dv;
+      const int64_t cost = dw < dob ? dw : dob;
+      const bool tw = tb_slot[w] >= 0, to = tb_slot[o] >= 0;
+      if (tw && to) continue;
+      if (!tw && !to) {
+        none += (unsigned long long)cost;
+        continue;
+      }
+      const unsigned long long at = atomicAdd(count, 1ull);
+      if ((int64_t)at < cap)
+        items[at] = PilotItem{(int32_t)(tw ? dw : dob), (int32_t)(tw ? dob : dw),
+                              (int32_t)(cost < INT32_MAX ? cost : INT32_MAX), 0};
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) none += __shfl_xor_sync(0xffffffffu, none, o);
+  if (lane == 0 && none) atomicAdd(rest, none);
 }
 
 // Marks mid vertices (lo <= degree < hi, no table slot) and big vertices
@@ -756,61 +813,101 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     }
   }
   // ---- mid x big co-degrees: rows for the highest-degree vertices below
-  // the table (degree >= kMidMinDegree), columns for the top 1024-4096 table
-  // vertices; whatever the budget has left
+  // the table (degree >= kMidMinDegree), columns for the top 1024-16384
+  // table vertices; whatever the budget has left
   double used = (double)n_bm * (double)words * 4.0 +
                 (double)n_hm * (double)g->dev.hm_words * 4.0 +
                 (double)g->dev.tb_count * (double)g->dev.tb_count + dir_bytes;
   const int64_t d_hi = d_tb < 65536 ? d_tb : 65536;
   if (g->dev.tb_count > 1 && d_hi > kMidMinDegree && (double)budget > used) {
-    // columns: the widest of 4096 / 2048 / 1024 top table vertices for which
-    // every vertex of degree [kMidMinDegree, d_hi) gets a row in the budget
-    auto count_ge = [&](int64_t d, int64_t* c) -> gs_status {
-      GS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream));
-      k_count_deg_ge<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, n, d, d_cnt);
-      unsigned long long h = 0;
-      GS_CUDA(cudaMemcpyAsync(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, stream));
-      GS_CUDA(cudaStreamSynchronize(stream));
-      *c = (int64_t)h;
-      return GS_OK;
-    };
-    int64_t c_lo = 0, c_hi = 0;
-    GS_TRY(count_ge(kMidMinDegree, &c_lo));
-    GS_TRY(count_ge(d_hi, &c_hi));
-    const double rows_all = (double)(c_lo - c_hi);
-    int64_t d_bg = 0, n_bg = 0;
-    for (int64_t cols = kBigMax; cols >= kBigChunk; cols /= 2) {
-      const int64_t bg_cap = g->dev.tb_count < cols ? g->dev.tb_count : cols;
-      GS_TRY(hub_threshold(g, bg_cap, d_tb, d_cnt, stream, &d_bg, &n_bg));
-      if (rows_all * 2.0 * (double)n_bg <= (double)budget - used) break;
-    }
-    const int64_t md_cap = n_bg > 0 ? (int64_t)(((double)budget - used) / (2.0 * (double)n_bg)) : 0;
-    // lowest degree d_md >= kMidMinDegree with at most md_cap mid vertices
-    int64_t d_md = 0, n_ge = 0;
-    if (md_cap > 0)
-      GS_TRY(hub_threshold(g, md_cap + g->dev.tb_count, kMidMinDegree, d_cnt, stream, &d_md, &n_ge));
-    // and, raising d_md if needed, at most kMidWorkMax build increments
-    auto work_at = [&](int64_t lo, unsigned long long* w) -> gs_status {
+    // shape: columns = the top 1024 .. 16384 table vertices by degree, rows
+    // = the highest-degree mid vertices that fit next to them in the budget
+    // (and whose build stays within kMidWorkMax increments); the shape kept
+    // leaves the fewest membership tests on a pilot of the graph's own edges
+    // (measured miss cost of each shape)
+    auto work_at = [&](int64_t lo, int64_t big, unsigned long long* w) -> gs_status {
       GS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream));
       k_mid_big_work<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.col, n,
-                                                                   lo, d_hi, d_bg, d_cnt);
+                                                                   lo, d_hi, big, d_cnt);
       GS_CUDA(cudaMemcpyAsync(w, d_cnt, sizeof(*w), cudaMemcpyDeviceToHost, stream));
       GS_CUDA(cudaStreamSynchronize(stream));
       return GS_OK;
     };
-    if (md_cap > 0 && n_bg > 0 && d_md < d_hi) {
+    // pilot items
+    constexpr int64_t kPilotEdges = 2048;
+    constexpr int64_t kPilotCap = (int64_t)1 << 23;
+    std::vector<PilotItem> pilot;
+    {
+      PilotItem* d_items = nullptr;
+      unsigned long long* d_pc = nullptr;
+      if (cudaMalloc(&d_items, sizeof(PilotItem) * (size_t)kPilotCap) == cudaSuccess &&
+          cudaMalloc(&d_pc, 2 * sizeof(unsigned long long)) == cudaSuccess) {
+        cudaMemsetAsync(d_pc, 0, 2 * sizeof(unsigned long long), stream);
+        const int64_t P = g->m < kPilotEdges ? g->m : kPilotEdges;
+        k_md_pilot<<<grid_for(P * 32, 256, 8), 256, 0, stream>>>(
+            g->dev, g->tb_slot, g->edge_off, P, kPilotCap, d_items, d_pc, d_pc + 1);
+        unsigned long long hc[2] = {0, 0};
+        cudaMemcpyAsync(hc, d_pc, sizeof(hc), cudaMemcpyDeviceToHost, stream);
+        cudaError_t pe = cudaStreamSynchronize(stream);
+        if (pe == cudaSuccess) {
+          const int64_t cnt = (int64_t)hc[0] < kPilotCap ? (int64_t)hc[0] : kPilotCap;
+          pilot.resize((size_t)cnt);
+          if (cnt > 0)
+            pe = cudaMemcpy(pilot.data(), d_items, sizeof(PilotItem) * (size_t)cnt,
+                            cudaMemcpyDeviceToHost);
+        }
+        if (pe != cudaSuccess) {
+          cudaFree(d_items);
+          cudaFree(d_pc);
+          return cuda_fail(pe, "mid x big pilot", __FILE__, __LINE__);
+        }
+      }
+      cudaFree(d_items);
+      cudaFree(d_pc);
+      cudaGetLastError();  // an allocation that failed only skips the pilot
+    }
+    int64_t d_bg = 0, n_bg = 0, d_md = d_hi;
+    double best = -1.0;
+    for (int64_t cols = kBigChunk; cols <= kBigMax; cols *= 2) {
+      const int64_t bg_cap = g->dev.tb_count < cols ? g->dev.tb_count : cols;
+      int64_t dbg = 0, nbg = 0;
+      GS_TRY(hub_threshold(g, bg_cap, d_tb, d_cnt, stream, &dbg, &nbg));
+      if (nbg <= 0) continue;
+      const int64_t md_cap = (int64_t)(((double)budget - used) / (2.0 * (double)nbg));
+      if (md_cap <= 0) continue;
+      // lowest degree d_md >= kMidMinDegree with at most md_cap mid vertices
+      int64_t dmd = 0, n_ge = 0;
+      GS_TRY(hub_threshold(g, md_cap + g->dev.tb_count, kMidMinDegree, d_cnt, stream, &dmd,
+                           &n_ge));
+      if (dmd >= d_hi) continue;
+      // and, raising d_md if needed, at most kMidWorkMax build increments
       unsigned long long w = 0;
-      GS_TRY(work_at(d_md, &w));
+      GS_TRY(work_at(dmd, dbg, &w));
       if (w > kMidWorkMax) {
-        int64_t lo = d_md, hi = d_hi;  // work(lo) too large, work(hi) = 0
+        int64_t lo = dmd, hi = d_hi;  // work(lo) too large, work(hi) = 0
         while (hi - lo > 1) {
           const int64_t mid = lo + (hi - lo) / 2;
-          GS_TRY(work_at(mid, &w));
+          GS_TRY(work_at(mid, dbg, &w));
           if (w <= kMidWorkMax) hi = mid; else lo = mid;
         }
-        d_md = hi;
+        dmd = hi;
       }
+      if (dmd >= d_hi) continue;
+      // pilot tests this shape answers
+      double saved = 0.0;
+      for (const PilotItem& it : pilot)
+        if (it.d_tab >= dbg && it.d_other >= dmd && it.d_other >= kMidMinDegree &&
+            it.d_other < d_hi)
+          saved += (double)it.cost;
+      if (saved > best) {  // ties keep the narrower shape
+        best = saved;
+        d_bg = dbg;
+        n_bg = nbg;
+        d_md = dmd;
+      }
+      if (bg_cap == g->dev.tb_count) break;
     }
+    const int64_t md_cap = n_bg > 0 ? 1 : 0;
     if (md_cap > 0 && d_md < d_hi) {
       int32_t* hubs = nullptr;
       GS_TRY(assign(d_bg, &g->bg_slot, &hubs, n_bg));
