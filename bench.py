@@ -45,6 +45,11 @@ WORKLOADS = {
         "edges), int32 CSR; exact 3-node counts (G3, G4) over all edges plus 4-node "
         "estimates (G3, G4, G7-G12) at 0.1% and 1% edge samples (seeded, library sampler)",
         [("exact_3node", 1.0, THREE), ("0.001", 0.001, CONN), ("0.01", 0.01, CONN)]),
+    "rmat_22": (
+        "rmat_22: R-MAT scale 22, edge factor 16, (a,b,c,d)=(0.57,0.19,0.19,0.05), "
+        "symmetrised, deduplicated, self-loops removed (4,194,304 vertices), int32 CSR; the "
+        "headline's parts on a graph small enough for full ncu counter captures",
+        [("exact_3node", 1.0, THREE), ("0.001", 0.001, CONN), ("0.01", 0.01, CONN)]),
     "chung_lu_1m": (
         "chung_lu_1m: Chung-Lu n=1,000,000, m~20M, degree exponent 2.1, expected degree "
         "cap 50,000, int32 CSR; edge-sample fractions 1%, 5%, 10% (seeded, library sampler) "
@@ -73,10 +78,11 @@ def parse():
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the Chung-Lu 1M measurement after the headline")
     ap.add_argument("--extra-steps", type=int, default=5)
-    ap.add_argument("--workload", choices=("rmat_24", "chung_lu_1m", "batch", "serve"),
+    ap.add_argument("--workload", choices=("rmat_24", "rmat_22", "chung_lu_1m", "batch", "serve"),
                     default="rmat_24",
-                    help="rmat_24 = the headline line; chung_lu_1m alone; batch / serve = the "
-                         "batched and served paths against one plain launch per graph / request")
+                    help="rmat_24 = the headline line; chung_lu_1m alone; rmat_22 = the small "
+                         "case for counter captures; batch / serve = the batched and served "
+                         "paths against one plain launch per graph / request")
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
@@ -87,7 +93,11 @@ def parse():
 
 def generate(name):
     import synth
-    return synth.rmat_24() if name == "rmat_24" else synth.chung_lu_1m()
+    if name == "rmat_24":
+        return synth.rmat_24()
+    if name == "rmat_22":
+        return synth.rmat(22, 16, synth.BASE_SEED + 2)
+    return synth.chung_lu_1m()
 
 
 # ------------------------------------------------------------------ helpers
@@ -242,6 +252,8 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
     def seed_of(step, fi):
         return (rank * 1_000_003 + step * 101 + fi * 7 + 1) & (2**63 - 1)
 
+    part_stats = {}
+
     def one_step(step):
         """Every part of the workload: sample (fraction < 1) + count +
         estimate. Returns (edges, [(label, ms)], [(stats)], incidences)."""
@@ -263,6 +275,10 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
             lat.append((label, ev0.elapsed_time(ev1)))
             quad.append((st.ms_quad, st.quad_tests - st.dense_groups, st.dense_groups,
                          st.model_quad_bytes))
+            part_stats[label] = {"K": k, "tri_tests": st.tri_tests, "ms_tri": round(st.ms_tri, 3),
+                                 "quad_tests": st.quad_tests - st.dense_groups,
+                                 "dense_groups": st.dense_groups, "ms_quad": round(st.ms_quad, 3),
+                                 "ms_cost": round(st.ms_cost, 3)}
             edges += k
             inc += incidences_from_numerators({gid: v[0] for gid, v in sums.sums().items()})
         return edges, lat, quad, inc
@@ -318,7 +334,8 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
             host_lists.append((pair_buf[:k].cpu().pin_memory(), mask))
     dev_buf = torch.empty_like(pair_buf)
     e2e_edges, e2e_ms, h2d, d2h = 0, 0.0, 0, 0
-    for step in range(steps):
+    e2e_steps = max(1, min(steps, 5))  # the same step, repeated at most 5 times
+    for step in range(e2e_steps):
         flush.fill_((step + 7) & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -337,8 +354,8 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
     e2e = {"value": e2e_edges / (e2e_ms / 1e3), "unit": UNIT,
-           "h2d_bytes_per_step": h2d // max(steps, 1),
-           "d2h_bytes_per_step": d2h // max(steps, 1)}
+           "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+           "steps": e2e_steps}
 
     peak, peak_kind = load_peaks()
     alg_bytes = BYTES_PER_TEST * tests + BYTES_PER_DENSE_GROUP * groups
@@ -373,7 +390,7 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
         "e2e": e2e, "roofline": roofline, "launches": launches, "clocks": clocks.summary(),
         "graph": g.info, "parts": [label for label, _, _ in parts],
         "registration_s": round(registration_s, 3), "index_bytes": int(index_bytes),
-        "workspace_bytes": int(ws.nbytes()),
+        "workspace_bytes": int(ws.nbytes()), "part_stats": part_stats,
     }
     g.close()
     del pair_buf, flush, dev_buf, row_ptr, colt
@@ -719,7 +736,7 @@ def line_from(r, args, world, steps, warmup, cpu=None):
                    "l2": "flushed (256 MiB write) before every timed step; CSR > L2",
                    "hub_index": {k: r["graph"][k] for k in ("bitmap_hubs", "table_hubs")},
                    "parallelism": f"replicas x{world}"},
-        "latency_ms": r["lat"],
+        "latency_ms": r["lat"], "part_stats_last_step": r["part_stats"],
         "graphlets_per_s": round(r["inc_all"] / (r["ms_total"] / 1e3), 1),
         "registration_s": r["registration_s"], "index_bytes": r["index_bytes"],
         "workspace_bytes": r["workspace_bytes"],
