@@ -250,6 +250,17 @@ struct gs_graph {
   int32_t* col_tb;
   int32_t* tb_giant;
   uint32_t* tb_giant_codeg;
+  // edges oriented from the lower to the higher (degree, id) endpoint, for
+  // the exact 3-node pass (NULL when not built): out- and in-lists in
+  // increasing id, in_pos = position of v in N+(u) for the in-edge u -> v,
+  // orient_units = scanned work units per vertex
+  int64_t* out_ptr;
+  int32_t* out_col;
+  int64_t* in_ptr;
+  int32_t* in_col;
+  uint32_t* in_pos;
+  int64_t* orient_units;
+  int64_t max_out_degree;
 };
 
 namespace gs {
@@ -363,6 +374,11 @@ int64_t launch_fold_seg(const DevGraph& g, bool four, const int64_t* seg_off, Co
                         cudaStream_t stream);
 gs_status fetch_error(DevError* d_err, cudaStream_t stream, const char* what);
 void store_sums(const unsigned long long* h, uint32_t mask, gs_sums* out);
+// tri_oriented.cu: oriented lists at registration and the exact 3-node pass
+// over every edge through them (sums in gs_count's 32-word layout).
+gs_status build_oriented(gs_graph* g, cudaStream_t stream);
+gs_status count_tri_oriented(const gs_graph* g, gs_workspace* ws, unsigned long long* h_sums,
+                             unsigned long long* h_stats, int64_t* launches, cudaStream_t stream);
 gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs, int64_t K,
                     uint32_t mask, bool check_dup, int64_t* d_per_edge, const int64_t* seg_off,
                     int64_t nseg, const Tuning& tu, CountBufs& b, cudaStream_t stream,

@@ -1510,8 +1510,32 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
     set_error("gs_count: with d_pairs = NULL, k must equal the edge count %lld", (long long)gr->m);
     return GS_EINVAL;
   }
-  CountBufs b;
   const Tuning tu = ws->has_tuning ? ws->tuning : default_tuning();
+  if (d_pairs == nullptr && d_per_edge == nullptr && (mask & ~(uint32_t)GS_THREE_NODE) == 0 &&
+      gr->out_col != nullptr && tu.use_hubs) {
+    // every edge, triangles and 2-stars only: triangles listed once through
+    // the oriented lists (same per-edge t, sums independent of the order)
+    unsigned long long h[32], hs[8];
+    int64_t nl = 0;
+    GS_TRY(count_tri_oriented(gr, ws, h, hs, &nl, stream));
+    store_sums(h, mask, h_sums);
+    gs_stats& st = ws->stats;
+    st.k = K;
+    st.tri_tests = (int64_t)hs[0];
+    st.model_bytes = hs[2];
+    st.model_tri_bytes = hs[2];
+    st.launches = nl;
+    ws->launches_total += nl;
+    st.timed = ws->timing;
+    if (ws->timing) {
+      float* ms[6] = {&st.ms_prep, &st.ms_tri, &st.ms_compact, &st.ms_cost, &st.ms_quad,
+                      &st.ms_fold};
+      for (int ph = 0; ph < 6; ++ph)
+        cudaEventElapsedTime(ms[ph], ws->ev[2 * ph], ws->ev[2 * ph + 1]);
+    }
+    return GS_OK;
+  }
+  CountBufs b;
   GS_TRY(count_run(gr, ws, d_pairs, K, mask, d_pairs != nullptr, d_per_edge, nullptr, 0, tu, b,
                    stream, "gs_count"));
   const bool four = (mask & (GS_G7 | GS_G8 | GS_G9 | GS_G10 | GS_G11 | GS_G12)) != 0;

@@ -1082,6 +1082,8 @@ extern "C" gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_
   }
   gs_status hs = build_hub_index(g, hub_budget_bytes, stream);
   if (hs != GS_OK) return fail(hs);
+  hs = build_oriented(g, stream);
+  if (hs != GS_OK) return fail(hs);
   if (n <= kDenseGraphMax && hub_budget_bytes != 1) {
     // a small graph gets its whole adjacency as a bit matrix (Sec. 2.6 notes
     // adjacency matrices for small graphs); a 1-byte budget turns every
@@ -1116,6 +1118,12 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->col_tb);
   cudaFree(g->tb_giant);
   cudaFree(g->tb_giant_codeg);
+  cudaFree(g->out_ptr);
+  cudaFree(g->out_col);
+  cudaFree(g->in_ptr);
+  cudaFree(g->in_col);
+  cudaFree(g->in_pos);
+  cudaFree(g->orient_units);
   delete g;
   return GS_OK;
 }
