@@ -255,23 +255,22 @@ gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);
 gs_status gs_sample_size(const gs_sums* s, double z, double rel_err, int64_t* k_out);
 
 /* Algorithm 8 (adaptive estimation): grows the sampled edge set until the
- * estimates stop moving. Iteration t adds the edges whose sampler key
- * (gs_sample's) lies between fractions p_{t-1} and p_t = p_{t-1} +
- * phi_t (1 - p_{t-1}) -- a uniform sample without replacement of about
- * phi_t of the edges not yet sampled -- counts only those (mask as in
- * gs_count), merges their exact sums into the running ones and
+ * estimates stop moving. Iteration t adds K_t = ceil(phi_t (m - |J|)) edges
+ * drawn uniformly without replacement from those not yet sampled -- the
+ * next K_t edges in the order of gs_sample's sampler keys, so J is always
+ * the |J| smallest keys (gs_sample_fixed(|J|, seed)) -- counts only those
+ * (mask as in gs_count), merges their exact sums into the running ones and
  * re-estimates; phi_{t+1} = phi_t / 2. The loss is the maximum relative
  * change max_i |X_i^(t) - X_i^(t-1)| / |X_i^(t-1)| over the 4-node
  * graphlets of the mask (the objective of Sec. 4 takes its maximum over
  * G^(4); a mask with none uses its 3-node graphlets); an unchanged estimate
- * counts 0 (also 0 -> 0), a change away from 0 counts as infinite. An
- * iteration with no earlier defined estimate (the first, or every earlier
- * sample empty) has loss 1. The loop stops when the loss is at most
+ * counts 0 (also 0 -> 0), a change away from 0 counts as infinite. The
+ * first iteration has loss 1. The loop stops when the loss is at most
  * beta (0 <= beta < 1; the first iteration always runs) or after t_max
  * iterations. phi <= 0 selects phi_1 = 1 / sqrt(m).
  * Outputs (host): the running sums, their estimates (z as gs_estimate),
- * the iterations run and the final fraction p. Because the samples are
- * nested, the result equals gs_count over gs_sample(p, seed).
+ * the iterations run and the final sampled fraction |J| / m. The result
+ * equals gs_count over gs_sample_fixed(|J|, seed).
  * Synchronises `stream`. */
 gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, double beta, int32_t t_max,
                             double phi, uint64_t seed, uint32_t mask, double z,
@@ -377,6 +376,14 @@ gs_status gs_micro(const gs_graph* g, gs_workspace* ws, const int32_t* d_pairs, 
  * increasing i); 0 <= k <= m. Synchronises `stream`. */
 gs_status gs_sample_fixed(const gs_graph* g, gs_workspace* ws, int64_t k, uint64_t seed,
                           int32_t* d_pairs, void* stream);
+
+/* The edges ranked [k_lo, k_hi) by gs_sample's sampler key (ties by
+ * canonical index), written in increasing canonical index to d_pairs
+ * (device int32[2 (k_hi - k_lo)]): the edges gs_sample_fixed(k_hi) adds to
+ * gs_sample_fixed(k_lo), so a sample can be grown without replacement by
+ * any number of edges. 0 <= k_lo <= k_hi <= m. Synchronises `stream`. */
+gs_status gs_sample_ranks(const gs_graph* g, gs_workspace* ws, int64_t k_lo, int64_t k_hi,
+                          uint64_t seed, int32_t* d_pairs, void* stream);
 
 /* ---- weighted sampling (Sec. 3.1's weighted distribution F) ------------
  * k-core numbers: d_core (device int32[n]) receives the largest k such that

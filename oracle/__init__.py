@@ -462,28 +462,32 @@ def relative_change(x: float, prev: float) -> float:
 
 def adaptive_estimate(row_ptr, col, beta: float, t_max: int, phi: float, seed: int,
                       graphlets=GRAPHLETS, z: float = Z95) -> dict:
-    """Algorithm 8 with the Bernoulli sampler of ``sample``: iteration t
-    grows the sampled set by about phi of the edges not yet sampled (the
-    fraction goes from p to p + phi (1 - p), which adds exactly the edges
-    whose key lies between the two, since the samples are nested), recomputes
-    the estimates from everything sampled so far, takes as loss the maximum
-    relative change (``relative_change``) of the estimates of the 4-node
-    graphlets among ``graphlets`` (``adaptive_loss_graphlets``) since the
-    previous iteration, and halves phi after the draw; it stops when the
-    loss is at most beta or after t_max iterations. An iteration with no
-    previous defined estimate (the first, or every earlier sample empty) has
-    loss 1. phi <= 0 means 1 / sqrt(M)."""
+    """Algorithm 8: iteration t draws K_t = ceil(phi_t (M - |J|)) new edges
+    uniformly without replacement from those not yet sampled -- the next
+    K_t edges in sampler-key order, so J is always the |J| smallest keys
+    (``sample_fixed``) -- recomputes the estimates from everything sampled
+    so far, takes as loss the maximum relative change (``relative_change``)
+    of the estimates of the 4-node graphlets among ``graphlets``
+    (``adaptive_loss_graphlets``) since the previous iteration, and halves
+    phi after the draw; it stops when the loss is at most beta or after
+    t_max iterations. The first iteration has loss 1. phi <= 0 means
+    1 / sqrt(M)."""
+    from synth import upper_pairs  # input helper only: lists the edges
     m = len(col) // 2
     if not phi > 0:
         phi = 1.0 / math.sqrt(m) if m > 0 else 1.0
     loss_set = adaptive_loss_graphlets(graphlets)
-    p, loss, t = 0.0, 1.0, 0
+    keys = sample_keys(row_ptr, col, seed)
+    order = np.lexsort((np.arange(m), keys))
+    up = upper_pairs(np.asarray(row_ptr), np.asarray(col))
+    J, loss, t = 0, 1.0, 0
     prev = None
     pairs = np.zeros((0, 2), dtype=np.int32)
     est = s = s2 = None
     while loss > beta and t < t_max:
-        p_new = p + phi * (1.0 - p)
-        pairs = sample(row_ptr, col, p_new, seed)
+        K_t = int(math.ceil(phi * float(m - J)))
+        J = min(m, J + K_t)
+        pairs = up[np.sort(order[:J])]
         lc = local_counts(row_ptr, col, pairs)
         s, s2 = numerators(lc)
         est = estimate(s, s2, m, len(pairs), z)
@@ -494,7 +498,7 @@ def adaptive_estimate(row_ptr, col, beta: float, t_max: int, phi: float, seed: i
             loss = max(relative_change(x[g], prev[g]) for g in loss_set)
         if len(pairs) > 0:
             prev = x
-        p = p_new
         phi *= 0.5
         t += 1
-    return {"iters": t, "p": p, "K": len(pairs), "sums": s, "sq": s2, "est": est}
+    return {"iters": t, "p": J / m if m else 0.0, "K": len(pairs), "sums": s, "sq": s2,
+            "est": est}

@@ -226,6 +226,7 @@ def lib() -> ctypes.CDLL:
         "gs_sample_size": ([ctypes.POINTER(GsSums), D, D, PI64], ctypes.c_int32),
         "gs_core_numbers": ([P, P, P, ctypes.POINTER(ctypes.c_int32), P], ctypes.c_int32),
         "gs_sample_fixed": ([P, P, I64, U64, P, P], ctypes.c_int32),
+        "gs_sample_ranks": ([P, P, I64, I64, U64, P, P], ctypes.c_int32),
         "gs_sample_weighted": ([P, P, P, D, U64, P, P, I64, PI64, ctypes.POINTER(ctypes.c_double),
                                 P], ctypes.c_int32),
         "gs_count_weighted": ([P, P, P, I64, P, D, U32, D, ctypes.POINTER(GsResult), P],
@@ -487,6 +488,19 @@ def gs_sample_fixed(graph: int, ws: int, k: int, seed: int, out_pairs, stream=No
     if out_pairs.dim() != 2 or out_pairs.shape[1] != 2 or out_pairs.shape[0] < k:
         raise ValueError("out_pairs must be a [>= k, 2] tensor")
     _check(lib().gs_sample_fixed(graph, ws, int(k), seed & (2**64 - 1),
+                                 _dev(out_pairs, torch.int32, "out_pairs"), _stream_ptr(stream)))
+    return out_pairs[:k]
+
+
+def gs_sample_ranks(graph: int, ws: int, k_lo: int, k_hi: int, seed: int, out_pairs,
+                    stream=None):
+    """Edges ranked [k_lo, k_hi) by sampler key into out_pairs (CUDA int32
+    [>= k_hi - k_lo, 2]); returns out_pairs[:k_hi - k_lo]."""
+    import torch
+    k = k_hi - k_lo
+    if out_pairs.dim() != 2 or out_pairs.shape[1] != 2 or out_pairs.shape[0] < k:
+        raise ValueError("out_pairs must be a [>= k_hi - k_lo, 2] tensor")
+    _check(lib().gs_sample_ranks(graph, ws, int(k_lo), int(k_hi), seed & (2**64 - 1),
                                  _dev(out_pairs, torch.int32, "out_pairs"), _stream_ptr(stream)))
     return out_pairs[:k]
 

@@ -306,6 +306,11 @@ gs_status sample_impl(const gs_graph* g, gs_workspace* ws, double fraction, uint
 // Samples canonical edges [e0, e0 + m) (hash index relative to e0).
 // Edges of [e0, e0 + m) whose sampler key lies in [fraction_lo, fraction)
 // x 2^53 (fraction_lo = 0: the Bernoulli(fraction) sample).
+// Edges ranked [k_lo, k_hi) by their sampler key (ties by canonical index),
+// in increasing canonical index; d_pairs NULL: into workspace slot 3.
+gs_status sample_ranks(const gs_graph* g, gs_workspace* ws, int64_t k_lo, int64_t k_hi,
+                       uint64_t seed, int32_t* d_pairs, int32_t** pairs_out,
+                       cudaStream_t stream);
 gs_status sample_range(const gs_graph* g, gs_workspace* ws, double fraction, uint64_t seed,
                        int64_t e0, int64_t m, int32_t* d_pairs, int64_t max_k, int64_t* k_out,
                        int32_t** pairs_out, cudaStream_t stream, double fraction_lo = 0.0);

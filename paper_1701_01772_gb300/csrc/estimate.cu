@@ -271,16 +271,21 @@ extern "C" gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, doub
   const uint32_t four = mask & (GS_G7 | GS_G8 | GS_G9 | GS_G10 | GS_G11 | GS_G12);
   const uint32_t loss_mask = four != 0 ? four : mask;
   static const uint32_t bit[8] = {GS_G3, GS_G4, GS_G7, GS_G8, GS_G9, GS_G10, GS_G11, GS_G12};
-  double p = 0.0, loss = 1.0;
+  double loss = 1.0;
   double prev[8];
   bool have_prev = false;
   int32_t t = 0;
+  int64_t J = 0;  // edges sampled so far: the J smallest sampler keys
   while (loss > beta && t < t_max) {
-    const double p_new = p + phi * (1.0 - p);
-    int64_t K = 0;
+    // K_t = ceil(phi (M - |J|)) new edges, uniformly without replacement:
+    // the next K_t edges in sampler-key order
+    const int64_t Kt = (int64_t)ceil(phi * (double)(M - J));
+    const int64_t J_new = J + Kt < M ? J + Kt : M;
+    const int64_t K = J_new - J;
     int32_t* pairs = nullptr;
-    GS_TRY(gs::sample_range(g, ws, p_new, seed, 0, M, nullptr, 0, &K, &pairs, stream, p));
-    if (K > 0) {  // (a ring can be empty on a small graph)
+    GS_TRY(gs::sample_ranks(g, ws, J, J_new, seed, nullptr, &pairs, stream));
+    J = J_new;
+    if (K > 0) {
       gs_sums part;
       GS_TRY(gs_count(g, ws, pairs, K, mask, nullptr, &part, stream));
       part.m = M;
@@ -307,12 +312,11 @@ extern "C" gs_status gs_count_adaptive(const gs_graph* g, gs_workspace* ws, doub
       for (int i = 0; i < 8; ++i) prev[i] = out->x[i];
       have_prev = true;
     }
-    p = p_new;
     phi *= 0.5;
     ++t;
   }
   if (iters_out) *iters_out = t;
-  if (fraction_out) *fraction_out = p;
+  if (fraction_out) *fraction_out = M > 0 ? (double)J / (double)M : 0.0;
   return GS_OK;
 }
 

@@ -265,13 +265,16 @@ __global__ void k_key_ties(int64_t m, uint64_t seed, uint64_t T, int64_t cap,
   }
 }
 
-// keep[i] = key < T, or key == T and i <= i_cut.
-__global__ void k_fixed_flags(int64_t m, uint64_t seed, uint64_t T, int64_t i_cut,
-                              uint8_t* __restrict__ keep) {
+// keep[i]: (key, i) among the k_hi smallest and not among the k_lo
+// smallest; each set is {key < T} plus {key == T, i <= i_cut}.
+__global__ void k_fixed_flags(int64_t m, uint64_t seed, uint64_t T_lo, int64_t cut_lo,
+                              uint64_t T_hi, int64_t cut_hi, uint8_t* __restrict__ keep) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     const uint64_t key = splitmix(seed ^ splitmix((uint64_t)i)) >> 11;
-    keep[i] = (key < T || (key == T && i <= i_cut)) ? 1 : 0;
+    const bool in_hi = key < T_hi || (key == T_hi && i <= cut_hi);
+    const bool in_lo = key < T_lo || (key == T_lo && i <= cut_lo);
+    keep[i] = (in_hi && !in_lo) ? 1 : 0;
   }
 }
 
@@ -588,43 +591,36 @@ extern "C" gs_status gs_count_weighted(const gs_graph* gr, gs_workspace* ws,
   return GS_OK;
 }
 
-extern "C" gs_status gs_sample_fixed(const gs_graph* gr, gs_workspace* ws, int64_t k,
-                                     uint64_t seed, int32_t* d_pairs, void* stream_) {
-  cudaStream_t stream = (cudaStream_t)stream_;
-  if (gr == nullptr || ws == nullptr || k < 0 || k > gr->m || (k > 0 && d_pairs == nullptr)) {
-    set_error("gs_sample_fixed: invalid arguments (need 0 <= k <= m and an output)");
-    return GS_EINVAL;
+namespace gs {
+
+// Boundary of the k smallest (key, i) of the sampler keys: the set is
+// {key < T} plus {key == T, i <= i_cut}; k = 0 gives the empty set.
+struct RankCut {
+  uint64_t T;
+  int64_t i_cut;
+};
+
+static gs_status rank_cut(const gs_graph* gr, int64_t k, uint64_t seed,
+                          unsigned long long* hist, int64_t* ties, int64_t tie_cap,
+                          int64_t* launches, RankCut* out, cudaStream_t stream) {
+  const int64_t m = gr->m;
+  if (k <= 0) {
+    *out = RankCut{0, -1};
+    return GS_OK;
   }
-  const int64_t n = gr->dev.n, m = gr->m;
-  if (k == 0) return GS_OK;
-  constexpr int64_t kTieCap = 1 << 16;
-  const int64_t tiles = (m + kSampTile - 1) / kSampTile;
-  const size_t bytes = Carve::bytes_for<unsigned long long>(kSelBins + 8) +
-                       Carve::bytes_for<int64_t>(kTieCap) + Carve::bytes_for<uint8_t>(m) +
-                       Carve::bytes_for<int64_t>(tiles + 1) * 2 +
-                       Carve::bytes_for<int64_t>(scan_tmp_elems(tiles));
-  void* base = nullptr;
-  GS_TRY(ws_reserve(ws, 0, bytes, stream, &base));
-  Carve c{(char*)base, 0};
-  unsigned long long* hist = c.take<unsigned long long>(kSelBins + 8);
-  int64_t* ties = c.take<int64_t>(kTieCap);
-  uint8_t* keep = c.take<uint8_t>(m);
-  int64_t* cnt = c.take<int64_t>(tiles + 1);
-  int64_t* off = c.take<int64_t>(tiles + 1);
-  int64_t* tmp = c.take<int64_t>(scan_tmp_elems(tiles));
   // order statistic: the k-th smallest key T, five digits from the top
   uint64_t prefix = 0;
   int above = 53;
   int64_t rank = k - 1;  // 0-based rank of T among the keys with this prefix
   static const int kDigits[5] = {11, 11, 11, 10, 10};
-  int64_t launches = 0, tie_count = 0;
+  int64_t tie_count = 0;
   std::vector<unsigned long long> h(kSelBins);
   for (int d = 0; d < 5; ++d) {
     const int bits = kDigits[d], shift = above - bits;
     GS_CUDA(cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * kSelBins, stream));
     k_key_hist<<<grid_for(m, kThreads, 4), kThreads, 0, stream>>>(m, seed, prefix, above, shift,
                                                                    bits, hist);
-    ++launches;
+    ++*launches;
     GS_CUDA(cudaMemcpyAsync(h.data(), hist, sizeof(unsigned long long) << bits,
                             cudaMemcpyDeviceToHost, stream));
     GS_CUDA(cudaStreamSynchronize(stream));
@@ -635,7 +631,7 @@ extern "C" gs_status gs_sample_fixed(const gs_graph* gr, gs_workspace* ws, int64
       accum += (int64_t)h[b];
     }
     if (b == (1 << bits)) {
-      set_error("gs_sample_fixed: key selection lost its rank");
+      set_error("sampler key selection lost its rank");
       return GS_ECUDA;
     }
     rank -= accum;
@@ -643,18 +639,16 @@ extern "C" gs_status gs_sample_fixed(const gs_graph* gr, gs_workspace* ws, int64
     above = shift;
     tie_count = (int64_t)h[b];
   }
-  const uint64_t T = prefix;
-  // rank = how many keys equal to T come before the last one kept
   int64_t i_cut = m;  // every tie kept
   if (rank + 1 < tie_count) {
-    if (tie_count > kTieCap) {
-      set_error("gs_sample_fixed: %lld sampler keys tie at the cut", (long long)tie_count);
+    if (tie_count > tie_cap) {
+      set_error("%lld sampler keys tie at the cut", (long long)tie_count);
       return GS_ECAPACITY;
     }
     GS_CUDA(cudaMemsetAsync(hist + kSelBins, 0, sizeof(unsigned long long), stream));
-    k_key_ties<<<grid_for(m, kThreads, 4), kThreads, 0, stream>>>(m, seed, T, kTieCap, ties,
+    k_key_ties<<<grid_for(m, kThreads, 4), kThreads, 0, stream>>>(m, seed, prefix, tie_cap, ties,
                                                                    hist + kSelBins);
-    ++launches;
+    ++*launches;
     std::vector<int64_t> ht((size_t)tie_count);
     GS_CUDA(cudaMemcpyAsync(ht.data(), ties, sizeof(int64_t) * (size_t)tie_count,
                             cudaMemcpyDeviceToHost, stream));
@@ -662,7 +656,46 @@ extern "C" gs_status gs_sample_fixed(const gs_graph* gr, gs_workspace* ws, int64
     std::sort(ht.begin(), ht.end());
     i_cut = ht[(size_t)rank];
   }
-  k_fixed_flags<<<grid_for(m, kThreads, 8), kThreads, 0, stream>>>(m, seed, T, i_cut, keep);
+  *out = RankCut{prefix, i_cut};
+  return GS_OK;
+}
+
+// Edges ranked [k_lo, k_hi) by (key, i), in increasing canonical index,
+// into d_pairs (device int32[2 (k_hi - k_lo)]) or, when d_pairs is NULL,
+// into workspace slot 3 (*pairs_out).
+gs_status sample_ranks(const gs_graph* gr, gs_workspace* ws, int64_t k_lo, int64_t k_hi,
+                       uint64_t seed, int32_t* d_pairs, int32_t** pairs_out,
+                       cudaStream_t stream) {
+  const int64_t n = gr->dev.n, m = gr->m;
+  if (pairs_out) *pairs_out = d_pairs;
+  if (k_hi <= k_lo) return GS_OK;
+  constexpr int64_t kTieCap = 1 << 16;
+  const int64_t tiles = (m + kSampTile - 1) / kSampTile;
+  const size_t bytes = Carve::bytes_for<unsigned long long>(kSelBins + 8) +
+                       Carve::bytes_for<int64_t>(kTieCap) + Carve::bytes_for<uint8_t>(m) +
+                       Carve::bytes_for<int64_t>(tiles + 1) * 2 +
+                       Carve::bytes_for<int64_t>(scan_tmp_elems(tiles));
+  void* base = nullptr;
+  GS_TRY(ws_reserve(ws, 2, bytes, stream, &base));
+  Carve c{(char*)base, 0};
+  unsigned long long* hist = c.take<unsigned long long>(kSelBins + 8);
+  int64_t* ties = c.take<int64_t>(kTieCap);
+  uint8_t* keep = c.take<uint8_t>(m);
+  int64_t* cnt = c.take<int64_t>(tiles + 1);
+  int64_t* off = c.take<int64_t>(tiles + 1);
+  int64_t* tmp = c.take<int64_t>(scan_tmp_elems(tiles));
+  int64_t launches = 0;
+  RankCut lo, hi;
+  GS_TRY(rank_cut(gr, k_lo, seed, hist, ties, kTieCap, &launches, &lo, stream));
+  GS_TRY(rank_cut(gr, k_hi, seed, hist, ties, kTieCap, &launches, &hi, stream));
+  if (d_pairs == nullptr) {
+    void* b3 = nullptr;
+    GS_TRY(ws_reserve(ws, 3, Carve::bytes_for<int32_t>(2 * (k_hi - k_lo)), stream, &b3));
+    d_pairs = (int32_t*)b3;
+    if (pairs_out) *pairs_out = d_pairs;
+  }
+  k_fixed_flags<<<grid_for(m, kThreads, 8), kThreads, 0, stream>>>(m, seed, lo.T, lo.i_cut, hi.T,
+                                                                    hi.i_cut, keep);
   k_flag_count<<<(unsigned)tiles, kThreads, 0, stream>>>(keep, m, cnt);
   GS_TRY(exclusive_scan_i64(cnt, off, tiles, tmp, stream));
   k_flag_write<<<(unsigned)tiles, kThreads, 0, stream>>>(gr->dev.col, gr->up_ptr, gr->edge_off,
@@ -673,10 +706,34 @@ extern "C" gs_status gs_sample_fixed(const gs_graph* gr, gs_workspace* ws, int64
   GS_CUDA(cudaMemcpyAsync(&kept, off + tiles, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
   GS_CUDA(cudaStreamSynchronize(stream));
   ws->launches_total += launches;
-  if (kept != k) {
-    set_error("gs_sample_fixed: selected %lld edges instead of %lld", (long long)kept,
-              (long long)k);
+  if (kept != k_hi - k_lo) {
+    set_error("sampler: selected %lld edges instead of %lld", (long long)kept,
+              (long long)(k_hi - k_lo));
     return GS_ECUDA;
   }
   return GS_OK;
+}
+
+}  // namespace gs
+
+extern "C" gs_status gs_sample_fixed(const gs_graph* gr, gs_workspace* ws, int64_t k,
+                                     uint64_t seed, int32_t* d_pairs, void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (gr == nullptr || ws == nullptr || k < 0 || k > gr->m || (k > 0 && d_pairs == nullptr)) {
+    set_error("gs_sample_fixed: invalid arguments (need 0 <= k <= m and an output)");
+    return GS_EINVAL;
+  }
+  return sample_ranks(gr, ws, 0, k, seed, d_pairs, nullptr, stream);
+}
+
+extern "C" gs_status gs_sample_ranks(const gs_graph* gr, gs_workspace* ws, int64_t k_lo,
+                                     int64_t k_hi, uint64_t seed, int32_t* d_pairs,
+                                     void* stream_) {
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (gr == nullptr || ws == nullptr || k_lo < 0 || k_hi < k_lo || k_hi > gr->m ||
+      (k_hi > k_lo && d_pairs == nullptr)) {
+    set_error("gs_sample_ranks: invalid arguments (need 0 <= k_lo <= k_hi <= m and an output)");
+    return GS_EINVAL;
+  }
+  return sample_ranks(gr, ws, k_lo, k_hi, seed, d_pairs, nullptr, stream);
 }

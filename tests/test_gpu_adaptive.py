@@ -1,6 +1,7 @@
 """Algorithm 8 (adaptive estimation) on the GPU against the oracle: same
-iterations, same final fraction, same sampled edges and exact sums, and
-the same result as one count of the final (nested) sample."""
+iterations, same number of sampled edges, same exact sums, and the same
+result as one count of the fixed-size sample of that size (the samples are
+the smallest sampler keys, so the iterations nest)."""
 import math
 
 import pytest
@@ -36,8 +37,8 @@ def test_adaptive_matches_oracle(maker, beta, t_max, phi, seed):
     for gid in gs.GRAPHLETS:
         a, b = est[gid]["X"], want["est"][gid]["X"]
         assert abs(a - b) <= 1e-12 * max(abs(a), abs(b), 1.0), gid
-    # the nested sample at the final fraction counts to the same sums
-    pairs = g.sample(frac, seed)
-    assert pairs.shape[0] == sums.k
+    # the fixed-size sample of the final size counts to the same sums
+    buf = torch.empty((max(sums.k, 1), 2), dtype=torch.int32, device="cuda")
+    pairs = gs.gs_sample_fixed(g.handle, g.ws.handle, sums.k, seed, buf)
     assert g.count(pairs).sums() == got
     g.close()

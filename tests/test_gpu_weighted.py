@@ -214,3 +214,26 @@ def test_fixed_size_samples_nest_with_bernoulli_at_full_size():
     fx2 = gs.gs_sample_fixed(g.handle, g.ws.handle, k - 1000, 9, buf)
     assert torch.isin(key(fx2), kf).all()
     g.close()
+
+
+def test_rank_ranges_grow_a_sample_without_replacement():
+    """Edges ranked [k_lo, k_hi) by sampler key: consecutive ranges
+    partition the fixed-size sample of the last rank, in canonical order."""
+    rp, col = GRAPHS["chung_lu_20k"]()
+    g = gs.Graph.from_numpy(rp, col)
+    m = g.m
+    buf = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+    cuts = [0, 1, 500, 7000, 7001, m // 2]
+    parts = []
+    for lo, hi in zip(cuts, cuts[1:]):
+        parts.append(gs.gs_sample_ranks(g.handle, g.ws.handle, lo, hi, 4, buf).cpu().numpy())
+    whole = oracle.sample_fixed(rp, col, cuts[-1], 4)
+    joined = np.concatenate(parts)
+    joined = joined[np.lexsort((joined[:, 1], joined[:, 0]))]
+    assert np.array_equal(joined, whole)
+    for (lo, hi), p in zip(zip(cuts, cuts[1:]), parts):
+        assert len(p) == hi - lo
+        want_hi = {tuple(x) for x in oracle.sample_fixed(rp, col, hi, 4).tolist()}
+        want_lo = {tuple(x) for x in oracle.sample_fixed(rp, col, lo, 4).tolist()}
+        assert {tuple(x) for x in p.tolist()} == want_hi - want_lo
+    g.close()

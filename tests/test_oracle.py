@@ -380,22 +380,24 @@ def test_disconnected_unbiased_over_seeds():
 # ------------------------------------------------------------------ Algorithm 8 (adaptive)
 
 def test_adaptive_with_zero_beta_runs_t_max_halving_phi():
+    """beta = 0 runs t_max iterations; iteration t draws ceil(phi_t (M - |J|))
+    new edges with phi halving after each draw."""
     rp, col = synth.er_2000()
+    m = len(col) // 2
     r = oracle.adaptive_estimate(rp, col, 0.0, 6, 0.05, 3)
     assert r["iters"] == 6
-    p, phi = 0.0, 0.05
+    J, phi = 0, 0.05
     for _ in range(6):
-        p, phi = p + phi * (1.0 - p), phi / 2
-    assert r["p"] == p
+        J, phi = min(m, J + math.ceil(phi * (m - J))), phi / 2
+    assert r["K"] == J and r["p"] == J / m
 
 
-def test_adaptive_result_is_the_nested_sample_and_larger_beta_stops_no_later():
+def test_adaptive_result_is_the_fixed_size_sample_and_larger_beta_stops_no_later():
     rp, col = synth.chung_lu(3000, 20000, 2.1, 300.0, seed=8)
     prev_iters = None
     for beta in (0.001, 0.01, 0.1):
         r = oracle.adaptive_estimate(rp, col, beta, 10, 0.02, 5)
-        pairs = oracle.sample(rp, col, r["p"], 5)
-        assert r["K"] == len(pairs)
+        pairs = oracle.sample_fixed(rp, col, r["K"], 5)
         s, s2 = oracle.numerators(oracle.local_counts(rp, col, pairs))
         assert s == r["sums"] and s2 == r["sq"]
         if prev_iters is not None:
@@ -448,34 +450,27 @@ def _closed_form_graph(kind):
 
 @pytest.mark.parametrize("kind", ["cycle30", "K12", "K4_6"])
 @pytest.mark.parametrize("beta", [0.0, 0.25])
-def test_adaptive_stops_one_iteration_after_the_first_estimate_on_edge_transitive_graphs(
-        kind, beta):
+def test_adaptive_stops_at_the_second_iteration_on_edge_transitive_graphs(kind, beta):
     """Every edge of an edge-transitive graph has the same (t, a, b, k, q), so
     any non-empty sample estimates every count exactly (sigma K N / D = M N /
-    D): the estimate is the closed form from the first non-empty iteration
-    on, the next iteration changes nothing (loss 0 <= beta, also beta = 0)
-    and the loop stops there."""
+    D): the first iteration (at least one edge) already gives the closed
+    form, the second changes nothing (loss 0 <= beta, also beta = 0) and the
+    loop stops there."""
     rp, col, closed = _closed_form_graph(kind)
     m = len(col) // 2
     for seed in (1, 2, 3):
         r = oracle.adaptive_estimate(rp, col, beta, 20, 0.3, seed)
-        # iteration of the first non-empty sample, from the fractions of the
-        # schedule p_t = p_{t-1} + phi_t (1 - p_{t-1}), phi_t = 0.3 / 2^(t-1)
-        p, phi, first = 0.0, 0.3, None
-        for t in range(1, 21):
-            p = p + phi * (1.0 - p)
-            phi /= 2
-            if first is None and len(oracle.sample(rp, col, p, seed)) > 0:
-                first = t
-                break
-        assert r["iters"] == first + 1, (kind, seed, r["iters"], first)
+        assert r["iters"] == 2, (kind, seed, r["iters"])
         for g in oracle.GRAPHLETS:
             assert r["est"][g]["X"] == float(closed.get(g, 0)), (kind, g)
-        assert 0 < r["K"] <= m
+        k1 = math.ceil(0.3 * m)
+        assert r["K"] == min(m, k1 + math.ceil(0.15 * (m - k1)))
 
 
 def test_adaptive_loss_sequence_on_a_two_class_graph():
-    """30 copies of K4 and 2 of the path P3, seed 11, beta 0.02, phi 0.1.
+    """30 copies of K4 and 2 of the path P3, seed 11, beta 0.02, phi 0.1;
+    iteration t adds the next ceil(phi_t (M - |J|)) edges in sampler-key
+    order.
     Per-edge numerators by hand: a K4 edge has t = 2, a = b = 0, k = 1, so
     N3 = 2, N7 = 1 and every other N is 0; a P3 edge has t = 0, a + b = 1, so
     N4 = 1 and every 4-node N is 0. With n_K, n_P edges of each kind in the
@@ -491,21 +486,25 @@ def test_adaptive_loss_sequence_on_a_two_class_graph():
     assert m == 184
     k4_end = ends[0][1]
 
+    up = synth.upper_pairs(rp, col)
+
     def replay(rule, beta=0.02, phi=0.1, seed=11, t_max=12):
-        p, t, loss, hist = 0.0, 0, 1.0, []
+        keys = oracle.sample_keys(rp, col, seed)
+        order = np.lexsort((np.arange(m), keys))
+        J, t, loss, hist = 0, 0, 1.0, []
         while loss > beta and t < t_max:
-            p_new = p + phi * (1.0 - p)
-            u = oracle.sample(rp, col, p_new, seed)[:, 0]
+            J = min(m, J + math.ceil(phi * (m - J)))
+            u = up[np.sort(order[:J])][:, 0]
             nk, npath = int((u < k4_end).sum()), int((u >= k4_end).sum())
             k = nk + npath
-            x = {3: m * 2 * nk / (3 * k), 4: m * npath / (2 * k), 7: m * nk / (6 * k)} if k else None
+            x = {3: m * 2 * nk / (3 * k), 4: m * npath / (2 * k), 7: m * nk / (6 * k)}
             ref = hist[-2] if rule == "t-2" and len(hist) >= 2 else (hist[-1] if hist else None)
             if ref is None:
                 loss = 1.0
-            elif x is not None:
-                keys = (3, 4, 7) if rule == "all" else (7,)
+            else:
+                keys_ = (3, 4, 7) if rule == "all" else (7,)
                 changes = []
-                for g in keys:
+                for g in keys_:
                     if x[g] == ref[g]:
                         changes.append(0.0)
                     elif ref[g] == 0:
@@ -514,17 +513,16 @@ def test_adaptive_loss_sequence_on_a_two_class_graph():
                         d = abs(x[g] - ref[g])
                         changes.append(d if rule == "abs" else d / abs(ref[g]))
                 loss = max(changes)
-            if x is not None:
-                hist.append(x)
-            p, phi, t = p_new, phi / 2, t + 1
-        return t, p
+            hist.append(x)
+            phi, t = phi / 2, t + 1
+        return t, J
 
     want = replay("paper")
     assert want[0] == 3
     for other in ("all", "abs", "t-2"):
         assert replay(other)[0] != want[0], other
     r = oracle.adaptive_estimate(rp, col, 0.02, 12, 0.1, 11)
-    assert (r["iters"], r["p"]) == want
+    assert (r["iters"], r["K"]) == want
 
 
 def test_adaptive_loss_helpers():
