@@ -421,62 +421,79 @@ def _oracle_worker_chunk(job):
     return oracle.numerators(lc)
 
 
-def oracle_part_rates(rp, col, parts, seconds: float, seed: int = 1, workers: int | None = None):
+class OraclePool:
+    """One spawned process per host core, each holding the CSR through
+    memory-mapped .npy files (written once)."""
+
+    def __init__(self, rp, col, workers=None):
+        import multiprocessing as mp
+        import tempfile
+
+        import numpy as np
+        self.workers = workers or os.cpu_count() or 1
+        self.tmp = tempfile.mkdtemp(prefix="gs_oracle_")
+        self.paths = (os.path.join(self.tmp, "rp.npy"), os.path.join(self.tmp, "col.npy"))
+        np.save(self.paths[0], rp)
+        np.save(self.paths[1], col)
+        self.pool = mp.get_context("spawn").Pool(self.workers, _oracle_worker_init, self.paths)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for f in self.paths:
+            os.remove(f)
+        os.rmdir(self.tmp)
+
+
+def oracle_part_rates(rp, col, parts, seconds: float, seed: int = 1, workers: int | None = None,
+                      pool: OraclePool | None = None):
     """The CPU oracle, unchanged, run by one spawned process per host core
     over disjoint chunks of each part's edges (the first edges of a seeded
     sample at that part's fraction; all edges in canonical order for the
     exact part): each part gets `seconds` / len(parts) of wall time, sized
     by a single-core calibration pass. Returns ({label: (edges, wall s)},
     cores)."""
-    import multiprocessing as mp
-    import tempfile
-
-    import numpy as np
     import oracle
     import synth
-    workers = workers or os.cpu_count() or 1
+    own = pool is None
+    if own:
+        pool = OraclePool(rp, col, workers)
     budget = seconds / max(len(parts), 1)
-    tmp = tempfile.mkdtemp(prefix="gs_oracle_")
-    rp_path, col_path = os.path.join(tmp, "rp.npy"), os.path.join(tmp, "col.npy")
-    np.save(rp_path, rp)
-    np.save(col_path, col)
     rates = {}
     try:
-        with mp.get_context("spawn").Pool(workers, _oracle_worker_init, (rp_path, col_path)) as pool:
-            for label, f, mask in parts:
-                four = bool(mask & ~THREE)
-                if f >= 1.0:
-                    pairs = synth.upper_pairs(rp, col)[: max(1, 400_000 * workers)]
-                else:
-                    pairs = oracle.sample(rp, col, f, seed)
-                # single-core calibration
-                n, used, done = 16, 0.0, 0
-                while done < len(pairs) and used < max(0.3, budget / 8):
-                    t0 = time.process_time()
-                    oracle.numerators(oracle.local_counts(rp, col, pairs[done:done + n], four=four))
-                    used += time.process_time() - t0
-                    done += n
-                    n = min(2 * n, 65536)
-                per_core = max(16, int(done / max(used, 1e-6) * budget))
-                total = min(len(pairs), per_core * workers)
-                step = max(1, total // (4 * workers))
-                jobs = [(pairs[i:i + step], four) for i in range(0, total, step)]
-                pool.map(_oracle_worker_chunk, [(pairs[:workers], four)], chunksize=1)
-                t0 = time.perf_counter()
-                pool.map(_oracle_worker_chunk, jobs, chunksize=1)
-                rates[label] = (total, time.perf_counter() - t0)
+        for label, f, mask in parts:
+            four = bool(mask & ~THREE)
+            if f >= 1.0:
+                pairs = synth.upper_pairs(rp, col)[: max(1, 400_000 * pool.workers)]
+            else:
+                pairs = oracle.sample(rp, col, f, seed)
+            # single-core calibration
+            n, used, done = 16, 0.0, 0
+            while done < len(pairs) and used < max(0.3, budget / 8):
+                t0 = time.process_time()
+                oracle.numerators(oracle.local_counts(rp, col, pairs[done:done + n], four=four))
+                used += time.process_time() - t0
+                done += n
+                n = min(2 * n, 65536)
+            per_core = max(16, int(done / max(used, 1e-6) * budget))
+            total = min(len(pairs), per_core * pool.workers)
+            step = max(1, total // (4 * pool.workers))
+            jobs = [(pairs[i:i + step], four) for i in range(0, total, step)]
+            pool.pool.map(_oracle_worker_chunk, [(pairs[:pool.workers], four)], chunksize=1)
+            t0 = time.perf_counter()
+            pool.pool.map(_oracle_worker_chunk, jobs, chunksize=1)
+            rates[label] = (total, time.perf_counter() - t0)
     finally:
-        for f in (rp_path, col_path):
-            os.remove(f)
-        os.rmdir(tmp)
-    return rates, workers
+        if own:
+            pool.close()
+    return rates, pool.workers
 
 
-def oracle_step_rate(rp, col, parts, seconds, seed=1):
+def oracle_step_rate(rp, col, parts, seconds, seed=1, pool=None):
     """Edges/s of the oracle on one whole step of the workload: each part's
     measured per-edge rate applied to that part's full edge count."""
     m = len(col) // 2
-    rates, cores = oracle_part_rates(rp, col, parts, seconds, seed)
+    rates, cores = oracle_part_rates(rp, col, parts, seconds, seed, pool=pool)
     step_edges = sum(m if f >= 1.0 else f * m for _, f, _ in parts)
     step_secs = sum((m if f >= 1.0 else f * m) * rates[label][1] / max(rates[label][0], 1)
                     for label, f, _ in parts)
@@ -493,11 +510,16 @@ def run_reference(args, rank, world):
     rp, col = generate(name)
     budget = max(6.0, min(45.0, 150.0 / max(args.steps + args.warmup, 1)))
     values, walls, cores, sample = [], 0.0, 1, ""
-    for step in range(args.warmup + args.steps):
-        v, cores, sample, wall = oracle_step_rate(rp, col, parts, budget, seed=1 + step)
-        if step >= args.warmup:
-            values.append(v)
-            walls += wall
+    pool = OraclePool(rp, col)
+    try:
+        for step in range(args.warmup + args.steps):
+            v, cores, sample, wall = oracle_step_rate(rp, col, parts, budget, seed=1 + step,
+                                                      pool=pool)
+            if step >= args.warmup:
+                values.append(v)
+                walls += wall
+    finally:
+        pool.close()
     value = statistics.median(values)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
@@ -592,7 +614,7 @@ def run_serve_bench(args):
     the offered rate). The capacity of one launch per request (requests run
     one by one with gs_count_estimate) is measured first; then open-loop
     Poisson streams at 30%, 60% and 90% of it, and at the offered 2000
-    req/s, run through the server (40 GB budget, 2 lanes) and through one
+    req/s, run through the server (40 GB budget, 4 lanes) and through one
     launch per request on the same GPU, with identical results required."""
     import numpy as np
     import torch
@@ -628,7 +650,7 @@ def run_serve_bench(args):
             masks.append(sum(1 << b for b in bits))
         return [(int(gidx[i]), float(frac[i]), int(seeds[i]), masks[i]) for i in range(n_req)]
 
-    srv = gs.Server(hbm_budget_bytes=40 << 30, max_batch=64, lanes=2)
+    srv = gs.Server(hbm_budget_bytes=40 << 30, max_batch=64, lanes=4)
     ids = [srv.add_numpy(rp, col) for rp, col in graphs]
     t0 = time.time()
     srv.start()
@@ -715,7 +737,7 @@ def run_serve_bench(args):
         "config": {"workload": "serve: 8 resident graphs (ER 2000 x2, Chung-Lu 100k x2, Chung-Lu "
                                "1M x2, R-MAT 24 x2), Poisson arrivals, fractions log-uniform "
                                "[0.1%, 10%], random masks (3-node only on R-MAT)",
-                   "budget_gb": 40, "lanes": 2, "generation_s": round(gen_s, 1),
+                   "budget_gb": 40, "lanes": 4, "generation_s": round(gen_s, 1),
                    "start_s": round(start_s, 2)},
         "capacity_one_launch_per_request_req_s": round(capacity, 2),
         "capacity_server_req_s": round(n_cap / smk, 2),

@@ -41,7 +41,11 @@ __device__ __forceinline__ void raise_error(DevError* err, int32_t code, int64_t
 
 // The hub-pair bit matrix covers at most this many vertices (2^14 squared
 // bits = 32 MiB, which stays resident in the 129 MB L2).
-constexpr int64_t kHubMatrixMax = 16384;
+#ifndef GS_HUB_MATRIX_MAX
+#define GS_HUB_MATRIX_MAX 16384
+#endif
+constexpr int64_t kHubMatrixMax = GS_HUB_MATRIX_MAX;
+static_assert(kHubMatrixMax <= 32767, "matrix slots are stored in 16 bits");
 
 // Device view of a registered graph plus its hub index.
 struct DevGraph {

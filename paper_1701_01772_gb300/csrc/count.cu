@@ -70,7 +70,7 @@ constexpr int kDenseBlocksPerSm = 6;
 // several units so that small samples still fill the GPU).
 constexpr int64_t kDenseUnit = 4 * kThreads;
 // Matrix rows are at most this many 128-bit groups.
-constexpr int kHubMatrixMaxGroups = (int)(kHubMatrixMax / 128);
+constexpr int kHubMatrixMaxGroups = (int)((kHubMatrixMax + 127) / 128);
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {

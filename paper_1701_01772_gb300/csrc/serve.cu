@@ -5,7 +5,10 @@
 // slow every other one down). Worker lanes (host threads, each with its own
 // CUDA stream and workspace) take queued requests in arrival order while the
 // batch's estimated device memory fits the server budget next to what the
-// other lanes hold; the estimate stays reserved until the batch finishes.
+// other lanes hold (the estimate stays reserved until the batch finishes)
+// and while the requests are of like estimated length (seconds per sampled
+// edge of each graph and mask class, learnt from the groups counted so
+// far), so that a short request is not held behind a long one.
 // A batch is counted graph by graph: all its requests on one graph are
 // sampled (the same sampler and seeds as gs_sample), concatenated and
 // counted in one pass whose fold sums each request's edges separately.
@@ -72,6 +75,7 @@ struct Req {
   uint64_t ticket;
   double t_submit, t_start, t_done;
   int64_t est_bytes;
+  double est_s;  // estimated service time (admission)
   int64_t k;
   int64_t batch_size;
   gs_status status;
@@ -90,6 +94,9 @@ struct gs_server {
   std::vector<gs_graph*> graphs;  // one registration (and hub index) per graph
   std::vector<int64_t> m;
   std::vector<double> bytes_per_edge;
+  // running service time per sampled edge, per graph and mask class (3-node
+  // only, or with 4-node graphlets), learnt from the groups counted so far
+  std::vector<double> sec_per_edge[2];
   // queue
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -107,6 +114,8 @@ struct gs_server {
 namespace {
 
 double now_s();
+// Batches of requests estimated shorter than this together are not split.
+constexpr double kBatchFloorSeconds = 0.002;
 
 // Marks a finished group's requests done (results are final) and wakes the
 // waiters, so a group does not wait for the rest of its batch.
@@ -169,10 +178,19 @@ gs_status process_group(gs_server* s, gs_workspace* ws, cudaStream_t stream, siz
   std::vector<unsigned long long> h((size_t)nb * 32, 0);
   if (K > 0) {
     CountBufs b;
-    GS_TRY(count_run(gr, ws, *pair_buf, K, mask, false, nullptr, *seg_dev, nb,
-                     ws->has_tuning ? ws->tuning : default_tuning(), b, stream, "gs_server"));
-    GS_CUDA(cudaMemcpyAsync(h.data(), b.seg_sums, sizeof(unsigned long long) * nb * 32,
-                            cudaMemcpyDeviceToHost, stream));
+    const Tuning tu = ws->has_tuning ? ws->tuning : default_tuning();
+    if (nb == 1) {
+      // a request alone: the plain fold (one sum, no per-request segments)
+      GS_TRY(count_run(gr, ws, *pair_buf, K, mask, false, nullptr, nullptr, 0, tu, b, stream,
+                       "gs_server"));
+      GS_CUDA(cudaMemcpyAsync(h.data(), b.sums, sizeof(unsigned long long) * 32,
+                              cudaMemcpyDeviceToHost, stream));
+    } else {
+      GS_TRY(count_run(gr, ws, *pair_buf, K, mask, false, nullptr, *seg_dev, nb, tu, b, stream,
+                       "gs_server"));
+      GS_CUDA(cudaMemcpyAsync(h.data(), b.seg_sums, sizeof(unsigned long long) * nb * 32,
+                              cudaMemcpyDeviceToHost, stream));
+    }
   }
   GS_CUDA(cudaStreamSynchronize(stream));
   for (int64_t i = 0; i < nb; ++i) {
@@ -186,6 +204,10 @@ gs_status process_group(gs_server* s, gs_workspace* ws, cudaStream_t stream, siz
     q->status = gs_estimate(&sums, q->r.z, &q->res);
   }
   return GS_OK;
+}
+
+int mask_class(uint32_t mask) {
+  return (mask & (GS_G7 | GS_G8 | GS_G9 | GS_G10 | GS_G11 | GS_G12)) != 0 ? 1 : 0;
 }
 
 // Runs a batch graph group by graph group (smallest estimated groups first)
@@ -205,8 +227,27 @@ gs_status run_batch(gs_server* s, gs_workspace* ws, cudaStream_t stream, std::ve
     if (!groups[gi].empty()) order.push_back(gi);
   std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return est[a] < est[b]; });
   for (size_t k = 0; k < order.size(); ++k) {
+    const double tg = now_s();
     gs_status st = process_group(s, ws, stream, order[k], groups[order[k]], pair_buf, pair_cap,
                                  seg_dev, seg_cap);
+    if (st == GS_OK) {
+      // learn the seconds per sampled edge of the classes in this group
+      int64_t K = 0;
+      bool c[2] = {false, false};
+      for (Req* q : groups[order[k]]) {
+        K += q->k;
+        c[mask_class(q->r.mask)] = true;
+      }
+      if (K > 0) {
+        const double r = (now_s() - tg) / (double)K;
+        std::lock_guard<std::mutex> lock(s->mu);
+        for (int ci = 0; ci < 2; ++ci) {
+          if (!c[ci]) continue;
+          double& x = s->sec_per_edge[ci][order[k]];
+          x = x > 0.0 ? 0.7 * x + 0.3 * r : r;
+        }
+      }
+    }
     if (st != GS_OK) {
       for (size_t r = k; r < order.size(); ++r)
         batch.insert(batch.end(), groups[order[r]].begin(), groups[order[r]].end());
@@ -235,10 +276,21 @@ void lane_main(gs_server* s) {
       s->cv_work.wait(lock, [&] { return s->stopping || !s->pending.empty(); });
       if (s->stopping) break;
       // admit FIFO while the estimate fits the budget next to other lanes
+      // and the requests are of like length: a request joins the batch only
+      // while the batch's estimated time stays within twice the first
+      // request's (or a few milliseconds), so a short request is not held
+      // behind a long pass of the same batch
+      double t_head = 0.0, t_batch = 0.0;
       while (!s->pending.empty() && (int)batch.size() < s->max_batch) {
         Req* q = s->pending.front();
         const bool alone = batch.empty() && s->reserved == 0;
         if (!alone && s->reserved + est + (uint64_t)q->est_bytes > s->budget) break;
+        const double tq = s->sec_per_edge[mask_class(q->r.mask)][q->r.graph] *
+                          q->r.fraction * (double)s->m[q->r.graph];
+        if (!batch.empty() && t_batch + tq > std::max(2.0 * t_head, kBatchFloorSeconds)) break;
+        if (batch.empty()) t_head = tq;
+        t_batch += tq;
+        q->est_s = tq;
         s->pending.pop_front();
         batch.push_back(q);
         est += q->est_bytes;
@@ -346,6 +398,8 @@ extern "C" gs_status gs_server_start(gs_server* s, uint32_t flags, uint64_t hub_
     // T-bit / cost / task words (20/32 B) and a T entry allowance (1 B)
     const double pp = gr->m > 0 ? (double)pos / (double)gr->m : 0.0;
     s->bytes_per_edge.push_back(120.0 + 1.625 * pp);
+    s->sec_per_edge[0].push_back(0.0);  // learnt from the first groups counted
+    s->sec_per_edge[1].push_back(0.0);
   }
   cudaFree(d_pos);
   s->started = true;
