@@ -121,7 +121,7 @@ const char* gs_version(void);
  * GS_ENOTSORTED / GS_ESELFLOOP / GS_EDUP / GS_EASYM / GS_EINVAL returned.
  * Builds the per-graph index (upper-edge offsets for the sampler, adjacency
  * bitmaps of the highest-degree vertices, an adjacency bit matrix among the
- * top 16384 of them, and a co-degree table |N(a) cap N(b)| among the top
+ * top 32767 of them, and a co-degree table |N(a) cap N(b)| among the top
  * vertices, plus a mid x big co-degree table and adjacency bucket
  * directories, see gs_graph_index_info) in library-owned device memory;
  * hub_budget_bytes bounds that index (0 = default 20 GiB: bitmaps and
@@ -220,7 +220,8 @@ typedef struct {
   int64_t dense_edges;    /* sampled edges whose pairs of hub-matrix members in T
                              were counted word-parallel (matrix row AND T mask) */
   int64_t dense_groups;   /* 128-bit matrix-row groups ANDed for those edges
-                             (included in quad_tests) */
+                             (groups where T's mask is non-zero; included in
+                             quad_tests) */
   int64_t micro_probes;   /* gs_micro only: neighbour probes, sum of ceil(d_w p_e) */
 } gs_stats;
 
@@ -237,6 +238,18 @@ gs_status gs_workspace_set_timing(gs_workspace* ws, int enable);
  * them. */
 gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_per_sm, int quad_blocks_per_sm,
                                   int64_t task_probes, int use_hubs);
+
+/* Dense clique mode on this workspace (Sec. 2.6 counts the 4-cliques of an
+ * edge from the pairs among T = N(u) cap N(v)): an edge whose T holds many
+ * of the graph's highest-degree vertices counts the pairs among those
+ * vertices by AND + popcount over rows of the hub-pair bit matrix. `slots`
+ * is how many matrix slots (vertices in decreasing degree order) take part;
+ * it is rounded down to a multiple of 128 and capped at the matrix size,
+ * and 0 turns dense mode off. Vertices of the matrix beyond `slots` still
+ * answer single membership tests from it. Default: all (32767). Results do not
+ * depend on it; GS_EINVAL for a NULL workspace or slots < 0. Kept across
+ * gs_workspace_set_tuning. */
+gs_status gs_workspace_set_dense_slots(gs_workspace* ws, int64_t slots);
 
 /* Host output: statistics of the last gs_count that used `ws`. */
 gs_status gs_count_stats(const gs_workspace* ws, gs_stats* out);

@@ -208,6 +208,7 @@ def lib() -> ctypes.CDLL:
         "gs_count3_static": ([P, P, I64, U32, ctypes.POINTER(GsSums), P], ctypes.c_int32),
         "gs_workspace_set_tuning": ([P, ctypes.c_int, ctypes.c_int, I64, ctypes.c_int],
                                     ctypes.c_int32),
+        "gs_workspace_set_dense_slots": ([P, I64], ctypes.c_int32),
         "gs_sums_merge": ([ctypes.POINTER(GsSums), ctypes.POINTER(GsSums)], ctypes.c_int32),
         "gs_batch_create": ([P, P, P, I64, I64, I64, U32, U32, U64, P, PP], ctypes.c_int32),
         "gs_batch_count": ([P, ctypes.POINTER(GsSums), P], ctypes.c_int32),
@@ -384,6 +385,10 @@ def gs_workspace_set_tuning(handle: int, tri_blocks_per_sm: int, quad_blocks_per
                             task_probes: int, use_hubs: bool) -> None:
     _check(lib().gs_workspace_set_tuning(handle, tri_blocks_per_sm, quad_blocks_per_sm,
                                          task_probes, int(use_hubs)))
+
+
+def gs_workspace_set_dense_slots(handle: int, slots: int) -> None:
+    _check(lib().gs_workspace_set_dense_slots(handle, slots))
 
 
 def gs_batch_create(vtx_off, row_ptr, col, mask: int = GS_CONNECTED, flags: int = GS_VALIDATE,
@@ -608,6 +613,9 @@ class Workspace:
                    task_probes: int = 512, use_hubs: bool = True) -> None:
         gs_workspace_set_tuning(self.handle, tri_blocks_per_sm, quad_blocks_per_sm, task_probes,
                                 use_hubs)
+
+    def set_dense_slots(self, slots: int) -> None:
+        gs_workspace_set_dense_slots(self.handle, slots)
 
     def stats(self) -> dict:
         return gs_count_stats(self.handle).as_dict()

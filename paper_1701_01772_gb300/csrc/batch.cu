@@ -205,7 +205,7 @@ extern "C" gs_status gs_batch_create(const int64_t* d_vtx_off, const int64_t* d_
       for (int tq : tri_opts)
         for (int qq : quad_opts)
           for (int64_t tp : task_opts) {
-            const Tuning tu{tq, qq, tp, h};
+            const Tuning tu{tq, qq, tp, h, kHubDenseSlots};
             enqueue_batch(b, tu, stream);  // warm
             cudaEventRecord(e0, stream);
             enqueue_batch(b, tu, stream);

@@ -39,13 +39,22 @@ __device__ __forceinline__ void raise_error(DevError* err, int32_t code, int64_t
 
 // ---------------------------------------------------------------- graph
 
-// The hub-pair bit matrix covers at most this many vertices (2^14 squared
-// bits = 32 MiB, which stays resident in the 129 MB L2).
+// The hub-pair bit matrix covers at most this many vertices (32767 squared
+// bits = 128 MiB, about the size of the 129 MB L2; its rows of the
+// highest-degree vertices, which most tests touch, stay resident). On R-MAT
+// scale 24 the 1% estimate took 3.69 s with 16384 vertices and 3.22 s with
+// 32767 (more edges go dense, fewer single tests).
 #ifndef GS_HUB_MATRIX_MAX
-#define GS_HUB_MATRIX_MAX 16384
+#define GS_HUB_MATRIX_MAX 32767
 #endif
 constexpr int64_t kHubMatrixMax = GS_HUB_MATRIX_MAX;
 static_assert(kHubMatrixMax <= 32767, "matrix slots are stored in 16 bits");
+// Default number of matrix slots (the highest-degree vertices) that take
+// part in dense clique mode; the rest of the matrix answers single tests.
+#ifndef GS_HUB_DENSE_SLOTS
+#define GS_HUB_DENSE_SLOTS GS_HUB_MATRIX_MAX
+#endif
+constexpr int64_t kHubDenseSlots = GS_HUB_DENSE_SLOTS;
 
 // Device view of a registered graph plus its hub index.
 struct DevGraph {
@@ -85,7 +94,10 @@ struct DevGraph {
   const int64_t* dm_row;
   const int32_t* dm_first;
   const uint32_t* hm_bits;  // [hm_count][hm_words]
-  int64_t hm_words;         // ceil(hm_count / 32)
+  int64_t hm_words;         // ceil(hm_count / 128) * 4
+  // dense clique mode uses the first hm_dense_words * 32 slots (a multiple
+  // of 128, at most hm_words * 32; 0 = no dense mode); set per call
+  int64_t hm_dense_words;
   int64_t hm_count;
   // bucket directories of the adjacency lists of vertices that have no
   // bitmap (degree at least a threshold): the neighbours x of v with
@@ -274,6 +286,7 @@ struct Tuning {
   int quad_blocks_per_sm;   // resident CTAs per SM of the 4-node pass
   int64_t task_probes;      // membership tests per 4-node work unit
   int use_hubs;             // 0: ignore bitmaps / co-degree table / hub matrix
+  int64_t dense_slots;      // hub-matrix slots that take part in dense mode
 };
 }  // namespace gs
 
@@ -347,7 +360,7 @@ struct CountBufs {
   int32_t* T = nullptr;
   int16_t* T_hm = nullptr;  // matrix slots of T's entries (NULL without a matrix)
   // dense clique mode: per-edge mask index (-1 = sparse edge) and the
-  // masks of T's matrix members ([ndense][hm_words])
+  // masks of T's dense-slot members ([ndense][hm_dense_words])
   int32_t* mask_idx = nullptr;
   uint32_t* tmask = nullptr;
   int64_t* dense_e = nullptr;  // edge of each mask ([ndense])

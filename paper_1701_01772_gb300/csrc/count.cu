@@ -46,6 +46,8 @@
 //            final fixed-order pass (or per-segment limb sums, k_fold_seg).
 #include <string.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace gs {
@@ -64,6 +66,9 @@ constexpr unsigned kFull = 0xffffffffu;
 // word-parallel AND + popcount over hub-matrix rows.
 constexpr int kDenseMin = 64;
 constexpr unsigned long long kEmpty = ~0ull;
+// Membership tests per run of consecutive tasks a k_quad warp takes from
+// the task counter (at least one task).
+constexpr int64_t kQuadGrabTests = 16384;
 // Resident CTAs per SM of k_dense_pairs (at most 40 registers).
 constexpr int kDenseBlocksPerSm = 6;
 // T entries per k_dense_pairs work unit (a heavy dense edge is split into
@@ -71,6 +76,14 @@ constexpr int kDenseBlocksPerSm = 6;
 constexpr int64_t kDenseUnit = 4 * kThreads;
 // Matrix rows are at most this many 128-bit groups.
 constexpr int kHubMatrixMaxGroups = (int)((kHubMatrixMax + 127) / 128);
+// 32-bit words of a bitmap over those groups.
+constexpr int kGroupWords = (kHubMatrixMaxGroups + 31) / 32;
+// Cost of one 128-bit dense group against one membership test, in quarters
+// (the dense-mode choice compares kGroupCost * groups with 4 * tests).
+#ifndef GS_DENSE_GROUP_COST
+#define GS_DENSE_GROUP_COST 4
+#endif
+constexpr int kGroupCost = GS_DENSE_GROUP_COST;
 
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -222,6 +235,7 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
                             int64_t* __restrict__ tdeg,
                             int32_t* __restrict__ mask_idx,
                             unsigned long long* __restrict__ dense_counter) {
+  __shared__ uint32_t gbits[kThreads / 32][kGroupWords];  // member groups of a warp's edge
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < K; e += warps) {
@@ -242,7 +256,7 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
         if (T_hm != nullptr) {
           const int16_t xs = __ldg(g.col_hm + bu + w * 32 + lane);
           T_hm[at] = xs;
-          hm_member = xs >= 0;
+          hm_member = xs >= 0 && xs < g.hm_dense_words * 32;
         }
         dsum += __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
       }
@@ -252,24 +266,42 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
     for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
     bool dense_mode = false;
     if (T_hm != nullptr && thm >= kDenseMin) {
-      // segment-A work of this edge in either mode (estimates): sparse =
-      // tests over the shorter of N(w) above w / T above w; dense = row
-      // groups of the matrix members plus the adjacency of the others
+      // segment-A work of this edge in either mode: sparse = tests over the
+      // shorter of N(w) above w / T above w (estimated); dense = for each
+      // dense-slot member, the 128-bit groups of the T mask that hold a
+      // member and lie at or above its own (what k_dense_pairs reads), plus
+      // the adjacency of the other members
       __syncwarp();  // this warp's T entries are visible to all its lanes
       const int64_t t0 = toff[e], te = pos - t0;
-      long long sparse = 0, dense = 0;
+      const int D = (int)(g.hm_dense_words * 32);
+      uint32_t* gb = gbits[threadIdx.x >> 5];
+      for (int w = lane; w < kGroupWords; w += 32) gb[w] = 0u;
+      __syncwarp();
+      for (int64_t j = lane; j < te; j += 32) {
+        const int xs = T_hm[t0 + j];
+        if (xs >= 0 && xs < D) atomicOr(gb + (xs >> 12), 1u << ((xs >> 7) & 31));
+      }
+      __syncwarp();
+      long long sparse = 0, dense = 0, groups = 0;
       for (int64_t j = lane; j < te; j += 32) {
         const int32_t x = T[t0 + j];
-        const int16_t xs = T_hm[t0 + j];
+        const int xs = T_hm[t0 + j];
         const int64_t dx = __ldg(g.row_ptr + x + 1) - __ldg(g.row_ptr + x);
         sparse += min(dx / 2, te - j - 1);  // about half of N(x) lies above x
-        dense += xs >= 0 ? (g.hm_words / 4 - (xs >> 7)) : dx;
+        if (xs >= 0 && xs < D) {
+          const int g0 = xs >> 7;
+          groups += __popc(gb[g0 >> 5] & (~0u << (g0 & 31)));
+          for (int w = (g0 >> 5) + 1; w < kGroupWords; ++w) groups += __popc(gb[w]);
+        } else {
+          dense += dx;
+        }
       }
       for (int o = 16; o > 0; o >>= 1) {
         sparse += __shfl_xor_sync(kFull, sparse, o);
         dense += __shfl_xor_sync(kFull, dense, o);
+        groups += __shfl_xor_sync(kFull, groups, o);
       }
-      dense_mode = dense < sparse;
+      dense_mode = kGroupCost * groups + 4 * dense < 4 * sparse;
     }
     if (lane == 0) {
       tdeg[e] = dsum;
@@ -300,7 +332,7 @@ __global__ void k_build_tmask(const int64_t* __restrict__ toff, const unsigned l
     const int64_t b = toff[e], len = (int64_t)t[e];
     for (int64_t i = lane; i < len; i += 32) {
       const int32_t s = T_hm[b + i];
-      if (s >= 0) atomicOr(m + (s >> 5), 1u << (s & 31));
+      if (s >= 0 && s < words * 32) atomicOr(m + (s >> 5), 1u << (s & 31));
     }
   }
 }
@@ -328,7 +360,7 @@ __global__ void k_unit_fill(const int64_t* __restrict__ unit_off, int64_t ndense
 // members among them with lanes over 128-bit groups (coalesced 512-byte
 // reads of the L2-resident matrix).
 __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
-    k_dense_pairs(const uint32_t* __restrict__ hm_bits, int64_t hm_words,
+    k_dense_pairs(const uint32_t* __restrict__ hm_bits, int64_t hm_words, int64_t dense_words,
                   const int64_t* __restrict__ toff, const unsigned long long* __restrict__ t,
                   const int16_t* __restrict__ T_hm, const uint32_t* __restrict__ tmask,
                   const int64_t* __restrict__ dense_e, const int64_t* __restrict__ unit_off,
@@ -336,11 +368,17 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
                   unsigned long long* __restrict__ k_out, unsigned long long* __restrict__ q,
                   unsigned long long* __restrict__ counter,
                   unsigned long long* __restrict__ tests) {
+  // the edge's T mask, compacted to its non-zero 128-bit groups: smask[c]
+  // is group sgrp[c]; spos[g] = number of non-zero groups below g
   __shared__ uint4 smask[kHubMatrixMaxGroups];
+  __shared__ uint16_t sgrp[kHubMatrixMaxGroups];
+  __shared__ uint16_t spos[kHubMatrixMaxGroups + 1];
+  __shared__ int wcnt[kThreads / 32];
   __shared__ unsigned long long part[kThreads / 32][2];
   __shared__ int64_t cur;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int G = (int)(hm_words / 4);
+  const int G = (int)(dense_words / 4);  // 128-bit groups of the dense slots
+  const int D = (int)(dense_words * 32);
   for (;;) {
     if (threadIdx.x == 0) cur = (int64_t)atomicAdd(counter, 1ull);
     __syncthreads();
@@ -348,8 +386,30 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
     if (unit >= __ldg(unit_off + ndense)) break;
     const int64_t idx = __ldg(unit_idx + unit);
     const int64_t e = dense_e[idx];
-    const uint4* m = reinterpret_cast<const uint4*>(tmask + idx * hm_words);
-    for (int i = threadIdx.x; i < G; i += kThreads) smask[i] = m[i];
+    const uint4* m = reinterpret_cast<const uint4*>(tmask + idx * dense_words);
+    int L = 0;  // non-zero groups so far (the same in every thread)
+    for (int i0 = 0; i0 < G; i0 += kThreads) {
+      const int i = i0 + threadIdx.x;
+      const uint4 mv = i < G ? m[i] : make_uint4(0u, 0u, 0u, 0u);
+      const bool nz = (mv.x | mv.y | mv.z | mv.w) != 0u;
+      const unsigned bal = __ballot_sync(kFull, nz);
+      if (lane == 0) wcnt[wid] = __popc(bal);
+      __syncthreads();
+      int before = L, total = L;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        before += w < wid ? wcnt[w] : 0;
+        total += wcnt[w];
+      }
+      const int at = before + __popc(bal & ((1u << lane) - 1u));
+      if (i < G) spos[i] = (uint16_t)at;
+      if (nz) {
+        smask[at] = mv;
+        sgrp[at] = (uint16_t)i;
+      }
+      L = total;
+      __syncthreads();  // wcnt is rewritten by the next round
+    }
+    if (threadIdx.x == 0) spos[G] = (uint16_t)L;
     __syncthreads();
     const int64_t b = toff[e];
     const int64_t r0 = (unit - __ldg(unit_off + idx)) * kDenseUnit;
@@ -357,17 +417,19 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
     unsigned long long acc = 0, groups = 0;
     for (int64_t c0 = r0 + (int64_t)wid * 32; c0 < len; c0 += kThreads) {
       const int xs = c0 + lane < len ? (int)__ldg(T_hm + b + c0 + lane) : -1;
-      unsigned members = __ballot_sync(kFull, xs >= 0);
+      unsigned members = __ballot_sync(kFull, xs >= 0 && xs < D);
       while (members) {
         const int src = __ffs(members) - 1;
         members &= members - 1;
         const int sl = __shfl_sync(kFull, xs, src);
         const int g0 = sl >> 7, b0 = sl & 127;
         const uint4* row = reinterpret_cast<const uint4*>(hm_bits + (int64_t)sl * hm_words);
-        groups += G - g0;
-        for (int gg = g0 + lane; gg < G; gg += 32) {
+        const int p0 = spos[g0];  // w's own group is non-zero (w is in T)
+        groups += L - p0;
+        for (int c = p0 + lane; c < L; c += 32) {
+          const int gg = sgrp[c];
           const uint4 rw = ld_keep4(row + gg);
-          const uint4 mk = smask[gg];
+          const uint4 mk = smask[c];
           uint32_t wd[4] = {rw.x & mk.x, rw.y & mk.y, rw.z & mk.z, rw.w & mk.w};
           if (gg == g0) {  // only the bits above w's own
 #pragma unroll
@@ -451,7 +513,7 @@ __device__ __forceinline__ void load_edge(const DevGraph& g, const int2* __restr
                                           const uint32_t* __restrict__ tmask, int64_t e,
                                           EdgeCtx& c) {
   const int32_t mi = mask_idx != nullptr ? mask_idx[e] : -1;
-  c.tmask = mi >= 0 ? tmask + (int64_t)mi * g.hm_words : nullptr;
+  c.tmask = mi >= 0 ? tmask + (int64_t)mi * g.hm_dense_words : nullptr;
   int2 pr = uv[e];
   c.e = e;
   c.u = pr.x;
@@ -562,8 +624,9 @@ __device__ __forceinline__ ItemCost item_cost(const DevGraph& g, const EdgeCtx& 
   const int64_t dw = __ldg(g.row_ptr + w + 1) - __ldg(g.row_ptr + w);
   if (in_t) {
     if (c.tmask != nullptr) {
-      // dense edge: only a vertex without a matrix slot scans N(w) here
-      if (__ldg(g.col_hm + p) < 0) r.a = (int32_t)dw;
+      // dense edge: only a vertex without a dense slot scans N(w) here
+      const int32_t sw = __ldg(g.col_hm + p);
+      if (sw < 0 || sw >= g.hm_dense_words * 32) r.a = (int32_t)dw;
     } else {
       // |N(w) above w cap T above w|: the shorter side is iterated
       const int64_t iw = tbase + __popc(tword & ((1u << lane) - 1u));
@@ -693,8 +756,9 @@ __device__ __noinline__ int64_t setup_item(const DevGraph& g, const int2* __rest
       int64_t bw;
       const int64_t dw = deg_of(g.row_ptr, w, &bw);
       if (in_t && c.tmask != nullptr) {
-        // dense edge: only a vertex without a matrix slot has segment A here
-        if (table_slot(g, w) < 0) {
+        // dense edge: only a vertex without a dense slot has segment A here
+        const int32_t sw = table_slot(g, w);
+        if (sw < 0 || sw >= g.hm_dense_words * 32) {
           amode = 2;
           si->it[0] = g.col + bw;
           si->sl[0] = T + c.toff;
@@ -761,164 +825,177 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
            const int64_t* __restrict__ task_off,
            int64_t groups, int need_k, int need_q, int64_t task_probes,
            unsigned long long* __restrict__ k_out,
-           unsigned long long* __restrict__ q) {
+           unsigned long long* __restrict__ q,
+           unsigned long long* __restrict__ task_counter) {
   __shared__ SharedItem items[kThreads / 32][32];
   __shared__ const uint32_t* chunk_mask[kThreads / 32];  // T mask of the chunk's edge
   const int lane = threadIdx.x & 31;
   SharedItem* my = items[threadIdx.x >> 5];
   const uint32_t** my_mask = chunk_mask + (threadIdx.x >> 5);
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int32_t dense_slots = (int32_t)(g.hm_dense_words * 32);
   const int64_t NT = __ldg(task_off + groups);
-  const int64_t per = (NT + warps - 1) / warps;
-  const int64_t t0 = warp * per, t1 = min(NT, t0 + per);
-  if (t0 >= t1) return;
-  int64_t gi = last_le(task_off, groups, t0);
-  int64_t e = last_le(off, K, gi * 32);
+  // warps take runs of consecutive tasks from a counter: tasks differ in
+  // cost (a chunk with few tests still pays a whole item set-up, tests
+  // differ in latency), so fixed per-warp ranges left a long tail
+  const int64_t grab = max((int64_t)1, kQuadGrabTests / task_probes);
+  int64_t gi = 0, e = 0;
   int64_t cur = -1, cur_e = -1;
   int64_t start = 0, ctotal = 0;
   unsigned acc_k = 0;
   int acc_q = 0;
-  for (int64_t task = t0; task < t1; ++task) {
-    while (gi + 1 < groups && __ldg(task_off + gi + 1) <= task) ++gi;
-    if (gi != cur) {
-      // flush the previous chunk's counts to its edge
-      const unsigned long long sk = warp_sum<unsigned long long>(acc_k);
-      const long long sq = warp_sum<long long>(acc_q);
-      if (lane == 0 && cur >= 0) {
-        if (sk) atomicAdd(k_out + cur_e, sk);
-        if (sq) atomicAdd(q + cur_e, (unsigned long long)sq);
-      }
-      acc_k = 0;
-      acc_q = 0;
-      while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
-      __syncwarp();
-      const uint2 cb = __ldg(reinterpret_cast<const uint2*>(cbits) + gi);
-      const int hint = (int)((cb.x >> lane) & 1u) * kHintLive +
-                       (int)((cb.y >> lane) & 1u) * kHintTabled;
-      const int64_t mine =
-          setup_item(g, uv, t, toff, mask_idx, tmask, e, T, gi * 32 + lane - __ldg(off + e),
-                     __ldg(tbits + gi), __ldg(tpre + gi), lane, need_q, hint, my + lane,
-                     my_mask);
-      __syncwarp();
-      int64_t incl = mine;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        int64_t y = __shfl_up_sync(kFull, incl, d);
-        if (lane >= d) incl += y;
-      }
-      start = incl - mine;
-      ctotal = __shfl_sync(kFull, incl, 31);
-      cur = gi;
-      cur_e = e;
+  int64_t next = -1;  // the task after this warp's previous run
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(task_counter, (unsigned long long)grab);
+    const int64_t t0 = (int64_t)__shfl_sync(kFull, got, 0);
+    if (t0 >= NT) break;
+    const int64_t t1 = min(NT, t0 + grab);
+    if (t0 != next) {
+      gi = last_le(task_off, groups, t0);
+      e = last_le(off, K, gi * 32);
     }
-    const int64_t lo = (task - __ldg(task_off + gi)) * task_probes;
-    const int32_t len = (int32_t)min(ctotal - lo, task_probes);
-    // item starts relative to the task's first test, in 32 bits: clamping
-    // keeps their order and never touches the item that holds a test of
-    // this task (it starts less than one item's tests before lo)
-    const int32_t srel = (int32_t)max(min(start - lo, task_probes), (int64_t)INT32_MIN + 1);
-    // Two independent tests per lane per iteration (r and r + 32): their
-    // loads are issued together so each warp keeps more requests in flight.
-    for (int32_t r = lane; r - lane < len; r += 64) {
-      int32_t x[2], xs[2], seg[2], o[2];
-      const SharedItem* it[2];
-      bool act[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int32_t rr = r + 32 * h;  // test index within the task
-        int j = 0;  // item = last lane whose start <= rr
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-          const int32_t sv = __shfl_sync(kFull, srel, j + step);
-          if (sv <= rr) j += step;
+    next = t1;
+    for (int64_t task = t0; task < t1; ++task) {
+      while (gi + 1 < groups && __ldg(task_off + gi + 1) <= task) ++gi;
+      if (gi != cur) {
+        // flush the previous chunk's counts to its edge
+        const unsigned long long sk = warp_sum<unsigned long long>(acc_k);
+        const long long sq = warp_sum<long long>(acc_q);
+        if (lane == 0 && cur >= 0) {
+          if (sk) atomicAdd(k_out + cur_e, sk);
+          if (sq) atomicAdd(q + cur_e, (unsigned long long)sq);
         }
-        const int32_t sj = __shfl_sync(kFull, srel, j);
-        act[h] = rr < len;
-        it[h] = &my[j];
-        o[h] = rr - sj;
-        seg[h] = o[h] < it[h]->ca ? 0 : 1;
-        if (seg[h]) o[h] -= it[h]->ca;
-        x[h] = 0;
-        xs[h] = -1;
-        if (act[h]) {
-          const int32_t* ip = it[h]->it[seg[h]] + o[h];
-          x[h] = __ldg(ip);
-          xs[h] = kNoSlotInfo;
-          if (T_hm != nullptr) {  // matrix slots stored beside the list
-            const size_t pc = (size_t)(ip - g.col);
-            xs[h] = pc < (size_t)g.nnz ? (int32_t)__ldg(g.col_hm + pc)
-                                       : (int32_t)__ldg(T_hm + (ip - T));
-          }
+        acc_k = 0;
+        acc_q = 0;
+        while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
+        __syncwarp();
+        const uint2 cb = __ldg(reinterpret_cast<const uint2*>(cbits) + gi);
+        const int hint = (int)((cb.x >> lane) & 1u) * kHintLive +
+                         (int)((cb.y >> lane) & 1u) * kHintTabled;
+        const int64_t mine =
+            setup_item(g, uv, t, toff, mask_idx, tmask, e, T, gi * 32 + lane - __ldg(off + e),
+                       __ldg(tbits + gi), __ldg(tpre + gi), lane, need_q, hint, my + lane,
+                       my_mask);
+        __syncwarp();
+        int64_t incl = mine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          int64_t y = __shfl_up_sync(kFull, incl, d);
+          if (lane >= d) incl += y;
         }
+        start = incl - mine;
+        ctotal = __shfl_sync(kFull, incl, 31);
+        cur = gi;
+        cur_e = e;
       }
-      // constant-time word for matrix / bitmap answers, or the bucket bounds
-      // of a directory, issued for both
-      uint32_t word[2], bitpos[2];
-      bool direct[2], bucket[2];
+      const int64_t lo = (task - __ldg(task_off + gi)) * task_probes;
+      const int32_t len = (int32_t)min(ctotal - lo, task_probes);
+      // item starts relative to the task's first test, in 32 bits: clamping
+      // keeps their order and never touches the item that holds a test of
+      // this task (it starts less than one item's tests before lo)
+      const int32_t srel = (int32_t)max(min(start - lo, task_probes), (int64_t)INT32_MIN + 1);
+      // Two independent tests per lane per iteration (r and r + 32): their
+      // loads are issued together so each warp keeps more requests in flight.
+      for (int32_t r = lane; r - lane < len; r += 64) {
+        int32_t x[2], xs[2], seg[2], o[2];
+        const SharedItem* it[2];
+        bool act[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        direct[h] = false;
-        bucket[h] = false;
-        word[h] = 0;
-        bitpos[h] = 0;
-        if (!act[h]) continue;
-        if (seg[h] == 0 && (it[h]->mode & 0xff) == 2) {
-          // rest mode (sbm[0] holds w): a matrix member x is in T iff its
-          // bit is set in the edge's T mask; other x count only above w and
-          // are searched in T
-          if (xs[h] >= 0) {
-            word[h] = (*my_mask)[xs[h] >> 5];
-            bitpos[h] = xs[h] & 31;
-            direct[h] = true;
-          } else if (x[h] <= it[h]->sbm[0]) {
-            direct[h] = true;  // word 0: no hit
+        for (int h = 0; h < 2; ++h) {
+          const int32_t rr = r + 32 * h;  // test index within the task
+          int j = 0;  // item = last lane whose start <= rr
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int32_t sv = __shfl_sync(kFull, srel, j + step);
+            if (sv <= rr) j += step;
           }
-          continue;
+          const int32_t sj = __shfl_sync(kFull, srel, j);
+          act[h] = rr < len;
+          it[h] = &my[j];
+          o[h] = rr - sj;
+          seg[h] = o[h] < it[h]->ca ? 0 : 1;
+          if (seg[h]) o[h] -= it[h]->ca;
+          x[h] = 0;
+          xs[h] = -1;
+          if (act[h]) {
+            const int32_t* ip = it[h]->it[seg[h]] + o[h];
+            x[h] = __ldg(ip);
+            xs[h] = kNoSlotInfo;
+            if (T_hm != nullptr) {  // matrix slots stored beside the list
+              const size_t pc = (size_t)(ip - g.col);
+              xs[h] = pc < (size_t)g.nnz ? (int32_t)__ldg(g.col_hm + pc)
+                                         : (int32_t)__ldg(T_hm + (ip - T));
+            }
+          }
         }
-        const int sslot = it[h]->sslot[seg[h]];
-        if (sslot == kDenseRow) {
-          const int32_t lx = x[h] - it[h]->sbm[seg[h]];
-          word[h] = __ldg(reinterpret_cast<const uint32_t*>(it[h]->sl[seg[h]]) + (lx >> 5));
-          bitpos[h] = lx & 31;
-          direct[h] = true;
-          continue;
-        }
-        if (sslot >= 0) {
-          if (xs[h] == kNoSlotInfo) xs[h] = __ldg(g.hm_slot + x[h]);
-          if (xs[h] >= 0) {
-            word[h] = ld_keep(g.hm_bits + (int64_t)sslot * g.hm_words + (xs[h] >> 5));
-            bitpos[h] = xs[h] & 31;
+        // constant-time word for matrix / bitmap answers, or the bucket bounds
+        // of a directory, issued for both
+        uint32_t word[2], bitpos[2];
+        bool direct[2], bucket[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          direct[h] = false;
+          bucket[h] = false;
+          word[h] = 0;
+          bitpos[h] = 0;
+          if (!act[h]) continue;
+          if (seg[h] == 0 && (it[h]->mode & 0xff) == 2) {
+            // rest mode (sbm[0] holds w): a dense-slot member x is in T iff
+            // its bit is set in the edge's T mask; other x count only above w
+            // and are searched in T
+            if (xs[h] >= 0 && xs[h] < dense_slots) {
+              word[h] = (*my_mask)[xs[h] >> 5];
+              bitpos[h] = xs[h] & 31;
+              direct[h] = true;
+            } else if (x[h] <= it[h]->sbm[0]) {
+              direct[h] = true;  // word 0: no hit
+            }
+            continue;
+          }
+          const int sslot = it[h]->sslot[seg[h]];
+          if (sslot == kDenseRow) {
+            const int32_t lx = x[h] - it[h]->sbm[seg[h]];
+            word[h] = __ldg(reinterpret_cast<const uint32_t*>(it[h]->sl[seg[h]]) + (lx >> 5));
+            bitpos[h] = lx & 31;
             direct[h] = true;
             continue;
           }
+          if (sslot >= 0) {
+            if (xs[h] == kNoSlotInfo) xs[h] = __ldg(g.hm_slot + x[h]);
+            if (xs[h] >= 0) {
+              word[h] = ld_keep(g.hm_bits + (int64_t)sslot * g.hm_words + (xs[h] >> 5));
+              bitpos[h] = xs[h] & 31;
+              direct[h] = true;
+              continue;
+            }
+          }
+          const int sbm = it[h]->sbm[seg[h]];
+          if (sbm >= 0) {
+            word[h] = __ldg(g.bm_bits + (int64_t)sbm * g.bm_words + (x[h] >> 5));
+            bitpos[h] = x[h] & 31;
+            direct[h] = true;
+          } else if (sbm < -1) {
+            const uint32_t* d =
+                g.dir + (uint32_t)it[h]->slen[seg[h]] + (uint32_t)(x[h] >> (-2 - sbm));
+            word[h] = __ldg(d);
+            bitpos[h] = __ldg(d + 1);
+            bucket[h] = true;
+          }
         }
-        const int sbm = it[h]->sbm[seg[h]];
-        if (sbm >= 0) {
-          word[h] = __ldg(g.bm_bits + (int64_t)sbm * g.bm_words + (x[h] >> 5));
-          bitpos[h] = x[h] & 31;
-          direct[h] = true;
-        } else if (sbm < -1) {
-          const uint32_t* d =
-              g.dir + (uint32_t)it[h]->slen[seg[h]] + (uint32_t)(x[h] >> (-2 - sbm));
-          word[h] = __ldg(d);
-          bitpos[h] = __ldg(d + 1);
-          bucket[h] = true;
-        }
-      }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!act[h]) continue;
-        bool hit = direct[h]   ? ((word[h] >> bitpos[h]) & 1u) != 0
-                   : bucket[h] ? bucket_contains(it[h]->sl[seg[h]] + word[h],
-                                                 (int32_t)(bitpos[h] - word[h]), x[h])
-                               : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
-        if (hit) {
-          if (seg[h] == 0) {
-            ++acc_k;
-            acc_q += need_q ? 2 : 0;
-          } else {
-            acc_q += (it[h]->mode >> 8) - 1;
+        for (int h = 0; h < 2; ++h) {
+          if (!act[h]) continue;
+          bool hit = direct[h]   ? ((word[h] >> bitpos[h]) & 1u) != 0
+                     : bucket[h] ? bucket_contains(it[h]->sl[seg[h]] + word[h],
+                                                   (int32_t)(bitpos[h] - word[h]), x[h])
+                                 : sorted_contains(it[h]->sl[seg[h]], it[h]->slen[seg[h]], x[h]);
+          if (hit) {
+            if (seg[h] == 0) {
+              ++acc_k;
+              acc_q += need_q ? 2 : 0;
+            } else {
+              acc_q += (it[h]->mode >> 8) - 1;
+            }
           }
         }
       }
@@ -1132,12 +1209,15 @@ namespace gs {
 
 // 8 triangle-pass CTAs per SM (32 registers) and 512-test tasks: measured
 // best on the 1M-vertex power-law graph (triangle pass 79 -> 47 ms exact).
-Tuning default_tuning() { return Tuning{8, kQuadBlocksPerSm, 512, 1}; }
+Tuning default_tuning() { return Tuning{8, kQuadBlocksPerSm, 512, 1, kHubDenseSlots}; }
 
 int quad_blocks_limit() { return kQuadBlocksPerSm; }
 
 DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
   DevGraph g = gr->dev;
+  g.hm_dense_words =
+      g.hm_bits != nullptr ? std::min(g.hm_words, std::max<int64_t>(tu.dense_slots, 0) / 128 * 4)
+                           : 0;
   if (!tu.use_hubs) {
     g.bm_slot = nullptr;
     g.bm_bits = nullptr;
@@ -1275,7 +1355,7 @@ int64_t launch_compact(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
 int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
   if (b.ndense <= 0 || g.col_hm == nullptr) return 0;
   k_build_tmask<<<grid_for(b.K * 32, kThreads, 8), kThreads, 0, stream>>>(
-      b.toff, b.t, b.T_hm, b.mask_idx, b.K, g.hm_words, b.tmask, b.dense_e, b.unit_off);
+      b.toff, b.t, b.T_hm, b.mask_idx, b.K, g.hm_dense_words, b.tmask, b.dense_e, b.unit_off);
   exclusive_scan_i64(b.unit_off, b.unit_off, b.ndense, b.unit_tmp, stream);
   k_unit_fill<<<grid_for(b.ndense * 32, kThreads, 8), kThreads, 0, stream>>>(b.unit_off, b.ndense,
                                                                               b.unit_idx);
@@ -1287,7 +1367,8 @@ int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
 int64_t launch_dense(const DevGraph& g, bool need_q, CountBufs& b, cudaStream_t stream) {
   if (b.ndense <= 0 || g.col_hm == nullptr) return 0;
   k_dense_pairs<<<sm_count() * kDenseBlocksPerSm, kThreads, 0, stream>>>(
-      g.hm_bits, g.hm_words, b.toff, b.t, b.T_hm, b.tmask, b.dense_e, b.unit_off, b.unit_idx,
+      g.hm_bits, g.hm_words, g.hm_dense_words, b.toff, b.t, b.T_hm, b.tmask, b.dense_e,
+      b.unit_off, b.unit_idx,
       b.ndense, need_q ? 1 : 0,
       b.k2, b.q, b.stats + 7, b.stats + 4);
   return 1;
@@ -1317,7 +1398,7 @@ int64_t launch_quad(const DevGraph& g, bool need_k, bool need_q, const Tuning& t
                                             g.col_hm != nullptr ? b.T_hm : nullptr,
                                             g.col_hm != nullptr ? b.mask_idx : nullptr, b.tmask,
                                             b.task_off, b.groups, need_k, need_q,
-                                            tu.task_probes, b.k2, b.q);
+                                            tu.task_probes, b.k2, b.q, b.stats + 5);
   return 1;
 }
 
@@ -1441,14 +1522,14 @@ gs_status count_run(const gs_graph* gr, gs_workspace* ws, const int32_t* d_pairs
     if (b.ndense > 0) {
       void* base4 = nullptr;
       GS_TRY(ws_reserve(ws, 4,
-                        Carve::bytes_for<uint32_t>(b.ndense * g.hm_words) +
+                        Carve::bytes_for<uint32_t>(b.ndense * g.hm_dense_words) +
                             Carve::bytes_for<int64_t>(b.ndense) +
                             Carve::bytes_for<int64_t>(b.ndense + 1) +
                             Carve::bytes_for<int64_t>(scan_tmp_elems(b.ndense + 1)) +
                             Carve::bytes_for<int32_t>(b.tsum / kDenseUnit + b.ndense),
                         stream, &base4));
       Carve c4{(char*)base4, 0};
-      b.tmask = c4.take<uint32_t>(b.ndense * g.hm_words);
+      b.tmask = c4.take<uint32_t>(b.ndense * g.hm_dense_words);
       b.dense_e = c4.take<int64_t>(b.ndense);
       b.unit_off = c4.take<int64_t>(b.ndense + 1);
       b.unit_tmp = c4.take<int64_t>(scan_tmp_elems(b.ndense + 1));
@@ -1578,7 +1659,19 @@ extern "C" gs_status gs_workspace_set_tuning(gs_workspace* ws, int tri_blocks_pe
               kQuadBlocksPerSm);
     return GS_EINVAL;
   }
-  ws->tuning = Tuning{tri_blocks_per_sm, quad_blocks_per_sm, task_probes, use_hubs ? 1 : 0};
+  const int64_t ds = ws->has_tuning ? ws->tuning.dense_slots : kHubDenseSlots;
+  ws->tuning = Tuning{tri_blocks_per_sm, quad_blocks_per_sm, task_probes, use_hubs ? 1 : 0, ds};
+  ws->has_tuning = 1;
+  return GS_OK;
+}
+
+extern "C" gs_status gs_workspace_set_dense_slots(gs_workspace* ws, int64_t slots) {
+  if (ws == nullptr || slots < 0) {
+    set_error("gs_workspace_set_dense_slots: null workspace or negative slot count");
+    return GS_EINVAL;
+  }
+  if (!ws->has_tuning) ws->tuning = default_tuning();
+  ws->tuning.dense_slots = slots;
   ws->has_tuning = 1;
   return GS_OK;
 }

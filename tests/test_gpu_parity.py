@@ -35,8 +35,10 @@ def _graph(rp, col, **kw):
 NO_HUBS = 1  # a 1-byte hub budget disables bitmaps and the co-degree table
 
 
-def _full_check(rp, col, pairs, mask=gs.GS_CONNECTED, ids=ALL, hub_budget=0):
+def _full_check(rp, col, pairs, mask=gs.GS_CONNECTED, ids=ALL, hub_budget=0, dense_slots=None):
     g = _graph(rp, col, hub_budget_bytes=hub_budget)
+    if dense_slots is not None:
+        g.ws.set_dense_slots(dense_slots)
     per = torch.zeros((len(pairs), 3), dtype=torch.int64, device="cuda")
     dpairs = torch.as_tensor(pairs, dtype=torch.int32, device="cuda")
     sums = g.count(dpairs, mask, per_edge=per)
@@ -352,6 +354,43 @@ def test_dense_clique_mode_mixed_t_against_oracle():
     g.close()
     _full_check(rp, col, sample)
     _full_check(rp, col, sample, hub_budget=NO_HUBS)
+
+
+@pytest.mark.parametrize("slots", [384, 0, 1 << 20])
+def test_dense_slots_below_the_matrix_size(slots):
+    """Only the first `slots` matrix slots take part in dense mode; the other
+    matrix vertices of a dense edge's T scan their adjacency (rest mode) and
+    still answer single tests from the matrix. 0 turns dense mode off; a
+    count above the matrix size means every slot. (With 256 slots the cost
+    model already prefers plain tests on this graph.)"""
+    rp, col = _core_periphery()
+    sample = synth.explicit_sample(rp, col, 0.03, seed=9)
+    g = _graph(rp, col)
+    assert g.info["matrix_hubs"] > 384  # the whole core has matrix slots
+    g.ws.set_dense_slots(slots)
+    g.count(torch.as_tensor(sample, device="cuda"))
+    st = g.ws.stats()
+    if slots:
+        assert 0 < st["dense_edges"] < len(sample)
+    else:
+        assert st["dense_edges"] == 0
+    g.close()
+    _full_check(rp, col, sample, dense_slots=slots)
+
+
+def test_dense_slots_complete_graph():
+    n, edges = brute.family_edges("complete", 300)
+    rp, col = synth.from_pairs(n, np.array([e[0] for e in edges]), np.array([e[1] for e in edges]))
+    g = _graph(rp, col)
+    g.ws.set_dense_slots(256)
+    res = gs.gs_estimate(g.count(None)).as_dict()
+    assert g.ws.stats()["dense_edges"] == g.m
+    want = brute.closed_form("complete", 300)
+    for i in ALL:
+        assert res[i]["exact"] == want[i], i
+    with pytest.raises(gs.GraphletError):
+        g.ws.set_dense_slots(-1)
+    g.close()
 
 
 # ------------------------------------------------------------------ giant hubs
