@@ -66,9 +66,19 @@ constexpr unsigned kFull = 0xffffffffu;
 // word-parallel AND + popcount over hub-matrix rows.
 constexpr int kDenseMin = 64;
 constexpr unsigned long long kEmpty = ~0ull;
+// Device counters of one count (CountBufs::stats): 0 triangle-pass tests,
+// 1 4-node tests, 2 / 3 model bytes (3-node / 4-node part), 4 dense groups,
+// 5 k_quad task counter, 6 dense edges, 7 k_dense_pairs unit counter,
+// 8 k_chunk_cost chunk counter.
+constexpr int kStatSlots = 16;
+// Chunks per run a k_chunk_cost warp takes from its counter.
+constexpr int kCostGrab = 16;
 // Membership tests per run of consecutive tasks a k_quad warp takes from
 // the task counter (at least one task).
-constexpr int64_t kQuadGrabTests = 16384;
+#ifndef GS_QUAD_GRAB_TESTS
+#define GS_QUAD_GRAB_TESTS 16384
+#endif
+constexpr int64_t kQuadGrabTests = GS_QUAD_GRAB_TESTS;
 // Resident CTAs per SM of k_dense_pairs (at most 40 registers).
 constexpr int kDenseBlocksPerSm = 6;
 // T entries per k_dense_pairs work unit (a heavy dense edge is split into
@@ -665,30 +675,37 @@ __global__ void __launch_bounds__(kThreads, kCostBlocksPerSm)
                  unsigned long long* __restrict__ stats) {
   unsigned long long tests = 0;
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t P = __ldg(off + K);
   const int64_t groups = P >> 5;  // padded: P is a multiple of 32
-  const int64_t per = (groups + warps - 1) / warps;
-  const int64_t g0 = warp * per, g1 = min(groups, g0 + per);
-  if (g0 >= g1) return;
-  int64_t e = last_le(off, K, g0 * 32);
+  int64_t e = 0;
   EdgeCtx c;
-  load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
-  for (int64_t gi = g0; gi < g1; ++gi) {
-    while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
-    if (e != c.e) load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
-    const ItemCost it = item_cost(g, c, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi),
-                                  __ldg(tpre + gi), lane, need_q);
-    const unsigned live = __ballot_sync(kFull, it.a + it.b > 0);
-    const unsigned tabled = __ballot_sync(kFull, it.tabled);
-    if (lane == 0) reinterpret_cast<uint2*>(cbits)[gi] = make_uint2(live, tabled);
-    int64_t cost = warp_sum<int64_t>((int64_t)it.a + it.b);
-    int64_t qc = warp_sum<int64_t>(it.qconst);
-    if (lane == 0) {
-      task_cnt[gi] = (cost + task_probes - 1) / task_probes;
-      if (qc != 0) atomicAdd(q + e, (unsigned long long)qc);
-      tests += cost;
+  c.e = -1;
+  int64_t next = -1;  // the chunk after this warp's previous run
+  // runs of kCostGrab consecutive chunks from a counter (chunks differ in
+  // cost: table answers, hub edges)
+  for (;;) {
+    unsigned long long got = 0;
+    if (lane == 0) got = atomicAdd(stats + 8, (unsigned long long)kCostGrab);
+    const int64_t g0 = (int64_t)__shfl_sync(kFull, got, 0);
+    if (g0 >= groups) break;
+    const int64_t g1 = min(groups, g0 + (int64_t)kCostGrab);
+    if (g0 != next) e = last_le(off, K, g0 * 32);
+    next = g1;
+    for (int64_t gi = g0; gi < g1; ++gi) {
+      while (e + 1 < K && __ldg(off + e + 1) <= gi * 32) ++e;
+      if (e != c.e) load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
+      const ItemCost it = item_cost(g, c, gi * 32 + lane - __ldg(off + e), __ldg(tbits + gi),
+                                    __ldg(tpre + gi), lane, need_q);
+      const unsigned live = __ballot_sync(kFull, it.a + it.b > 0);
+      const unsigned tabled = __ballot_sync(kFull, it.tabled);
+      if (lane == 0) reinterpret_cast<uint2*>(cbits)[gi] = make_uint2(live, tabled);
+      int64_t cost = warp_sum<int64_t>((int64_t)it.a + it.b);
+      int64_t qc = warp_sum<int64_t>(it.qconst);
+      if (lane == 0) {
+        task_cnt[gi] = (cost + task_probes - 1) / task_probes;
+        if (qc != 0) atomicAdd(q + e, (unsigned long long)qc);
+        tests += cost;
+      }
     }
   }
   if (lane == 0 && tests) atomicAdd(stats + 1, (unsigned long long)tests);
@@ -1243,7 +1260,7 @@ size_t count_front_bytes(int64_t K, bool all_edges, bool check_dup, int64_t nseg
   while (dup_cap < 2 * K) dup_cap <<= 1;
   const int fold_blocks = grid_for(K, kThreads, 2);
   return Carve::bytes_for<DevError>(1) + Carve::bytes_for<unsigned long long>(32) +
-         Carve::bytes_for<unsigned long long>(8) +
+         Carve::bytes_for<unsigned long long>(kStatSlots) +
          (all_edges ? Carve::bytes_for<int32_t>(2 * K) : 0) + Carve::bytes_for<int2>(K) +
          Carve::bytes_for<int64_t>(K + 1) * 2 + Carve::bytes_for<unsigned long long>(K) * 3 +
          Carve::bytes_for<int64_t>(K) + Carve::bytes_for<int32_t>(K) +
@@ -1265,7 +1282,7 @@ void carve_front(void* base, int64_t K, bool all_edges, bool check_dup, int64_t 
   b.fold_blocks = grid_for(K, kThreads, 2);
   b.err = c.take<DevError>(1);
   b.sums = c.take<unsigned long long>(32);
-  b.stats = c.take<unsigned long long>(8);
+  b.stats = c.take<unsigned long long>(kStatSlots);
   b.pairs_all = all_edges ? c.take<int32_t>(2 * K) : nullptr;
   b.uv = c.take<int2>(K);
   b.off = c.take<int64_t>(K + 1);
@@ -1308,7 +1325,7 @@ int64_t launch_front(const gs_graph* gr, const DevGraph& g, const int32_t* pairs
   int64_t launches = 0;
   const int64_t K = b.K;
   cudaMemsetAsync(b.err, 0, sizeof(DevError), stream);
-  cudaMemsetAsync(b.stats, 0, sizeof(unsigned long long) * 8, stream);
+  cudaMemsetAsync(b.stats, 0, sizeof(unsigned long long) * kStatSlots, stream);
   cudaMemsetAsync(b.t, 0, sizeof(unsigned long long) * K, stream);
   if (four) {
     cudaMemsetAsync(b.k2, 0, sizeof(unsigned long long) * K, stream);
