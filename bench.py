@@ -292,6 +292,7 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
     total_edges, total_ms, total_inc = 0, 0.0, 0
     lat_by = {label: [] for label, _, _ in parts}
     quad_ms, tests, groups, model_bytes, quad_launches = 0.0, 0, 0, 0, 0
+    units_by = {}  # 4-node units (tests + dense groups) per part label
     launches0 = gs.gs_count_stats(ws.handle).launches_total
     with ClockSampler(device) as clocks:
         for step in range(steps):
@@ -303,13 +304,14 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
             total_ms += sum(ms for _, ms in lat)
             for label, ms in lat:
                 lat_by[label].append(ms)
-            for qms, qt, qg, qb in quad:
+            for (label, _), (qms, qt, qg, qb) in zip(lat, quad):
                 if qms > 0:
                     quad_ms += qms
                     tests += qt
                     groups += qg
                     model_bytes += qb
                     quad_launches += 1
+                    units_by[label] = units_by.get(label, 0) + qt + qg
     torch.cuda.synchronize()
     launches = gs.gs_count_stats(ws.handle).launches_total - launches0
     if world > 1:
@@ -362,8 +364,13 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
     secs = quad_ms / 1e3
     achieved = alg_bytes / secs / 1e9 if secs > 0 else 0.0
     traffic = load_traffic(f"quad_phase_{name}")
-    units_per_launch = (tests + groups) / max(quad_launches, 1)
-    traffic_bytes = traffic["dram_bytes_per_test"] * units_per_launch if traffic else None
+    traffic_bytes = None
+    if traffic:
+        # DRAM bytes per unit measured per sample fraction on the small case
+        # (a larger sample reuses more of L2), applied to each part's units
+        bpu = traffic["dram_bytes_per_unit"]
+        traffic_bytes = sum(units * bpu.get(label, bpu["default"])
+                            for label, units in units_by.items()) / max(quad_launches, 1)
     avg_s = secs / max(quad_launches, 1)
     roofline = {
         "kernel": "4-node phase: k_quad (membership tests) + k_dense_pairs (dense-edge "
@@ -374,7 +381,8 @@ def run_gpu(args, rank, world, device, name, rp, col, steps, warmup):
                        "128-bit dense group",
         "traffic": round(traffic_bytes) if traffic_bytes else None,
         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_quad + "
-                           "k_dense_pairs per test on a small case, x tests per launch")
+                           "k_dense_pairs per unit on a small case at the same sample "
+                           "fractions, x each part's units")
         if traffic else None,
         "dram_frac": round(traffic_bytes / avg_s / 1e9 / peak, 4) if traffic_bytes else None,
         "avg_launch_ms": round(quad_ms / max(quad_launches, 1), 3),
@@ -653,9 +661,9 @@ def run_serve_bench(args):
     srv = gs.Server(hbm_budget_bytes=40 << 30, max_batch=64, lanes=4)
     ids = [srv.add_numpy(rp, col) for rp, col in graphs]
     t0 = time.time()
-    srv.start()
+    srv.start(hub_budget_bytes=20 << 30)  # eight resident graphs share the GPU
     start_s = time.time() - t0
-    singles = [gs.Graph.from_numpy(rp, col) for rp, col in graphs]
+    singles = [gs.Graph.from_numpy(rp, col, hub_budget_bytes=20 << 30) for rp, col in graphs]
     for gi in range(len(graphs)):  # warm-up
         srv.wait(srv.submit(ids[gi], 0.001, 1, gs.GS_THREE_NODE))
         singles[gi].count_estimate(0.001, 1, gs.GS_THREE_NODE)

@@ -124,7 +124,7 @@ const char* gs_version(void);
  * top 32767 of them, and a co-degree table |N(a) cap N(b)| among the top
  * vertices, plus a mid x big co-degree table and adjacency bucket
  * directories, see gs_graph_index_info) in library-owned device memory;
- * hub_budget_bytes bounds that index (0 = default 20 GiB: bitmaps and
+ * hub_budget_bytes bounds that index (0 = default 64 GiB: bitmaps and
  * matrix up to 1/8 each, directories up to 1/16, the 16-bit co-degree table
  * most of the rest, at most 65535 vertices, the mid x big table and a table
  * slot per adjacency entry whatever remains).

@@ -33,7 +33,15 @@ constexpr int kThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int64_t kInChunk = 256;      // in-neighbours per work unit
 constexpr int32_t kMaxOutDegree = 4096;  // larger out-lists: the general pass
-constexpr int kOrientBlocksPerSm = 4;
+// Resident CTAs per SM (shared memory allows 6-7 at R-MAT scale 24's
+// 4096-slot tables, 8 for shorter out-lists). R-MAT 24 exact 3-node pass:
+// 0.42 s at 4, 0.31 s at 6 and 8.
+#ifndef GS_ORIENT_BLOCKS_PER_SM
+#define GS_ORIENT_BLOCKS_PER_SM 8
+#endif
+constexpr int kOrientBlocksPerSm = GS_ORIENT_BLOCKS_PER_SM;
+// Out-list entries a lane loads before it probes them (loads in flight).
+constexpr int kProbeBatch = 4;
 
 typedef unsigned __int128 u128;
 
@@ -136,7 +144,9 @@ __device__ __forceinline__ uint32_t slot_hash(int32_t x, int bits) {
 
 // Triangles by middle vertex (see the file comment). Persistent CTAs take
 // units from a counter; dynamic shared memory holds the hash table of
-// N+(v): keys (int32, -1 empty), counts of (v, x), out-list positions.
+// N+(v): keys (int32, -1 empty) and one word per slot holding the out-list
+// position of x (low 16 bits) and the count of (v, x) (high 16 bits: at
+// most kInChunk per unit).
 __global__ void __launch_bounds__(kThreads, kOrientBlocksPerSm)
     k_tri_oriented(const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_col,
                    const int64_t* __restrict__ in_ptr, const int32_t* __restrict__ in_col,
@@ -147,8 +157,7 @@ __global__ void __launch_bounds__(kThreads, kOrientBlocksPerSm)
   extern __shared__ int32_t smem[];
   const int S = 1 << bits;
   int32_t* keys = smem;
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + S);
-  uint32_t* pos = cnt + S;
+  uint32_t* slotw = reinterpret_cast<uint32_t*>(smem + S);
   __shared__ int64_t cur;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t U = __ldg(unit_off + n);
@@ -168,31 +177,41 @@ __global__ void __launch_bounds__(kThreads, kOrientBlocksPerSm)
     const int64_t ob = out_ptr[v], od = out_ptr[v + 1] - ob;
     const int64_t j0 = in_ptr[v] + (unit - __ldg(unit_off + v)) * kInChunk;
     const int64_t j1 = min(in_ptr[v + 1], j0 + kInChunk);
-    for (int s = threadIdx.x; s < S; s += kThreads) {
-      keys[s] = -1;
-      cnt[s] = 0;
-    }
+    // this unit's table: the smallest power of two >= 2 |N+(v)| (at least
+    // 64 slots), so short out-lists clear and flush only a few slots
+    int ub_bits = 6;
+    while ((1ll << ub_bits) < 2 * od) ++ub_bits;
+    const int Su = 1 << ub_bits;
+    for (int s = threadIdx.x; s < Su; s += kThreads) keys[s] = -1;
     __syncthreads();
     for (int64_t i = threadIdx.x; i < od; i += kThreads) {
       const int32_t x = out_col[ob + i];
-      uint32_t s = slot_hash(x, bits);
-      while (atomicCAS(keys + s, -1, x) != -1) s = (s + 1) & (uint32_t)(S - 1);
-      pos[s] = (uint32_t)i;
+      uint32_t s = slot_hash(x, ub_bits);
+      while (atomicCAS(keys + s, -1, x) != -1) s = (s + 1) & (uint32_t)(Su - 1);
+      slotw[s] = (uint32_t)i;  // position, count 0
     }
     __syncthreads();
     for (int64_t j = j0 + wid; j < j1; j += kThreads / 32) {
       const int32_t u = in_col[j];
       const int64_t ub = out_ptr[u], ud = out_ptr[u + 1] - ub;
       unsigned hits = 0;
-      for (int64_t i = lane; i < ud; i += 32) {
-        const int32_t x = __ldg(out_col + ub + i);
-        uint32_t s = slot_hash(x, bits);
-        int32_t k;
-        while ((k = keys[s]) != -1 && k != x) s = (s + 1) & (uint32_t)(S - 1);
-        if (k == x) {
-          ++hits;
-          atomicAdd(cnt + s, 1u);
-          atomicAdd(tplus + ub + i, 1u);  // edge (u, x)
+      for (int64_t i0 = lane; i0 < ud; i0 += 32 * kProbeBatch) {
+        int32_t xb[kProbeBatch];
+#pragma unroll
+        for (int q = 0; q < kProbeBatch; ++q)
+          xb[q] = i0 + 32 * q < ud ? __ldg(out_col + ub + i0 + 32 * q) : -1;
+#pragma unroll
+        for (int q = 0; q < kProbeBatch; ++q) {
+          const int32_t x = xb[q];
+          if (x < 0) continue;
+          uint32_t s = slot_hash(x, ub_bits);
+          int32_t k;
+          while ((k = keys[s]) != -1 && k != x) s = (s + 1) & (uint32_t)(Su - 1);
+          if (k == x) {
+            ++hits;
+            atomicAdd(slotw + s, 1u << 16);
+            atomicAdd(tplus + ub + i0 + 32 * q, 1u);  // edge (u, x)
+          }
         }
       }
       my_probes += (unsigned long long)(ud > lane ? (ud - lane + 31) / 32 : 0);
@@ -200,8 +219,10 @@ __global__ void __launch_bounds__(kThreads, kOrientBlocksPerSm)
       if (lane == 0 && hits) atomicAdd(tplus + in_pos[j], hits);  // edge (u, v)
     }
     __syncthreads();
-    for (int s = threadIdx.x; s < S; s += kThreads)
-      if (keys[s] != -1 && cnt[s] != 0) atomicAdd(tplus + ob + pos[s], cnt[s]);  // edge (v, x)
+    for (int s = threadIdx.x; s < Su; s += kThreads) {
+      const uint32_t w = slotw[s];
+      if (keys[s] != -1 && (w >> 16) != 0) atomicAdd(tplus + ob + (w & 0xffffu), w >> 16);  // (v, x)
+    }
     __syncthreads();  // the table and cur are reused for the next unit
   }
   my_probes = __reduce_add_sync(kFull, (unsigned)min(my_probes, 0xffffffffull));
@@ -345,7 +366,7 @@ gs_status count_tri_oriented(const gs_graph* g, gs_workspace* ws, unsigned long 
   const int64_t n = g->dev.n, m = g->m;
   int bits = 6;
   while ((1 << bits) < 2 * g->max_out_degree) ++bits;
-  const size_t smem = (size_t)(1 << bits) * 3 * sizeof(int32_t);
+  const size_t smem = (size_t)(1 << bits) * 2 * sizeof(int32_t);
   const int fold_blocks = grid_for(n * 32, kThreads, 2);
   void* base = nullptr;
   GS_TRY(ws_reserve(ws, 0,
@@ -367,7 +388,7 @@ gs_status count_tri_oriented(const gs_graph* g, gs_workspace* ws, unsigned long 
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr_set[dev]) {
     GS_CUDA(cudaFuncSetAttribute(k_tri_oriented, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)(2 * kMaxOutDegree) * 3 * sizeof(int32_t))));
+                                 (int)((size_t)(2 * kMaxOutDegree) * 2 * sizeof(int32_t))));
     attr_set[dev] = true;
   }
   if (ws->timing) cudaEventRecord(ws->ev[2], stream);
