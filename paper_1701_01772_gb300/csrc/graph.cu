@@ -207,55 +207,150 @@ __global__ void k_dense_rows(const int64_t* __restrict__ row_ptr, const int32_t*
   }
 }
 
-// Mid x big co-degrees: every vertex x adds 1 to c(w, h) for each mid
-// neighbour w (tb_slot[w] = -2 - row) and big neighbour h (x is a common
-// neighbour of w and h). Entries are 16 bits wide, updated through the 32-bit
-// word that holds them; a co-degree is below the mid vertex's degree
-// (< 65536), so no carry reaches the neighbouring entry. One warp per vertex;
-// x's big neighbours are gathered in shared memory kBigChunk at a time (the
-// table has at most kBigMax columns).
+// Mid x big co-degrees, one table row at a time: c(w, b) for a mid vertex w
+// (tb_slot[w] = -2 - row) and the bg_count big vertices b is the number of
+// x in N(w) with b in N(x). A CTA holds the row's counters in shared memory
+// (16 bits each, two per 32-bit word: a co-degree is below the mid vertex's
+// degree < 65536, so no carry reaches the neighbouring counter), adds, for
+// every x in N(w), one to the counter of each big neighbour of x (the
+// 16-bit column slots of x's big neighbours, listed beforehand), and writes
+// the finished row out. The whole CTA walks the concatenation of the
+// big-neighbour lists of N(w) (kMidRowThreads entries at a time): warps
+// take 32-position segments, one position per lane, so a hub in N(w) with
+// thousands of big neighbours is spread over all warps.
 #ifndef GS_BIG_MAX
 #define GS_BIG_MAX 65536
 #endif
 constexpr int kBigMax = GS_BIG_MAX;
-constexpr int kBigChunk = 1024;
-__global__ void __launch_bounds__(256) k_mid_big_pairs(const int64_t* __restrict__ row_ptr,
-                                                       const int32_t* __restrict__ col, int64_t n,
-                                                       const int32_t* __restrict__ tb_slot,
-                                                       const int32_t* __restrict__ bg_slot,
-                                                       int64_t bg_count,
-                                                       uint32_t* __restrict__ words) {
-  __shared__ int32_t bigs[8][kBigChunk];
+static_assert(kBigMax <= 65536, "column slots are stored in 16 bits");
+constexpr int kBigMin = 1024;  // narrowest shape tried
+constexpr int kMidRowThreads = 1024;
+
+// Number of big neighbours of every vertex. One warp per vertex.
+__global__ void k_big_count(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            int64_t n, const int32_t* __restrict__ bg_slot,
+                            int64_t* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
-  int32_t* mine = bigs[threadIdx.x >> 5];
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
-    const int64_t s = row_ptr[x], e = row_ptr[x + 1];
-    int64_t p0 = s;  // next adjacency entry to scan for big neighbours
-    while (p0 < e) {
-      // gather big neighbours until the chunk could overflow on the next 32
-      int nb = 0;
-      for (; p0 < e && nb <= kBigChunk - 32; p0 += 32) {
-        const int64_t p = p0 + lane;
-        const int32_t c = p < e ? __ldg(bg_slot + col[p]) : -1;
-        const unsigned ball = __ballot_sync(0xffffffffu, c >= 0);
-        if (c >= 0) mine[nb + __popc(ball & ((1u << lane) - 1u))] = c;
-        nb += __popc(ball);
+    unsigned c = 0;
+    for (int64_t p = row_ptr[x] + lane; p < row_ptr[x + 1]; p += 32) c += __ldg(bg_slot + col[p]) >= 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) cnt[x] = c;
+  }
+}
+
+// Column slots of the big neighbours of every vertex, in adjacency order,
+// at off[x]. One warp per vertex.
+__global__ void k_big_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                           int64_t n, const int32_t* __restrict__ bg_slot,
+                           const int64_t* __restrict__ off, uint16_t* __restrict__ list) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+    int64_t at = off[x];
+    for (int64_t p0 = row_ptr[x]; p0 < row_ptr[x + 1]; p0 += 32) {
+      const int64_t p = p0 + lane;
+      const int32_t b = p < row_ptr[x + 1] ? __ldg(bg_slot + col[p]) : -1;
+      const unsigned ball = __ballot_sync(0xffffffffu, b >= 0);
+      if (b >= 0) list[at + __popc(ball & ((1u << lane) - 1u))] = (uint16_t)b;
+      at += __popc(ball);
+    }
+  }
+}
+
+// Vertex of every mid row.
+__global__ void k_mid_row_vertex(const int32_t* __restrict__ tb_slot, int64_t n,
+                                 int32_t* __restrict__ rows_v) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t s = tb_slot[v];
+    if (s < -1) rows_v[-2 - s] = (int32_t)v;
+  }
+}
+
+__global__ void __launch_bounds__(kMidRowThreads, 1)
+    k_mid_rows(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+               const int32_t* __restrict__ rows_v, int64_t rows,
+               const int64_t* __restrict__ boff, const uint16_t* __restrict__ blist,
+               int64_t bg_count, uint16_t* __restrict__ md,
+               unsigned long long* __restrict__ counter) {
+  extern __shared__ uint32_t acc[];  // (bg_count + 1) / 2 words
+  // the current kMidRowThreads entries of N(w) that have big neighbours:
+  // list offset and first position in the concatenation of their lists
+  __shared__ int64_t sbo[kMidRowThreads];
+  __shared__ int32_t sst[kMidRowThreads];
+  __shared__ int32_t wn[kMidRowThreads / 32], wl[kMidRowThreads / 32];
+  __shared__ int64_t cur;
+  constexpr int kWarps = kMidRowThreads / 32;
+  const int W = (int)((bg_count + 1) / 2);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) cur = (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();  // the previous row has been written out
+    const int64_t r = cur;
+    if (r >= rows) break;
+    for (int i = threadIdx.x; i < W; i += kMidRowThreads) acc[i] = 0u;
+    const int32_t w = rows_v[r];
+    const int64_t s = row_ptr[w], d = row_ptr[w + 1] - s;
+    for (int64_t c0 = 0; c0 < d; c0 += kMidRowThreads) {
+      int64_t bo = 0;
+      int32_t len = 0;
+      if (c0 + threadIdx.x < d) {
+        const int32_t x = col[s + c0 + threadIdx.x];
+        bo = boff[x];
+        len = (int32_t)(boff[x + 1] - bo);
       }
-      __syncwarp();
-      if (nb > 0) {
-        for (int64_t p = s + lane; p < e; p += 32) {
-          const int32_t r = __ldg(tb_slot + col[p]);
-          if (r > -2) continue;
-          const int64_t base = (int64_t)(-2 - r) * bg_count;
-          for (int i = 0; i < nb; ++i) {
-            const int64_t at = base + mine[i];
-            atomicAdd(words + (at >> 1), 1u << (16 * (int)(at & 1)));
-          }
+      // block-wide exclusive scans of (len > 0) and len
+      const unsigned nz = __ballot_sync(0xffffffffu, len > 0);
+      int32_t incl = len;
+#pragma unroll
+      for (int k = 1; k < 32; k <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, k);
+        if (lane >= k) incl += y;
+      }
+      if (lane == 31) {
+        wn[wid] = __popc(nz);
+        wl[wid] = incl;
+      }
+      __syncthreads();
+      int32_t bn = 0, bl = 0, cnt = 0, total = 0;
+      for (int k = 0; k < kWarps; ++k) {
+        if (k < wid) {
+          bn += wn[k];
+          bl += wl[k];
+        }
+        cnt += wn[k];
+        total += wl[k];
+      }
+      if (len > 0) {
+        const int at = bn + __popc(nz & ((1u << lane) - 1u));
+        sbo[at] = bo;
+        sst[at] = bl + incl - len;
+      }
+      __syncthreads();
+      // 32-position segments of the concatenation, one per warp at a time;
+      // a segment spans at most 32 entries (all non-empty)
+      for (int32_t q0 = wid * 32; q0 < total; q0 += kMidRowThreads) {
+        int k0 = 0;  // last entry starting at or before q0
+        for (int step = kMidRowThreads / 2; step > 0; step >>= 1)
+          if (k0 + step < cnt && sst[k0 + step] <= q0) k0 += step;
+        const int32_t q = q0 + lane;
+        int k = k0;  // last entry starting at or before q
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (k + step < cnt && sst[k + step] <= q) k += step;
+        if (q < total) {
+          const uint32_t b = __ldg(blist + sbo[k] + (q - sst[k]));
+          atomicAdd(acc + (b >> 1), 1u << (16 * (b & 1u)));
         }
       }
-      __syncwarp();
+      __syncthreads();  // sbo, sst, wn and wl are reused by the next chunk
     }
+    __syncthreads();
+    const uint16_t* a16 = reinterpret_cast<const uint16_t*>(acc);
+    uint16_t* out = md + r * bg_count;
+    for (int64_t c = threadIdx.x; c < bg_count; c += kMidRowThreads) out[c] = a16[c];
   }
 }
 
@@ -877,7 +972,7 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     }
     int64_t d_bg = 0, n_bg = 0, d_md = d_hi;
     double best = -1.0;
-    for (int64_t cols = kBigChunk; cols <= kBigMax; cols *= 2) {
+    for (int64_t cols = kBigMin; cols <= kBigMax; cols *= 2) {
       const int64_t bg_cap = g->dev.tb_count < cols ? g->dev.tb_count : cols;
       int64_t dbg = 0, nbg = 0;
       GS_TRY(hub_threshold(g, bg_cap, d_tb, d_cnt, stream, &dbg, &nbg));
@@ -931,13 +1026,37 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
         const int64_t nwords = (rows * n_bg + 1) / 2;
         cudaError_t me = cudaMalloc(&g->md_codeg, sizeof(uint32_t) * (size_t)nwords);
         if (me != cudaSuccess) return cuda_fail(me, "mid x big table", __FILE__, __LINE__);
-        GS_CUDA(cudaMemsetAsync(g->md_codeg, 0, sizeof(uint32_t) * (size_t)nwords, stream));
         k_set_mid_rows<<<grid_for(n, 256, 8), 256, 0, stream>>>(flag, g->dev.row_ptr, n, d_md,
                                                                 d_hi, g->tb_slot);
-        k_mid_big_pairs<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(
-            g->dev.row_ptr, g->dev.col, n, g->tb_slot, g->bg_slot, n_bg,
-            reinterpret_cast<uint32_t*>(g->md_codeg));
-        cudaError_t e = cudaStreamSynchronize(stream);
+        // big-neighbour lists (flag is free again: offsets), row vertices
+        k_big_count<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.col, n,
+                                                                  g->bg_slot, flag);
+        GS_TRY(exclusive_scan_i64(flag, flag, n, tmp, stream));
+        int64_t nb = 0;
+        GS_CUDA(cudaMemcpyAsync(&nb, flag + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+        GS_CUDA(cudaStreamSynchronize(stream));
+        uint16_t* blist = nullptr;
+        int32_t* rows_v = nullptr;
+        cudaError_t le = cudaMalloc(&blist, sizeof(uint16_t) * (size_t)(nb > 0 ? nb : 1));
+        if (le == cudaSuccess) le = cudaMalloc(&rows_v, sizeof(int32_t) * (size_t)rows);
+        if (le != cudaSuccess) {
+          cudaFree(blist);
+          return cuda_fail(le, "mid x big table lists", __FILE__, __LINE__);
+        }
+        k_big_fill<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(g->dev.row_ptr, g->dev.col, n,
+                                                                 g->bg_slot, flag, blist);
+        k_mid_row_vertex<<<grid_for(n, 256, 8), 256, 0, stream>>>(g->tb_slot, n, rows_v);
+        const size_t row_smem = sizeof(uint32_t) * (size_t)((n_bg + 1) / 2);
+        cudaError_t e = cudaFuncSetAttribute(k_mid_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)row_smem);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream);
+        if (e == cudaSuccess) {
+          k_mid_rows<<<sm_count(), kMidRowThreads, row_smem, stream>>>(
+              g->dev.row_ptr, g->dev.col, rows_v, rows, flag, blist, n_bg, g->md_codeg, d_cnt);
+          e = cudaStreamSynchronize(stream);
+        }
+        cudaFree(blist);
+        cudaFree(rows_v);
         if (e != cudaSuccess) return cuda_fail(e, "mid x big table", __FILE__, __LINE__);
         g->dev.bg_slot = g->bg_slot;
         g->dev.md_codeg = g->md_codeg;
