@@ -124,10 +124,12 @@ const char* gs_version(void);
  * top 32767 of them, and a co-degree table |N(a) cap N(b)| among the top
  * vertices, plus a mid x big co-degree table and adjacency bucket
  * directories, see gs_graph_index_info) in library-owned device memory;
- * hub_budget_bytes bounds that index (0 = default 64 GiB: bitmaps and
- * matrix up to 1/8 each, directories up to 1/16, the 16-bit co-degree table
- * most of the rest, at most 65535 vertices, the mid x big table and a table
- * slot per adjacency entry whatever remains).
+ * hub_budget_bytes bounds that index (0 = default 96 GiB, a third of the
+ * GPU, for one large resident graph; pass less when several graphs share
+ * the device): bitmaps and matrix up to 1/8 each, directories up to 1/16,
+ * the 16-bit co-degree table most of the rest (at most 65535 vertices), the
+ * mid x big table and a table slot per adjacency entry whatever remains.
+ * The budget is an upper bound: a small graph's index stays small.
  * Synchronises `stream`. */
 gs_status gs_graph_create(const int64_t* d_row_ptr, const int32_t* d_col, int64_t n, int64_t nnz,
                           uint32_t flags, uint64_t hub_budget_bytes, void* stream,

@@ -16,9 +16,9 @@ constexpr int64_t kHubMinDegree = 64;
 constexpr int64_t kDirMinDegree = 16;
 // Mid rows of the mid x big co-degree table start at this degree, and their
 // build adds at most kMidWorkMax wedge increments (higher-degree rows first).
-// On R-MAT scale 24 with a 64 GiB budget the cap allows 419,899 rows x
-// 65,250 columns (registration 22 s instead of 9.5 s with 1.6e11, and the
-// 1% 4-node estimate in 1.16 s instead of 2.08 s).
+// On R-MAT scale 24 the cap leaves the budget binding: 637,384 rows x
+// 65,250 columns at 96 GiB (the 1% 4-node estimate in 1.02 s, against
+// 2.08 s with 234,019 x 16,317 under a cap of 1.6e11 and 20 GiB).
 constexpr int64_t kMidMinDegree = 2;
 #ifndef GS_MID_WORK_MAX
 #define GS_MID_WORK_MAX 640000000000ull
@@ -698,14 +698,14 @@ static gs_status hub_threshold(const gs_graph* g, int64_t cap, int64_t min_deg,
   return GS_OK;
 }
 
-// Builds, within `budget` bytes (0 = 64 GiB): bitmaps (up to 1/8 of the
+// Builds, within `budget` bytes (0 = 96 GiB): bitmaps (up to 1/8 of the
 // budget), the hub-pair matrix (up to 1/8, at most kHubMatrixMax vertices),
 // bucket directories (up to 1/16), the 16-bit co-degree table (most of the
 // rest, at most 65535 vertices), the mid x big table and, if room is left,
 // the table slot of every adjacency entry.
 static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stream) {
   const int64_t n = g->dev.n;
-  if (budget == 0) budget = (uint64_t)64 << 30;
+  if (budget == 0) budget = (uint64_t)96 << 30;
   if (n == 0 || g->max_degree < kHubMinDegree) return GS_OK;
   const int64_t words = (n + 31) / 32;
   // bitmaps and the matrix get up to 1/8 of the budget each, the table the rest
