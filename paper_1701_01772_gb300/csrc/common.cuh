@@ -98,6 +98,15 @@ struct DevGraph {
   // dense clique mode uses the first hm_dense_words * 32 slots (a multiple
   // of 128, at most hm_words * 32; 0 = no dense mode); set per call
   int64_t hm_dense_words;
+  // per vertex v, for the work of T's members without a dense slot in a
+  // dense edge: the matrix slots of v's matrix neighbours (in adjacency
+  // order) and v's neighbours above v without a matrix slot; hm_vertex =
+  // vertex of each matrix slot (all NULL without a matrix)
+  const int64_t* mn_ptr;   // [n+1]
+  const int16_t* mn_slot;  // [mn_ptr[n]]
+  const int64_t* nm_ptr;   // [n+1]
+  const int32_t* nm_col;   // [nm_ptr[n]]
+  const int32_t* hm_vertex;  // [hm_count]
   int64_t hm_count;
   // bucket directories of the adjacency lists of vertices that have no
   // bitmap (degree at least a threshold): the neighbours x of v with
@@ -256,6 +265,11 @@ struct gs_graph {
   int32_t* hm_slot;
   uint32_t* hm_bits;
   int16_t* col_hm;
+  int64_t* mn_ptr;
+  int16_t* mn_slot;
+  int64_t* nm_ptr;
+  int32_t* nm_col;
+  int32_t* hm_vertex;
   uint32_t* dm_bits;
   int64_t* dm_row;
   int32_t* dm_first;

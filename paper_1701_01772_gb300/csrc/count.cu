@@ -27,7 +27,8 @@
 //            32 positions.
 //   compact  T lists written in order with their hub-matrix slots (one warp
 //            per edge); edges with at least kDenseMin matrix members in T
-//            whose dense-mode work (row groups plus rest adjacency) is below
+//            whose dense-mode work (row groups plus the other members'
+//            neighbour lists) is below
 //            their sparse-mode tests are marked dense and get a T mask over
 //            matrix slots.
 //   cost     per chunk of 32 positions (items w = N(u)[i]): membership-test
@@ -35,13 +36,17 @@
 //            longer); constant terms (the -1s, table co-degrees) added
 //            directly; two ballots per chunk (items with tests, items a table
 //            answered) for the 4-node pass.
-//   quad     chunks are cut into tasks of task_probes tests; tasks are split
-//            evenly over all warps; inside a task lanes take consecutive
-//            tests (two per lane per iteration) and find their item by a
-//            search over the warp's scanned costs (load-balanced search).
-//   dense    in a dense edge the pairs of hub members of T are counted by
-//            k_dense_pairs: matrix rows ANDed with the T mask, 128 bits at a
-//            time, in work units of kDenseUnit T entries.
+//   quad     chunks are cut into tasks of task_probes tests; warps take
+//            runs of consecutive tasks from a counter; inside a task lanes
+//            take consecutive tests (two per lane per iteration) and find
+//            their item by a search over the warp's scanned costs
+//            (load-balanced search).
+//   dense    in a dense edge segment A is counted by k_dense_pairs, in work
+//            units of kDenseUnit T entries: pairs of dense-slot members by
+//            matrix rows ANDed with the T mask, 128 bits at a time; for the
+//            other members w, w's matrix neighbours (a bit of the mask, or,
+//            past the dense slots, a search of T when above w) and w's
+//            neighbours above w without a matrix slot (a search of T).
 //   fold     per edge numerators N_i in 128-bit, block partial sums, one
 //            final fixed-order pass (or per-segment limb sums, k_fold_seg).
 #include <string.h>
@@ -69,7 +74,8 @@ constexpr unsigned long long kEmpty = ~0ull;
 // Device counters of one count (CountBufs::stats): 0 triangle-pass tests,
 // 1 4-node tests, 2 / 3 model bytes (3-node / 4-node part), 4 dense groups,
 // 5 k_quad task counter, 6 dense edges, 7 k_dense_pairs unit counter,
-// 8 k_chunk_cost chunk counter.
+// 8 k_chunk_cost chunk counter, 9 tests of dense edges' members without a
+// dense slot (k_dense_pairs).
 constexpr int kStatSlots = 16;
 // Chunks per run a k_chunk_cost warp takes from its counter.
 constexpr int kCostGrab = 16;
@@ -302,8 +308,10 @@ __global__ void k_compact_T(DevGraph g, const int2* __restrict__ uv, const int64
           const int g0 = xs >> 7;
           groups += __popc(gb[g0 >> 5] & (~0u << (g0 & 31)));
           for (int w = (g0 >> 5) + 1; w < kGroupWords; ++w) groups += __popc(gb[w]);
-        } else {
-          dense += dx;
+        } else {  // k_dense_pairs walks its matrix and non-matrix-above lists
+          dense += g.mn_ptr != nullptr ? (__ldg(g.mn_ptr + x + 1) - __ldg(g.mn_ptr + x)) +
+                                             (__ldg(g.nm_ptr + x + 1) - __ldg(g.nm_ptr + x))
+                                       : dx;
         }
       }
       for (int o = 16; o > 0; o >>= 1) {
@@ -370,25 +378,34 @@ __global__ void k_unit_fill(const int64_t* __restrict__ unit_off, int64_t ndense
 // members among them with lanes over 128-bit groups (coalesced 512-byte
 // reads of the L2-resident matrix).
 __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
-    k_dense_pairs(const uint32_t* __restrict__ hm_bits, int64_t hm_words, int64_t dense_words,
-                  const int64_t* __restrict__ toff, const unsigned long long* __restrict__ t,
+    k_dense_pairs(const __grid_constant__ DevGraph g, const int64_t* __restrict__ toff,
+                  const unsigned long long* __restrict__ t, const int32_t* __restrict__ T,
                   const int16_t* __restrict__ T_hm, const uint32_t* __restrict__ tmask,
                   const int64_t* __restrict__ dense_e, const int64_t* __restrict__ unit_off,
                   const int32_t* __restrict__ unit_idx, int64_t ndense, int need_q,
                   unsigned long long* __restrict__ k_out, unsigned long long* __restrict__ q,
                   unsigned long long* __restrict__ counter,
-                  unsigned long long* __restrict__ tests) {
-  // the edge's T mask, compacted to its non-zero 128-bit groups: smask[c]
-  // is group sgrp[c]; spos[g] = number of non-zero groups below g
+                  unsigned long long* __restrict__ tests,
+                  unsigned long long* __restrict__ rest_tests) {
+  // the edge's T mask, whole (fmask) and compacted to its non-zero 128-bit
+  // groups: smask[c] is group sgrp[c]; spos[g] = number of non-zero groups
+  // below g
+  __shared__ uint4 fmask[kHubMatrixMaxGroups];
   __shared__ uint4 smask[kHubMatrixMaxGroups];
   __shared__ uint16_t sgrp[kHubMatrixMaxGroups];
   __shared__ uint16_t spos[kHubMatrixMaxGroups + 1];
-  __shared__ int wcnt[kThreads / 32];
-  __shared__ unsigned long long part[kThreads / 32][2];
+  __shared__ int wcnt[kThreads / 32], wlen[kThreads / 32];
+  // members without a dense slot among kThreads T entries: vertex, list
+  // offsets and lengths, first position in the concatenation of their lists
+  __shared__ int64_t ra[kThreads], rb[kThreads];
+  __shared__ int32_t rw[kThreads], rna[kThreads], rst[kThreads];
+  __shared__ unsigned long long part[kThreads / 32][3];
   __shared__ int64_t cur;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t dense_words = g.hm_dense_words;
   const int G = (int)(dense_words / 4);  // 128-bit groups of the dense slots
   const int D = (int)(dense_words * 32);
+  const uint32_t* fmask32 = reinterpret_cast<const uint32_t*>(fmask);
   for (;;) {
     if (threadIdx.x == 0) cur = (int64_t)atomicAdd(counter, 1ull);
     __syncthreads();
@@ -401,6 +418,7 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
     for (int i0 = 0; i0 < G; i0 += kThreads) {
       const int i = i0 + threadIdx.x;
       const uint4 mv = i < G ? m[i] : make_uint4(0u, 0u, 0u, 0u);
+      if (i < G) fmask[i] = mv;
       const bool nz = (mv.x | mv.y | mv.z | mv.w) != 0u;
       const unsigned bal = __ballot_sync(kFull, nz);
       if (lane == 0) wcnt[wid] = __popc(bal);
@@ -433,7 +451,7 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
         members &= members - 1;
         const int sl = __shfl_sync(kFull, xs, src);
         const int g0 = sl >> 7, b0 = sl & 127;
-        const uint4* row = reinterpret_cast<const uint4*>(hm_bits + (int64_t)sl * hm_words);
+        const uint4* row = reinterpret_cast<const uint4*>(g.hm_bits + (int64_t)sl * g.hm_words);
         const int p0 = spos[g0];  // w's own group is non-zero (w is in T)
         groups += L - p0;
         for (int c = p0 + lane; c < L; c += 32) {
@@ -453,25 +471,112 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
         }
       }
     }
+    // members without a dense slot: w's matrix neighbours x (a bit of the
+    // mask below D; past D, x = hm_vertex[s] counts when above w and in T)
+    // and w's neighbours above w without a matrix slot (counted when in T).
+    // The block walks the concatenation of these lists, 32 positions per
+    // warp at a time.
+    unsigned long long rhits = 0, rtested = 0;
+    const int64_t te = (int64_t)t[e];
+    const int32_t* Te = T + b;
+    for (int64_t c0 = r0; c0 < len; c0 += kThreads) {
+      const int64_t j = c0 + threadIdx.x;
+      int32_t w = -1, na = 0, nb = 0;
+      int64_t a0 = 0, b0 = 0;
+      if (j < len) {
+        const int xs = __ldg(T_hm + b + j);
+        if (!(xs >= 0 && xs < D)) {
+          w = __ldg(Te + j);
+          a0 = __ldg(g.mn_ptr + w);
+          na = (int32_t)(__ldg(g.mn_ptr + w + 1) - a0);
+          b0 = __ldg(g.nm_ptr + w);
+          nb = (int32_t)(__ldg(g.nm_ptr + w + 1) - b0);
+        }
+      }
+      const int32_t mine = na + nb;
+      const unsigned nz = __ballot_sync(kFull, mine > 0);
+      int32_t incl = mine;
+#pragma unroll
+      for (int k = 1; k < 32; k <<= 1) {
+        const int32_t y = __shfl_up_sync(kFull, incl, k);
+        if (lane >= k) incl += y;
+      }
+      if (lane == 31) {
+        wcnt[wid] = __popc(nz);
+        wlen[wid] = incl;
+      }
+      __syncthreads();
+      int32_t bn = 0, bl = 0, cnt = 0, total = 0;
+      for (int k = 0; k < kThreads / 32; ++k) {
+        if (k < wid) {
+          bn += wcnt[k];
+          bl += wlen[k];
+        }
+        cnt += wcnt[k];
+        total += wlen[k];
+      }
+      if (mine > 0) {
+        const int at = bn + __popc(nz & ((1u << lane) - 1u));
+        rw[at] = w;
+        ra[at] = a0;
+        rna[at] = na;
+        rb[at] = b0;
+        rst[at] = bl + incl - mine;
+      }
+      __syncthreads();
+      for (int32_t q0 = wid * 32; q0 < total; q0 += kThreads) {
+        int k0 = 0;  // last entry starting at or before q0
+        for (int step = kThreads / 2; step > 0; step >>= 1)
+          if (k0 + step < cnt && rst[k0 + step] <= q0) k0 += step;
+        const int32_t qq = q0 + lane;
+        int k = k0;  // last entry starting at or before qq (within 32)
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (k + step < cnt && rst[k + step] <= qq) k += step;
+        if (qq < total) {
+          const int32_t o = qq - rst[k];
+          bool hit;
+          if (o < rna[k]) {
+            const int sx = __ldg(g.mn_slot + ra[k] + o);
+            if (sx < D) {
+              hit = ((fmask32[sx >> 5] >> (sx & 31)) & 1u) != 0;
+            } else {
+              const int32_t x = __ldg(g.hm_vertex + sx);
+              hit = x > rw[k] && sorted_contains(Te, te, x);
+            }
+          } else {
+            hit = sorted_contains(Te, te, __ldg(g.nm_col + rb[k] + (o - rna[k])));
+          }
+          rhits += hit ? 1 : 0;
+          ++rtested;
+        }
+      }
+      __syncthreads();  // rw, ra, rb, rna, rst, wcnt and wlen are reused
+    }
+    acc += rhits;
     acc = warp_sum<unsigned long long>(acc);
+    rtested = warp_sum<unsigned long long>(rtested);
     if (lane == 0) {
       part[wid][0] = acc;
       part[wid][1] = groups;  // the same on every lane
+      part[wid][2] = rtested;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      unsigned long long sk = 0, sg = 0;
+      unsigned long long sk = 0, sg = 0, sr = 0;
       for (int w = 0; w < kThreads / 32; ++w) {
         sk += part[w][0];
         sg += part[w][1];
+        sr += part[w][2];
       }
       if (sk) {
         atomicAdd(k_out + e, sk);
         if (need_q) atomicAdd(q + e, 2 * sk);
       }
       if (sg) atomicAdd(tests, sg);
+      if (sr) atomicAdd(rest_tests, sr);
     }
-    __syncthreads();  // smask, part and cur are reused for the next unit
+    __syncthreads();  // the masks, part and cur are reused for the next unit
   }
 }
 
@@ -502,11 +607,9 @@ struct Seg {
   int32_t cnt;          // number of tests
 };
 
-// Segment-A modes of an item w in T (k_quad): 0 = tests (pairs above w),
-// 2 = rest (w has no matrix slot and the edge is dense: x over N(w),
-// counted when x is in T and either has a matrix slot or is above w). A
-// matrix member of a dense edge has no segment A there: k_dense_pairs
-// counts its pairs with other members.
+// Segment A of an item w in T (k_quad) counts the pairs above w. In a dense
+// edge no item has a segment A: k_dense_pairs counts all of that edge's
+// pairs.
 
 struct EdgeCtx {
   int64_t e;
@@ -634,9 +737,8 @@ __device__ __forceinline__ ItemCost item_cost(const DevGraph& g, const EdgeCtx& 
   const int64_t dw = __ldg(g.row_ptr + w + 1) - __ldg(g.row_ptr + w);
   if (in_t) {
     if (c.tmask != nullptr) {
-      // dense edge: only a vertex without a dense slot scans N(w) here
-      const int32_t sw = __ldg(g.col_hm + p);
-      if (sw < 0 || sw >= g.hm_dense_words * 32) r.a = (int32_t)dw;
+      // dense edge: segment A is k_dense_pairs' work (pairs of dense-slot
+      // members; the other members' matrix and non-matrix neighbours)
     } else {
       // |N(w) above w cap T above w|: the shorter side is iterated
       const int64_t iw = tbase + __popc(tword & ((1u << lane) - 1u));
@@ -732,9 +834,8 @@ __device__ __forceinline__ bool bucket_contains(const int32_t* __restrict__ p, i
 // Kept to 64 bytes: eight CTAs of 256 items then take 128 KB of shared
 // memory, which leaves the rest of the SM's 256 KB to the L1 cache that the
 // membership tests depend on. The matrix slots of an iterated list are found
-// beside it (col_hm for adjacency lists, T_hm for T), the rest-mode vertex
-// w sits in sbm[0] (a T search has no bitmap) and amode and the segment-B
-// sign share one word.
+// beside it (col_hm for adjacency lists, T_hm for T) and the segment-B sign
+// is stored in one word.
 struct SharedItem {
   const int32_t* it[2];
   const int32_t* sl[2];
@@ -742,7 +843,7 @@ struct SharedItem {
   int32_t slen[2];
   int16_t sslot[2];
   int32_t ca;
-  int32_t mode;  // amode | (bsign + 1) << 8
+  int32_t mode;  // (bsign + 1) << 8
 };
 static_assert(sizeof(SharedItem) == 64, "SharedItem size");
 
@@ -760,12 +861,10 @@ __device__ __noinline__ int64_t setup_item(const DevGraph& g, const int2* __rest
                                            const uint32_t* __restrict__ tmask, int64_t e,
                                            const int32_t* __restrict__ T, int64_t i,
                                            uint32_t tword, int32_t tbase, int lane, bool need_q,
-                                           int hint, SharedItem* si,
-                                           const uint32_t** chunk_mask) {
+                                           int hint, SharedItem* si) {
   EdgeCtx c;
   load_edge(g, uv, t, toff, mask_idx, tmask, e, c);
-  if (lane == 0) *chunk_mask = c.tmask;
-  int32_t ca = 0, cb = 0, amode = 0, bsign = 0;
+  int32_t ca = 0, cb = 0, bsign = 0;
   if (i < c.du && (hint & kHintLive)) {
     const int32_t w = __ldg(g.col + c.bu + i);
     if (w != c.v) {
@@ -773,17 +872,7 @@ __device__ __noinline__ int64_t setup_item(const DevGraph& g, const int2* __rest
       int64_t bw;
       const int64_t dw = deg_of(g.row_ptr, w, &bw);
       if (in_t && c.tmask != nullptr) {
-        // dense edge: only a vertex without a dense slot has segment A here
-        const int32_t sw = table_slot(g, w);
-        if (sw < 0 || sw >= g.hm_dense_words * 32) {
-          amode = 2;
-          si->it[0] = g.col + bw;
-          si->sl[0] = T + c.toff;
-          si->slen[0] = (int32_t)c.te;
-          si->sslot[0] = -1;
-          si->sbm[0] = w;
-          ca = (int32_t)dw;
-        }
+        // dense edge: segment A is done by k_dense_pairs
       } else if (in_t) {
         const int64_t iw = tbase + __popc(tword & ((1u << lane) - 1u));
         const int64_t tg = c.te - iw - 1;
@@ -828,7 +917,7 @@ __device__ __noinline__ int64_t setup_item(const DevGraph& g, const int2* __rest
   si->ca = ca;
   // per-hit weights: segment A adds one 4-clique pair (k += 1, q += 2 when q
   // is wanted); segment B adds bsign to q
-  si->mode = amode | ((bsign + 1) << 8);
+  si->mode = (bsign + 1) << 8;
   return (int64_t)ca + cb;
 }
 
@@ -845,11 +934,8 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
            unsigned long long* __restrict__ q,
            unsigned long long* __restrict__ task_counter) {
   __shared__ SharedItem items[kThreads / 32][32];
-  __shared__ const uint32_t* chunk_mask[kThreads / 32];  // T mask of the chunk's edge
   const int lane = threadIdx.x & 31;
   SharedItem* my = items[threadIdx.x >> 5];
-  const uint32_t** my_mask = chunk_mask + (threadIdx.x >> 5);
-  const int32_t dense_slots = (int32_t)(g.hm_dense_words * 32);
   const int64_t NT = __ldg(task_off + groups);
   // warps take runs of consecutive tasks from a counter: tasks differ in
   // cost (a chunk with few tests still pays a whole item set-up, tests
@@ -891,8 +977,7 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
                          (int)((cb.y >> lane) & 1u) * kHintTabled;
         const int64_t mine =
             setup_item(g, uv, t, toff, mask_idx, tmask, e, T, gi * 32 + lane - __ldg(off + e),
-                       __ldg(tbits + gi), __ldg(tpre + gi), lane, need_q, hint, my + lane,
-                       my_mask);
+                       __ldg(tbits + gi), __ldg(tpre + gi), lane, need_q, hint, my + lane);
         __syncwarp();
         int64_t incl = mine;
 #pragma unroll
@@ -956,19 +1041,6 @@ __global__ void __launch_bounds__(kThreads, kQuadBlocksPerSm)
           word[h] = 0;
           bitpos[h] = 0;
           if (!act[h]) continue;
-          if (seg[h] == 0 && (it[h]->mode & 0xff) == 2) {
-            // rest mode (sbm[0] holds w): a dense-slot member x is in T iff
-            // its bit is set in the edge's T mask; other x count only above w
-            // and are searched in T
-            if (xs[h] >= 0 && xs[h] < dense_slots) {
-              word[h] = (*my_mask)[xs[h] >> 5];
-              bitpos[h] = xs[h] & 31;
-              direct[h] = true;
-            } else if (x[h] <= it[h]->sbm[0]) {
-              direct[h] = true;  // word 0: no hit
-            }
-            continue;
-          }
           const int sslot = it[h]->sslot[seg[h]];
           if (sslot == kDenseRow) {
             const int32_t lx = x[h] - it[h]->sbm[seg[h]];
@@ -1246,6 +1318,11 @@ DevGraph graph_view(const gs_graph* gr, const Tuning& tu) {
     g.hm_slot = nullptr;
     g.hm_bits = nullptr;
     g.col_hm = nullptr;
+    g.mn_ptr = nullptr;
+    g.mn_slot = nullptr;
+    g.nm_ptr = nullptr;
+    g.nm_col = nullptr;
+    g.hm_vertex = nullptr;
     g.bg_slot = nullptr;
     g.md_codeg = nullptr;
     g.dir_at = nullptr;
@@ -1384,10 +1461,8 @@ int64_t launch_tmask(const DevGraph& g, CountBufs& b, cudaStream_t stream) {
 int64_t launch_dense(const DevGraph& g, bool need_q, CountBufs& b, cudaStream_t stream) {
   if (b.ndense <= 0 || g.col_hm == nullptr) return 0;
   k_dense_pairs<<<sm_count() * kDenseBlocksPerSm, kThreads, 0, stream>>>(
-      g.hm_bits, g.hm_words, g.hm_dense_words, b.toff, b.t, b.T_hm, b.tmask, b.dense_e,
-      b.unit_off, b.unit_idx,
-      b.ndense, need_q ? 1 : 0,
-      b.k2, b.q, b.stats + 7, b.stats + 4);
+      g, b.toff, b.t, b.T, b.T_hm, b.tmask, b.dense_e, b.unit_off, b.unit_idx, b.ndense,
+      need_q ? 1 : 0, b.k2, b.q, b.stats + 7, b.stats + 4, b.stats + 9);
   return 1;
 }
 
@@ -1638,7 +1713,7 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
                    stream, "gs_count"));
   const bool four = (mask & (GS_G7 | GS_G8 | GS_G9 | GS_G10 | GS_G11 | GS_G12)) != 0;
   unsigned long long h[32];
-  unsigned long long hs[8];
+  unsigned long long hs[kStatSlots];
   int64_t ntasks = 0;
   GS_CUDA(cudaMemcpyAsync(h, b.sums, sizeof(h), cudaMemcpyDeviceToHost, stream));
   GS_CUDA(cudaMemcpyAsync(hs, b.stats, sizeof(hs), cudaMemcpyDeviceToHost, stream));
@@ -1651,7 +1726,7 @@ extern "C" gs_status gs_count(const gs_graph* gr, gs_workspace* ws, const int32_
   st.k = K;
   st.tri_tests = (int64_t)hs[0];
   st.dense_edges = (int64_t)hs[6];
-  st.quad_tests = (int64_t)(hs[1] + hs[4]);
+  st.quad_tests = (int64_t)(hs[1] + hs[4] + hs[9]);
   st.dense_groups = (int64_t)hs[4];
   st.model_bytes = hs[2] + hs[3];
   st.model_tri_bytes = hs[2];

@@ -180,6 +180,43 @@ __global__ void k_col_slots(const int32_t* __restrict__ col, int64_t nnz,
     col_hm[p] = (int16_t)__ldg(slot + col[p]);
 }
 
+// Per vertex: matrix neighbours (mn) and neighbours above v without a
+// matrix slot (nm). One warp per vertex; counts first, then the lists in
+// adjacency order at the scanned offsets.
+__global__ void k_rest_lists(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                             const int16_t* __restrict__ col_hm, int64_t n,
+                             int64_t* __restrict__ mn_cnt, int64_t* __restrict__ nm_cnt,
+                             const int64_t* __restrict__ mn_off, const int64_t* __restrict__ nm_off,
+                             int16_t* __restrict__ mn_slot, int32_t* __restrict__ nm_col) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+    int64_t am = mn_off != nullptr ? mn_off[v] : 0, an = nm_off != nullptr ? nm_off[v] : 0;
+    unsigned cm = 0, cn = 0;
+    for (int64_t p0 = row_ptr[v]; p0 < row_ptr[v + 1]; p0 += 32) {
+      const int64_t p = p0 + lane;
+      const bool in = p < row_ptr[v + 1];
+      const int16_t s = in ? col_hm[p] : (int16_t)-1;
+      const int32_t x = in ? col[p] : -1;
+      const unsigned bm = __ballot_sync(0xffffffffu, in && s >= 0);
+      const unsigned bn = __ballot_sync(0xffffffffu, in && s < 0 && x > (int32_t)v);
+      const unsigned below = (1u << lane) - 1u;
+      if (mn_off != nullptr) {
+        if ((bm >> lane) & 1u) mn_slot[am + __popc(bm & below)] = s;
+        if ((bn >> lane) & 1u) nm_col[an + __popc(bn & below)] = x;
+      }
+      am += __popc(bm);
+      an += __popc(bn);
+      cm += __popc(bm);
+      cn += __popc(bn);
+    }
+    if (mn_off == nullptr && lane == 0) {
+      mn_cnt[v] = cm;
+      nm_cnt[v] = cn;
+    }
+  }
+}
+
 // col_tb[p] = table slot of col[p] (tb_slot encoding, mid rows included):
 // stored beside the adjacency so the cost pass reads it with the element
 // instead of gathering it per item before the table read.
@@ -821,6 +858,7 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   // ---- hub-pair bit matrix over the top vertices (kept small: it must stay
   // in L2 to pay off)
   int64_t d_hm = 0, n_hm = 0;
+  double rest_bytes = 0.0;  // col_hm and the lists built with the matrix
   if (hm_cap > 1) GS_TRY(hub_threshold(g, hm_cap, kHubMinDegree, d_cnt, stream, &d_hm, &n_hm));
   if (n_hm > 1) {
     int32_t* hubs = nullptr;
@@ -836,12 +874,38 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
     GS_CUDA(cudaMemsetAsync(g->hm_bits, 0, sizeof(uint32_t) * (size_t)(hm_words * n_hm), stream));
     k_hub_matrix<<<grid_for(n_hm * 256, 256, 8), 256, 0, stream>>>(
         g->dev.row_ptr, g->dev.col, g->hm_slot, hubs, n_hm, hm_words, g->hm_bits);
-    cudaFree(hubs);
+    g->hm_vertex = hubs;  // slot -> vertex
     GS_CUDA(cudaMalloc(&g->col_hm, sizeof(int16_t) * (size_t)(g->dev.nnz > 0 ? g->dev.nnz : 1)));
     if (g->dev.nnz > 0)
       k_col_slots<<<grid_for(g->dev.nnz, 256, 8), 256, 0, stream>>>(g->dev.col, g->dev.nnz,
                                                                     g->hm_slot, g->col_hm);
+    // matrix-neighbour and non-matrix-above lists (work of dense edges'
+    // members without a dense slot)
+    GS_CUDA(cudaMalloc(&g->mn_ptr, sizeof(int64_t) * (size_t)(n + 1)));
+    GS_CUDA(cudaMalloc(&g->nm_ptr, sizeof(int64_t) * (size_t)(n + 1)));
+    k_rest_lists<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(
+        g->dev.row_ptr, g->dev.col, g->col_hm, n, g->mn_ptr, g->nm_ptr, nullptr, nullptr, nullptr,
+        nullptr);
+    GS_TRY(exclusive_scan_i64(g->mn_ptr, g->mn_ptr, n, tmp, stream));
+    GS_TRY(exclusive_scan_i64(g->nm_ptr, g->nm_ptr, n, tmp, stream));
+    int64_t tot[2] = {0, 0};
+    GS_CUDA(cudaMemcpyAsync(tot, g->mn_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
+    GS_CUDA(cudaMemcpyAsync(tot + 1, g->nm_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            stream));
     GS_CUDA(cudaStreamSynchronize(stream));
+    GS_CUDA(cudaMalloc(&g->mn_slot, sizeof(int16_t) * (size_t)(tot[0] > 0 ? tot[0] : 1)));
+    GS_CUDA(cudaMalloc(&g->nm_col, sizeof(int32_t) * (size_t)(tot[1] > 0 ? tot[1] : 1)));
+    k_rest_lists<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(
+        g->dev.row_ptr, g->dev.col, g->col_hm, n, nullptr, nullptr, g->mn_ptr, g->nm_ptr,
+        g->mn_slot, g->nm_col);
+    rest_bytes = 16.0 * (double)(n + 1) + 2.0 * (double)tot[0] + 4.0 * (double)tot[1] +
+                 2.0 * (double)g->dev.nnz;
+    GS_CUDA(cudaStreamSynchronize(stream));
+    g->dev.mn_ptr = g->mn_ptr;
+    g->dev.mn_slot = g->mn_slot;
+    g->dev.nm_ptr = g->nm_ptr;
+    g->dev.nm_col = g->nm_col;
+    g->dev.hm_vertex = g->hm_vertex;
     g->dev.col_hm = g->col_hm;
     g->dev.hm_slot = g->hm_slot;
     g->dev.hm_bits = g->hm_bits;
@@ -920,7 +984,7 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   // the table (degree >= kMidMinDegree), columns for the top 1024-65536
   // table vertices; whatever the budget has left
   double used = (double)n_bm * (double)words * 4.0 +
-                (double)n_hm * (double)g->dev.hm_words * 4.0 +
+                (double)n_hm * (double)g->dev.hm_words * 4.0 + rest_bytes +
                 (double)g->dev.tb_count * (double)g->dev.tb_count + dir_bytes;
   const int64_t d_hi = d_tb < 65536 ? d_tb : 65536;
   if (g->dev.tb_count > 1 && d_hi > kMidMinDegree && (double)budget > used) {
@@ -1236,6 +1300,11 @@ extern "C" gs_status gs_graph_destroy(gs_graph* g) {
   cudaFree(g->hm_slot);
   cudaFree(g->hm_bits);
   cudaFree(g->col_hm);
+  cudaFree(g->mn_ptr);
+  cudaFree(g->mn_slot);
+  cudaFree(g->nm_ptr);
+  cudaFree(g->nm_col);
+  cudaFree(g->hm_vertex);
   cudaFree(g->dm_bits);
   cudaFree(g->dm_row);
   cudaFree(g->dm_first);
