@@ -585,8 +585,7 @@ __global__ void k_hub_nbr_count(const int64_t* __restrict__ row_ptr, const int32
 // (hence increasing slot).
 __global__ void k_hub_nbr_fill(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                const int32_t* __restrict__ slot, int64_t n,
-                               const int64_t* __restrict__ off, int32_t* __restrict__ lists,
-                               int32_t* __restrict__ owner) {
+                               const int64_t* __restrict__ off, int32_t* __restrict__ lists) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
@@ -598,43 +597,8 @@ __global__ void k_hub_nbr_fill(const int64_t* __restrict__ row_ptr, const int32_
       if (s >= 0) {
         int64_t at = pos + __popc(b & ((1u << lane) - 1u));
         lists[at] = s;
-        owner[at] = (int32_t)x;
       }
       pos += __popc(b);
-    }
-  }
-}
-
-// One thread per list entry i of vertex x: adds 1 to c(L[i], L[j]) for every
-// later entry j, i.e. x is a common neighbour of that hub pair (L is in
-// increasing slot order, so L[i] < L[j]). Entries are 16 bits wide, two to a
-// 32-bit word, in the upper triangle (tb_index). A co-degree is at most the
-// smaller degree, so it stays below 65,536 unless both hubs are "giants"
-// (degree >= 65,536, giant[slot] = index among them, else -1): those pairs
-// go to a 32-bit giant x giant table instead, and their 16-bit entry is
-// marked 0xFFFF afterwards.
-__global__ void k_codeg_pairs(const int32_t* __restrict__ lists, const int32_t* __restrict__ owner,
-                              const int64_t* __restrict__ off, int64_t total, int64_t count,
-                              const int32_t* __restrict__ giant, int64_t giants,
-                              uint32_t* __restrict__ giant_codeg, uint32_t* __restrict__ words) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t x = owner[i];
-    const int64_t end = off[x + 1];
-    const int64_t a = lists[i];
-    const int32_t ga = giant != nullptr ? giant[a] : -1;
-    const int64_t base = a * (2 * count - a - 1) / 2 - a - 1;  // tb_index(a, b) = base + b
-    for (int64_t j = i + 1; j < end; ++j) {
-      const int64_t b = __ldg(lists + j);
-      if (ga >= 0) {
-        const int32_t gb = giant[b];
-        if (gb >= 0) {
-          atomicAdd(giant_codeg + (int64_t)ga * giants + gb, 1u);
-          continue;
-        }
-      }
-      const int64_t at = base + b;
-      atomicAdd(words + (at >> 1), 1u << (16 * (int)(at & 1)));
     }
   }
 }
@@ -661,6 +625,116 @@ __global__ void k_giant_index(const int64_t* __restrict__ flag_scan, int64_t cou
 
 // Marks the 16-bit entries of giant pairs 0xFFFF (answered by the giant
 // table). One thread per slot a; only giant rows do work.
+// Co-degree table among the table vertices, one row at a time: row a holds
+// c(a, b) for b > a (contiguous in tb_index order), the number of x in N(a)
+// with b in N(x). A CTA accumulates the row in shared memory (16-bit
+// counters, two per word) from the table-neighbour lists of a's neighbours
+// -- each sorted by slot, so the part after a is a suffix found by a
+// halving search -- walked as one concatenation in 32-position segments per
+// warp, and writes the row once. Pairs of two giants (degree >= 65,536,
+// whose co-degree may not fit 16 bits) go to the 32-bit giant table by
+// global atomics instead (marked 0xFFFF afterwards by k_mark_giant_pairs).
+__global__ void __launch_bounds__(kMidRowThreads, 1)
+    k_table_rows(const int64_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                 const int32_t* __restrict__ tb_vertex, int64_t count,
+                 const int64_t* __restrict__ loff, const int32_t* __restrict__ lists,
+                 const int32_t* __restrict__ giant, int64_t giants,
+                 uint32_t* __restrict__ giant_codeg, uint16_t* __restrict__ tb,
+                 unsigned long long* __restrict__ counter) {
+  extern __shared__ uint32_t acc[];  // count / 2 words (row 0 is the longest)
+  __shared__ int64_t sbo[kMidRowThreads];
+  __shared__ int32_t sst[kMidRowThreads];
+  __shared__ int32_t wn[kMidRowThreads / 32], wl[kMidRowThreads / 32];
+  __shared__ int64_t cur;
+  constexpr int kWarps = kMidRowThreads / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (;;) {
+    if (threadIdx.x == 0) cur = (int64_t)atomicAdd(counter, 1ull);
+    __syncthreads();  // the previous row has been written out
+    const int64_t a = cur;
+    if (a >= count - 1) break;  // the last row is empty
+    const int64_t R = count - a - 1;
+    const int W = (int)((R + 1) / 2);
+    for (int i = threadIdx.x; i < W; i += kMidRowThreads) acc[i] = 0u;
+    const int32_t va = tb_vertex[a];
+    const int32_t ga = giant != nullptr ? giant[a] : -1;
+    const int64_t s = row_ptr[va], d = row_ptr[va + 1] - s;
+    for (int64_t c0 = 0; c0 < d; c0 += kMidRowThreads) {
+      int64_t bo = 0;
+      int32_t len = 0;
+      if (c0 + threadIdx.x < d) {
+        const int32_t x = col[s + c0 + threadIdx.x];
+        int64_t lo = loff[x];
+        const int64_t hi = loff[x + 1];
+        int64_t n = hi - lo;  // first entry above a (a itself is in the list)
+        while (n > 0) {
+          const int64_t h = n >> 1;
+          if (__ldg(lists + lo + h) <= a) {
+            lo += h + 1;
+            n -= h + 1;
+          } else {
+            n = h;
+          }
+        }
+        bo = lo;
+        len = (int32_t)(hi - lo);
+      }
+      const unsigned nz = __ballot_sync(0xffffffffu, len > 0);
+      int32_t incl = len;
+#pragma unroll
+      for (int k = 1; k < 32; k <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, k);
+        if (lane >= k) incl += y;
+      }
+      if (lane == 31) {
+        wn[wid] = __popc(nz);
+        wl[wid] = incl;
+      }
+      __syncthreads();
+      int32_t bn = 0, bl = 0, cnt = 0, total = 0;
+      for (int k = 0; k < kWarps; ++k) {
+        if (k < wid) {
+          bn += wn[k];
+          bl += wl[k];
+        }
+        cnt += wn[k];
+        total += wl[k];
+      }
+      if (len > 0) {
+        const int at = bn + __popc(nz & ((1u << lane) - 1u));
+        sbo[at] = bo;
+        sst[at] = bl + incl - len;
+      }
+      __syncthreads();
+      for (int32_t q0 = wid * 32; q0 < total; q0 += kMidRowThreads) {
+        int k0 = 0;
+        for (int step = kMidRowThreads / 2; step > 0; step >>= 1)
+          if (k0 + step < cnt && sst[k0 + step] <= q0) k0 += step;
+        const int32_t q = q0 + lane;
+        int k = k0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1)
+          if (k + step < cnt && sst[k + step] <= q) k += step;
+        if (q < total) {
+          const int32_t b = __ldg(lists + sbo[k] + (q - sst[k]));
+          const int32_t gb = ga >= 0 ? __ldg(giant + b) : -1;
+          if (gb >= 0) {
+            atomicAdd(giant_codeg + (int64_t)ga * giants + gb, 1u);
+          } else {
+            const uint32_t c = (uint32_t)(b - a - 1);
+            atomicAdd(acc + (c >> 1), 1u << (16 * (c & 1u)));
+          }
+        }
+      }
+      __syncthreads();  // sbo, sst, wn and wl are reused by the next chunk
+    }
+    __syncthreads();
+    const uint16_t* a16 = reinterpret_cast<const uint16_t*>(acc);
+    uint16_t* out = tb + tb_index(a, a + 1, count);
+    for (int64_t c = threadIdx.x; c < R; c += kMidRowThreads) out[c] = a16[c];
+  }
+}
+
 __global__ void k_mark_giant_pairs(const int32_t* __restrict__ giant, int64_t count,
                                    uint32_t* __restrict__ words) {
   for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < count;
@@ -922,9 +996,12 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
   if (tb_cap > 1) {
     GS_TRY(hub_threshold(g, tb_cap, kHubMinDegree, d_cnt, stream, &d_tb, &n_tb));
     if (n_tb > 1) {
-      int32_t* hubs = nullptr;
+      int32_t* hubs = nullptr;  // slot -> vertex, for the row build
       GS_TRY(assign(d_tb, &g->tb_slot, &hubs, n_tb));
-      cudaFree(hubs);
+      struct FreeHubs {
+        int32_t* p;
+        ~FreeHubs() { cudaFree(p); }
+      } hubs_guard{hubs};
       const int64_t tb_words = (n_tb * (n_tb - 1) / 2 + 1) / 2;
       GS_CUDA(cudaMalloc(&g->tb_codeg, sizeof(uint32_t) * (size_t)tb_words));
       GS_CUDA(cudaMemsetAsync(g->tb_codeg, 0, sizeof(uint32_t) * (size_t)tb_words, stream));
@@ -954,23 +1031,24 @@ static gs_status build_hub_index(gs_graph* g, uint64_t budget, cudaStream_t stre
       GS_CUDA(cudaMemcpyAsync(&total, flag + n, sizeof(int64_t), cudaMemcpyDeviceToHost, stream));
       GS_CUDA(cudaStreamSynchronize(stream));
       int32_t* lists = nullptr;
-      int32_t* owner = nullptr;
       GS_CUDA(cudaMalloc(&lists, sizeof(int32_t) * (size_t)(total > 0 ? total : 1)));
-      if (cudaMalloc(&owner, sizeof(int32_t) * (size_t)(total > 0 ? total : 1)) != cudaSuccess) {
-        cudaFree(lists);
-        set_error("hub index: out of device memory");
-        return GS_ENOMEM;
-      }
       k_hub_nbr_fill<<<grid_for(n * 32, 256, 8), 256, 0, stream>>>(
-          g->dev.row_ptr, g->dev.col, g->tb_slot, n, flag, lists, owner);
+          g->dev.row_ptr, g->dev.col, g->tb_slot, n, flag, lists);
       uint32_t* tb_w = reinterpret_cast<uint32_t*>(g->tb_codeg);
-      k_codeg_pairs<<<grid_for(total, 256, 8), 256, 0, stream>>>(
-          lists, owner, flag, total, n_tb, g->tb_giant, giants, g->tb_giant_codeg, tb_w);
-      if (g->tb_giant != nullptr)
-        k_mark_giant_pairs<<<grid_for(n_tb, 256, 8), 256, 0, stream>>>(g->tb_giant, n_tb, tb_w);
-      cudaError_t e = cudaStreamSynchronize(stream);
+      const size_t row_smem = sizeof(uint32_t) * (size_t)(n_tb / 2 + 1);
+      cudaError_t e = cudaFuncSetAttribute(k_table_rows,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)row_smem);
+      if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), stream);
+      if (e == cudaSuccess) {
+        k_table_rows<<<sm_count(), kMidRowThreads, row_smem, stream>>>(
+            g->dev.row_ptr, g->dev.col, hubs, n_tb, flag, lists, g->tb_giant, giants,
+            g->tb_giant_codeg, g->tb_codeg, d_cnt);
+        if (g->tb_giant != nullptr)
+          k_mark_giant_pairs<<<grid_for(n_tb, 256, 8), 256, 0, stream>>>(g->tb_giant, n_tb, tb_w);
+        e = cudaStreamSynchronize(stream);
+      }
       cudaFree(lists);
-      cudaFree(owner);
       if (e != cudaSuccess) return cuda_fail(e, "co-degree table", __FILE__, __LINE__);
       g->dev.tb_slot = g->tb_slot;
       g->dev.tb_codeg = g->tb_codeg;
