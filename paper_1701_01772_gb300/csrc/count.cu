@@ -79,6 +79,14 @@ constexpr unsigned long long kEmpty = ~0ull;
 constexpr int kStatSlots = 16;
 // Chunks per run a k_chunk_cost warp takes from its counter.
 constexpr int kCostGrab = 16;
+// Filter of a dense edge's T members without a matrix slot in k_dense_pairs:
+// 2^15 bits, built when T has at most kTFilterMaxT entries.
+constexpr int kTFilterWords = 1024;
+constexpr int64_t kTFilterMaxT = 16384;
+__device__ __forceinline__ uint32_t tfilter_hash(int32_t x) {
+  return ((uint32_t)x * 2654435761u) >> 17;
+}
+
 // Membership tests per run of consecutive tasks a k_quad warp takes from
 // the task counter (at least one task).
 #ifndef GS_QUAD_GRAB_TESTS
@@ -399,6 +407,9 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
   // offsets and lengths, first position in the concatenation of their lists
   __shared__ int64_t ra[kThreads], rb[kThreads];
   __shared__ int32_t rw[kThreads], rna[kThreads], rst[kThreads];
+  // hashed filter of T's members without a matrix slot (what the
+  // non-matrix lists search for): a clear bit means "not in T"
+  __shared__ uint32_t tfilt[kTFilterWords];
   __shared__ unsigned long long part[kThreads / 32][3];
   __shared__ int64_t cur;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -479,6 +490,17 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
     unsigned long long rhits = 0, rtested = 0;
     const int64_t te = (int64_t)t[e];
     const int32_t* Te = T + b;
+    const bool filt = te <= kTFilterMaxT;
+    if (filt) {
+      for (int i = threadIdx.x; i < kTFilterWords; i += kThreads) tfilt[i] = 0u;
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < te; i += kThreads)
+        if (__ldg(T_hm + b + i) < 0) {
+          const uint32_t h = tfilter_hash(__ldg(Te + i));
+          atomicOr(tfilt + (h >> 5), 1u << (h & 31u));
+        }
+      __syncthreads();
+    }
     for (int64_t c0 = r0; c0 < len; c0 += kThreads) {
       const int64_t j = c0 + threadIdx.x;
       int32_t w = -1, na = 0, nb = 0;
@@ -545,7 +567,9 @@ __global__ void __launch_bounds__(kThreads, kDenseBlocksPerSm)
               hit = x > rw[k] && sorted_contains(Te, te, x);
             }
           } else {
-            hit = sorted_contains(Te, te, __ldg(g.nm_col + rb[k] + (o - rna[k])));
+            const int32_t x = __ldg(g.nm_col + rb[k] + (o - rna[k]));
+            const uint32_t h = tfilter_hash(x);
+            hit = (!filt || ((tfilt[h >> 5] >> (h & 31u)) & 1u) != 0) && sorted_contains(Te, te, x);
           }
           rhits += hit ? 1 : 0;
           ++rtested;
