@@ -121,9 +121,12 @@ const char* gs_version(void);
  * GS_ENOTSORTED / GS_ESELFLOOP / GS_EDUP / GS_EASYM / GS_EINVAL returned.
  * Builds the per-graph index (upper-edge offsets for the sampler, adjacency
  * bitmaps of the highest-degree vertices, an adjacency bit matrix among the
- * top 32767 of them, and a co-degree table |N(a) cap N(b)| among the top
- * vertices, plus a mid x big co-degree table and adjacency bucket
- * directories, see gs_graph_index_info) in library-owned device memory;
+ * top 32767 of them with, per vertex, the matrix slots of its matrix
+ * neighbours and its neighbours above it outside the matrix, a co-degree
+ * table |N(a) cap N(b)| among the top vertices, plus a mid x big co-degree
+ * table, adjacency bucket directories and degree-oriented adjacency lists
+ * for the exact 3-node pass, see gs_graph_index_info) in library-owned
+ * device memory;
  * hub_budget_bytes bounds that index (0 = default 96 GiB, a third of the
  * GPU, for one large resident graph; pass less when several graphs share
  * the device): bitmaps and matrix up to 1/8 each, directories up to 1/16,
